@@ -1,0 +1,213 @@
+/*
+ * mnl.h - C ABI of the GB300 multinomial-logit Newton-Raphson library.
+ *
+ * Model (Sec. 2.1, eq. "unormalized utility"): observation i chooses one of K
+ * alternatives (k = 0 is the base, Sec. 2.1 "normalizing") with utility
+ *     U_ik = X_i . beta_k + Y_ik . gamma_k + Z_ik . alpha
+ * X: individual-specific data with per-alternative coefficients beta_k
+ * (beta_0 = 0; an intercept is an X column of ones, Sec. 3.1); Y: alternative-
+ * specific data with per-alternative coefficients gamma_k; Z: alternative-
+ * specific data with one generic coefficient alpha.  P_ik is the softmax of
+ * U_i. over k (eqs. "probability", "base probability"), l the log-likelihood
+ * (eq. "log-lik function"), and one Newton-Raphson step (eq. "NR update",
+ * Sec. 3.1) is  theta <- theta + t (-H)^{-1} g  with t = 1, 1/2, ... chosen by
+ * step halving until l does not decrease.
+ *
+ * Coefficient vector theta (eq. "theta vec"), float64:
+ *     [ beta_1 .. beta_{K-1} (p each) | gamma_{1 or 0} .. gamma_{K-1} (d each) | alpha (f) ]
+ * gamma_base = 0 (default): gamma_0 is fixed at 0 and the k = 0 rows of Y are
+ *   ignored; n_theta = (K-1)(p+d) + f.
+ * gamma_base = 1: gamma_0 is estimated as in the paper; n_theta = (K-1)p + Kd + f.
+ *   (Accepted by mnl_num_params; mnl_create returns MNL_ERR_UNSUPPORTED.)
+ *
+ * Data layout (all row-major, float32, read-only, owned by the caller):
+ *     X      [N][p]       individual-specific columns
+ *     Y      [N][K][d]    alternative-specific, per-alternative coefficients (NULL if d = 0)
+ *     Z      [N][K][f]    alternative-specific, generic coefficient; raw values, the
+ *                         library uses only differences against alternative 0 (NULL if f = 0)
+ *     choice [N]          int32 in [0, K), the observed alternative
+ *
+ * Devices and streams: every entry point works on the CUDA device that was
+ * current at mnl_create and enqueues its work on the stream given there (NULL:
+ * the legacy default stream).  Pointers documented as "device" must be device
+ * (or managed) memory of that device.
+ *
+ * Errors: every int-returning function returns MNL_OK (0) or one of the
+ * MNL_ERR_* codes below; no C++ exception crosses this boundary.  After
+ * MNL_ERR_CUDA the handle should be destroyed.  mnl_status_string gives text.
+ */
+#ifndef MNL_H
+#define MNL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MNL_API __attribute__((visibility("default")))
+#else
+#define MNL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  MNL_OK = 0,
+  MNL_ERR_INVALID_ARG = 1, /* bad size, NULL required pointer, choice out of range          */
+  MNL_ERR_OOM = 2,         /* a device allocation failed                                     */
+  MNL_ERR_CUDA = 3,        /* a CUDA runtime/driver call failed                              */
+  MNL_ERR_NOT_PD = 4,      /* Cholesky of -H found a non-positive pivot: singular design     */
+  MNL_ERR_NONFINITE = 5,   /* NaN/Inf in the data, the log-likelihood or the gradient        */
+  MNL_ERR_LINESEARCH = 6,  /* no step size 2^-j, j <= max_halvings, kept l from decreasing    */
+  MNL_MAXITER = 7,         /* mnl_fit: maxiter reached without meeting a tolerance (non-fatal) */
+  MNL_ERR_TIMEOUT = 8,     /* a bounded device-side wait gave up; the result is invalid      */
+  MNL_ERR_UNSUPPORTED = 9  /* valid request this build does not implement                    */
+};
+
+/* Arithmetic of the Hessian contraction.  In every mode the Cholesky solve,
+ * the reductions across blocks and the convergence tests are float64.
+ *   MNL_FP64: every step in float64 (CUDA-core DFMA).
+ *   MNL_TF32: utilities, softmax, log-likelihood and gradient in float32 with
+ *             compensated sums; A^T A on tcgen05 tensor cores with TF32 inputs
+ *             and float32 accumulation; other Hessian blocks float32.
+ *   MNL_BF16: as MNL_TF32 with BF16 tensor-core inputs, rounded stochastically
+ *             (unbiased, reproducible); problems with fewer than 1024
+ *             observations, too few for the rounding errors to average out,
+ *             use TF32 inputs instead. */
+typedef enum { MNL_FP64 = 0, MNL_TF32 = 1, MNL_BF16 = 2 } mnl_precision;
+
+typedef struct mnl_dims {
+  int64_t N;          /* observations, >= 1                       */
+  int32_t K;          /* alternatives, >= 2                        */
+  int32_t p, d, f;    /* columns of X, Y, Z (each >= 0, p+d+f >= 1) */
+  int32_t gamma_base; /* 0 or 1, see above                         */
+} mnl_dims;
+
+typedef struct mnl_data {
+  const float *X;
+  const float *Y;
+  const float *Z;
+  const int32_t *choice;
+} mnl_data;
+
+typedef struct mnl_handle mnl_handle;
+
+/* One Newton-Raphson iteration (mnl_newton_step). */
+typedef struct mnl_step_info {
+  double loglik_old; /* l(theta) before the step                    */
+  double loglik_new; /* l(theta + t*delta) after the accepted step   */
+  double grad_inf;   /* max_j |g_j| at theta before the step         */
+  double step_inf;   /* max_j |t*delta_j|                            */
+  double theta_inf;  /* max_j |theta_j| after the step               */
+  double step_scale; /* t = 2^-halvings                              */
+  double ls_noise;   /* tolerance tau the line search allowed        */
+  int32_t halvings;  /* j of the accepted step                       */
+  int32_t ls_evals;  /* log-likelihood evaluations in the line search */
+  /* Device time per phase (CUDA events on the handle's stream):
+   * pass = utilities/softmax/l/g; hess = every Hessian kernel; chol = factor + solve; ls = line search. */
+  float t_pass_ms, t_hess_ms, t_chol_ms, t_ls_ms;
+  /* Inside the Hessian and solve phases: operand build, A^T A contraction (all class blocks),
+   * diagonal class blocks, Z blocks, assembly, Cholesky factorisation, triangular solves. */
+  float t_build_ms, t_syrk_ms, t_band_ms, t_zblk_ms, t_asm_ms, t_factor_ms, t_solve_ms;
+  int32_t launches;  /* kernels this library launched for the step   */
+  int32_t pad;
+} mnl_step_info;
+
+typedef struct mnl_fit_opts {
+  int32_t maxiter;      /* Newton iterations at most (paper default 50)              */
+  int32_t max_halvings; /* line-search halvings at most                              */
+  double gtol;          /* stop when max|g| < gtol before a step                     */
+  double ftol;          /* stop when |l_new - l_old| < ftol after a step (0: off)      */
+  double steptol;       /* stop when max|step| <= steptol * max(1, max|theta|) (0: off;
+                           < 0: 1e-10 for MNL_FP64, 1e-7 for MNL_TF32 / MNL_BF16, whose
+                           float32 gradient has a noise floor near 1e-8 relative)   */
+} mnl_fit_opts;
+
+/* Defaults: maxiter 50, max_halvings 30, gtol 1e-8, ftol 0, steptol -1 (per precision). */
+MNL_API void mnl_fit_opts_default(mnl_fit_opts *opts);
+
+enum { MNL_STOP_GTOL = 1, MNL_STOP_FTOL = 2, MNL_STOP_STEPTOL = 3, MNL_STOP_MAXITER = 4 };
+
+typedef struct mnl_fit_info {
+  int32_t iters;       /* Newton iterations taken                          */
+  int32_t ls_evals;    /* log-likelihood evaluations in line searches      */
+  int32_t stop_reason; /* MNL_STOP_* (0 when the fit ended in an error)     */
+  int32_t status;      /* same value mnl_fit returned                      */
+  double loglik;       /* l at the returned theta                          */
+  double grad_inf;     /* max|g| at the last gradient evaluation           */
+  double dloglik;      /* l change of the last step                        */
+  double step_rel;     /* max|step| / max(1, max|theta|) of the last step    */
+  double t_total_ms;   /* wall time of mnl_fit                             */
+  double t_pass_ms, t_hess_ms, t_chol_ms, t_ls_ms; /* summed device time per phase */
+} mnl_fit_info;
+
+/* Number of coefficients, (K-1)p + (K-1 or K)d + f; -1 for invalid dims. */
+MNL_API int64_t mnl_num_params(const mnl_dims *dims);
+
+/* Static text for a status code (never NULL). */
+MNL_API const char *mnl_status_string(int status);
+
+/* Device bytes mnl_create would allocate for these dims and precision (0 on error). */
+MNL_API size_t mnl_workspace_bytes(const mnl_dims *dims, int precision);
+
+/* Create a handle for one problem.
+ *   dims      sizes (copied).
+ *   data      DEVICE pointers to the caller's arrays, which must stay valid
+ *             and unchanged until mnl_destroy; or NULL, in which case the
+ *             handle allocates its own device copies, to be filled by
+ *             mnl_upload before any computation.
+ *   precision an mnl_precision value.
+ *   stream    cudaStream_t (as void*) all work is enqueued on; NULL = default.
+ *   out       receives the handle (NULL on error).
+ * Allocates every workspace up front (mnl_workspace_bytes) and, when data is
+ * given, validates it on the device: a choice outside [0, K) returns
+ * MNL_ERR_INVALID_ARG, a NaN/Inf in X, Y or Z returns MNL_ERR_NONFINITE.
+ * Synchronises the stream. */
+MNL_API int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *stream, mnl_handle **out);
+
+/* Copy HOST arrays into the handle's own device buffers (handles created with
+ * data = NULL only; otherwise MNL_ERR_INVALID_ARG), then validate them as
+ * mnl_create does.  Pinned host memory makes the copy asynchronous and fast;
+ * pageable memory works too.  Synchronises the stream. */
+MNL_API int mnl_upload(mnl_handle *h, const mnl_data *host_data);
+
+/* Log-likelihood and gradient at theta (eq. "log-lik function", eq. "loglik gradient").
+ *   theta   DEVICE [n_theta] float64.
+ *   loglik  HOST double, or NULL.  When given, the call synchronises the stream.
+ *   grad    DEVICE [n_theta] float64, or NULL; written in stream order. */
+MNL_API int mnl_loglik_grad(mnl_handle *h, const double *theta, double *loglik, double *grad);
+
+/* Hessian of l at theta (eq. "hessian block"), paper sign (negative definite).
+ *   theta DEVICE [n_theta] float64.
+ *   H     DEVICE [n_theta][n_theta] float64, column-major, both triangles
+ *         written (the matrix is symmetric); enqueued in stream order. */
+MNL_API int mnl_hessian(mnl_handle *h, const double *theta, double *H);
+
+/* One Newton-Raphson iteration with step halving (eq. "NR update", Sec. 3.1):
+ * computes l, g, H at theta, solves (-H) delta = g by Cholesky, evaluates
+ * l(theta + 2^-j delta) for j = 0, 1, ... and accepts the first step whose
+ * log-likelihood is not lower than l(theta) by more than the rounding noise
+ * of the sum (info->ls_noise).  theta is DEVICE [n_theta] float64, updated in
+ * place only when the call returns MNL_OK.  info (HOST) may be NULL.
+ * Synchronises the stream.  Errors: MNL_ERR_NOT_PD, MNL_ERR_NONFINITE,
+ * MNL_ERR_LINESEARCH, MNL_ERR_TIMEOUT, MNL_ERR_CUDA. */
+MNL_API int mnl_newton_step(mnl_handle *h, double *theta, mnl_step_info *info);
+
+/* Newton-Raphson to convergence (Sec. 3.1; stopping rules of Sec. 2.3:
+ * maxiter, ftol, gtol; plus the relative step test steptol).
+ *   opts  HOST, or NULL for mnl_fit_opts_default.
+ *   theta DEVICE [n_theta] float64: start in, estimate out.
+ *   info  HOST, may be NULL.
+ * Returns MNL_OK when a tolerance was met, MNL_MAXITER when maxiter ran out
+ * (theta holds the last iterate), or an error of mnl_newton_step. */
+MNL_API int mnl_fit(mnl_handle *h, const mnl_fit_opts *opts, double *theta, mnl_fit_info *info);
+
+/* Free the handle and every device buffer it owns (NULL is a no-op). */
+MNL_API int mnl_destroy(mnl_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MNL_H */

@@ -215,7 +215,7 @@ int oracle_neg_hessian(const oracle_problem *P, const double *theta, double *F, 
   double *prob = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1) * K);
   if (!prob) return -3;
   if (oracle_probs(P, theta, prob, NULL)) { free(prob); return -1; }
-  const int64_t RB = 32;
+  const int64_t RB = 64;
   const int64_t nblk = (n + RB - 1) / RB;
   int err = 0;
 #ifdef _OPENMP

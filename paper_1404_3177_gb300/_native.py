@@ -1,0 +1,191 @@
+"""ctypes binding of ``include/mnl.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own.  Loading fails loudly when the CUDA library has not been
+built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import _build
+
+MNL_OK = 0
+MNL_ERR_INVALID_ARG = 1
+MNL_ERR_OOM = 2
+MNL_ERR_CUDA = 3
+MNL_ERR_NOT_PD = 4
+MNL_ERR_NONFINITE = 5
+MNL_ERR_LINESEARCH = 6
+MNL_MAXITER = 7
+MNL_ERR_TIMEOUT = 8
+MNL_ERR_UNSUPPORTED = 9
+
+MNL_FP64, MNL_TF32, MNL_BF16 = 0, 1, 2
+PRECISIONS = {"fp64": MNL_FP64, "tf32": MNL_TF32, "bf16": MNL_BF16}
+
+MNL_STOP_GTOL, MNL_STOP_FTOL, MNL_STOP_STEPTOL, MNL_STOP_MAXITER = 1, 2, 3, 4
+
+# Every entry point declared in include/mnl.h.
+EXPORTS = (
+    "mnl_num_params", "mnl_status_string", "mnl_workspace_bytes", "mnl_fit_opts_default", "mnl_create",
+    "mnl_upload", "mnl_loglik_grad", "mnl_hessian", "mnl_newton_step", "mnl_fit", "mnl_destroy",
+)
+
+
+class mnl_dims(C.Structure):
+    _fields_ = [("N", C.c_int64), ("K", C.c_int32), ("p", C.c_int32), ("d", C.c_int32), ("f", C.c_int32),
+                ("gamma_base", C.c_int32)]
+
+
+class mnl_data(C.Structure):
+    _fields_ = [("X", C.c_void_p), ("Y", C.c_void_p), ("Z", C.c_void_p), ("choice", C.c_void_p)]
+
+
+class mnl_step_info(C.Structure):
+    _fields_ = [("loglik_old", C.c_double), ("loglik_new", C.c_double), ("grad_inf", C.c_double),
+                ("step_inf", C.c_double), ("theta_inf", C.c_double), ("step_scale", C.c_double),
+                ("ls_noise", C.c_double), ("halvings", C.c_int32), ("ls_evals", C.c_int32),
+                ("t_pass_ms", C.c_float), ("t_hess_ms", C.c_float), ("t_chol_ms", C.c_float),
+                ("t_ls_ms", C.c_float), ("t_build_ms", C.c_float), ("t_syrk_ms", C.c_float),
+                ("t_band_ms", C.c_float), ("t_zblk_ms", C.c_float), ("t_asm_ms", C.c_float),
+                ("t_factor_ms", C.c_float), ("t_solve_ms", C.c_float), ("launches", C.c_int32),
+                ("pad", C.c_int32)]
+
+
+class mnl_fit_opts(C.Structure):
+    _fields_ = [("maxiter", C.c_int32), ("max_halvings", C.c_int32), ("gtol", C.c_double), ("ftol", C.c_double),
+                ("steptol", C.c_double)]
+
+
+class mnl_fit_info(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("ls_evals", C.c_int32), ("stop_reason", C.c_int32), ("status", C.c_int32),
+                ("loglik", C.c_double), ("grad_inf", C.c_double), ("dloglik", C.c_double),
+                ("step_rel", C.c_double), ("t_total_ms", C.c_double), ("t_pass_ms", C.c_double),
+                ("t_hess_ms", C.c_double), ("t_chol_ms", C.c_double), ("t_ls_ms", C.c_double)]
+
+
+def struct_dict(s: C.Structure) -> dict:
+    return {name: getattr(s, name) for name, _ in s._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load() -> C.CDLL:
+    """Load libmnl.so (built by ``_build.build()``); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"the CUDA library {path} is not built; run paper_1404_3177_gb300._build.build() "
+                               "(there is no CPU fallback)")
+        lib = C.CDLL(path)
+        vp, i32, i64 = C.c_void_p, C.c_int, C.c_int64
+        lib.mnl_num_params.restype = i64
+        lib.mnl_num_params.argtypes = [C.POINTER(mnl_dims)]
+        lib.mnl_status_string.restype = C.c_char_p
+        lib.mnl_status_string.argtypes = [i32]
+        lib.mnl_workspace_bytes.restype = C.c_size_t
+        lib.mnl_workspace_bytes.argtypes = [C.POINTER(mnl_dims), i32]
+        lib.mnl_fit_opts_default.restype = None
+        lib.mnl_fit_opts_default.argtypes = [C.POINTER(mnl_fit_opts)]
+        lib.mnl_create.restype = i32
+        lib.mnl_create.argtypes = [C.POINTER(mnl_dims), C.POINTER(mnl_data), i32, vp, C.POINTER(vp)]
+        lib.mnl_upload.restype = i32
+        lib.mnl_upload.argtypes = [vp, C.POINTER(mnl_data)]
+        lib.mnl_loglik_grad.restype = i32
+        lib.mnl_loglik_grad.argtypes = [vp, vp, C.POINTER(C.c_double), vp]
+        lib.mnl_hessian.restype = i32
+        lib.mnl_hessian.argtypes = [vp, vp, vp]
+        lib.mnl_newton_step.restype = i32
+        lib.mnl_newton_step.argtypes = [vp, vp, C.POINTER(mnl_step_info)]
+        lib.mnl_fit.restype = i32
+        lib.mnl_fit.argtypes = [vp, C.POINTER(mnl_fit_opts), vp, C.POINTER(mnl_fit_info)]
+        lib.mnl_destroy.restype = i32
+        lib.mnl_destroy.argtypes = [vp]
+        _lib = lib
+        return lib
+
+
+class MnlError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {mnl_status_string(status)} (status {status})")
+
+
+def _check(rc: int, where: str) -> int:
+    if rc != MNL_OK and rc != MNL_MAXITER:
+        raise MnlError(rc, where)
+    return rc
+
+
+# ---- same-name wrappers --------------------------------------------------
+
+def mnl_status_string(status: int) -> str:
+    return load().mnl_status_string(status).decode()
+
+
+def mnl_num_params(dims: mnl_dims) -> int:
+    return int(load().mnl_num_params(C.byref(dims)))
+
+
+def mnl_workspace_bytes(dims: mnl_dims, precision: int) -> int:
+    return int(load().mnl_workspace_bytes(C.byref(dims), precision))
+
+
+def mnl_fit_opts_default() -> mnl_fit_opts:
+    o = mnl_fit_opts()
+    load().mnl_fit_opts_default(C.byref(o))
+    return o
+
+
+def mnl_create(dims: mnl_dims, data: mnl_data | None, precision: int, stream: int | None) -> int:
+    h = C.c_void_p()
+    rc = load().mnl_create(C.byref(dims), C.byref(data) if data is not None else None, precision,
+                           C.c_void_p(stream or 0), C.byref(h))
+    _check(rc, "mnl_create")
+    return h.value
+
+
+def mnl_upload(handle: int, host_data: mnl_data) -> None:
+    _check(load().mnl_upload(C.c_void_p(handle), C.byref(host_data)), "mnl_upload")
+
+
+def mnl_loglik_grad(handle: int, theta_ptr: int, want_loglik: bool, grad_ptr: int | None) -> float | None:
+    l = C.c_double()
+    rc = load().mnl_loglik_grad(C.c_void_p(handle), C.c_void_p(theta_ptr), C.byref(l) if want_loglik else None,
+                                C.c_void_p(grad_ptr) if grad_ptr else None)
+    _check(rc, "mnl_loglik_grad")
+    return l.value if want_loglik else None
+
+
+def mnl_hessian(handle: int, theta_ptr: int, H_ptr: int) -> None:
+    _check(load().mnl_hessian(C.c_void_p(handle), C.c_void_p(theta_ptr), C.c_void_p(H_ptr)), "mnl_hessian")
+
+
+def mnl_newton_step(handle: int, theta_ptr: int) -> mnl_step_info:
+    info = mnl_step_info()
+    _check(load().mnl_newton_step(C.c_void_p(handle), C.c_void_p(theta_ptr), C.byref(info)), "mnl_newton_step")
+    return info
+
+
+def mnl_fit(handle: int, opts: mnl_fit_opts | None, theta_ptr: int) -> mnl_fit_info:
+    info = mnl_fit_info()
+    rc = load().mnl_fit(C.c_void_p(handle), C.byref(opts) if opts is not None else None, C.c_void_p(theta_ptr),
+                        C.byref(info))
+    _check(rc, "mnl_fit")
+    return info
+
+
+def mnl_destroy(handle: int) -> None:
+    _check(load().mnl_destroy(C.c_void_p(handle)), "mnl_destroy")

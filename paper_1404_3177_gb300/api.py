@@ -1,0 +1,115 @@
+"""torch-facing wrapper around the C ABI (marshalling only; no arithmetic here)."""
+from __future__ import annotations
+
+import torch
+
+from . import _native as nat
+
+
+def _ptr(t):
+    return t.data_ptr() if t is not None and t.numel() > 0 else None
+
+
+class MNL:
+    """One multinomial-logit problem resident on the current CUDA device.
+
+    X [N][p], Y [N][K][d], Z [N][K][f] (float32) and choice [N] (int32) are CUDA
+    tensors that must outlive this object; pass None for an empty block.  K is
+    taken from Y or Z, or must be given.  ``precision`` is "fp64", "tf32" or
+    "bf16" (the arithmetic of the Hessian contraction, see include/mnl.h).
+    """
+
+    def __init__(self, X=None, Y=None, Z=None, choice=None, *, K=None, precision="bf16", stream=None,
+                 host_owned_dims=None):
+        self.precision = nat.PRECISIONS[precision]
+        self._stream = (stream or torch.cuda.current_stream()).cuda_stream
+        if host_owned_dims is not None:
+            self.dims = host_owned_dims
+            self._keep = ()
+            self.h = nat.mnl_create(self.dims, None, self.precision, self._stream)
+            return
+        if choice is None:
+            raise ValueError("choice is required")
+        N = choice.shape[0]
+        if Y is not None:
+            K = Y.shape[1]
+        elif Z is not None:
+            K = Z.shape[1]
+        if K is None:
+            raise ValueError("K must be given when neither Y nor Z is present")
+        p = X.shape[1] if X is not None else 0
+        d = Y.shape[2] if Y is not None else 0
+        f = Z.shape[2] if Z is not None else 0
+        for name, t, dt in (("X", X, torch.float32), ("Y", Y, torch.float32), ("Z", Z, torch.float32),
+                            ("choice", choice, torch.int32)):
+            if t is not None and (not t.is_cuda or t.dtype != dt or not t.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous CUDA tensor of dtype {dt}")
+        self._keep = (X, Y, Z, choice)
+        self.dims = nat.mnl_dims(N, K, p, d, f, 0)
+        data = nat.mnl_data(_ptr(X), _ptr(Y), _ptr(Z), _ptr(choice))
+        self.h = nat.mnl_create(self.dims, data, self.precision, self._stream)
+
+    @classmethod
+    def with_host_upload(cls, N, K, p, d, f, *, precision="bf16", stream=None):
+        """A handle that owns its device copies of the data; fill it with ``upload``."""
+        return cls(precision=precision, stream=stream, host_owned_dims=nat.mnl_dims(N, K, p, d, f, 0))
+
+    def upload(self, X=None, Y=None, Z=None, choice=None):
+        """Copy host tensors (pinned for speed) into the handle's own device buffers."""
+        data = nat.mnl_data(_ptr(X), _ptr(Y), _ptr(Z), _ptr(choice))
+        self._host_keep = (X, Y, Z, choice)
+        nat.mnl_upload(self.h, data)
+
+    @property
+    def n_theta(self) -> int:
+        return nat.mnl_num_params(self.dims)
+
+    def _theta(self, theta):
+        if theta is None:
+            return torch.zeros(self.n_theta, dtype=torch.float64, device="cuda")
+        if not theta.is_cuda or theta.dtype != torch.float64 or theta.shape != (self.n_theta,):
+            raise ValueError("theta must be a float64 CUDA tensor of shape (n_theta,)")
+        return theta.contiguous()
+
+    def loglik_grad(self, theta=None, grad=True):
+        th = self._theta(theta)
+        g = torch.empty(self.n_theta, dtype=torch.float64, device=th.device) if grad else None
+        l = nat.mnl_loglik_grad(self.h, th.data_ptr(), True, _ptr(g))
+        return l, g
+
+    def hessian(self, theta=None):
+        """Hessian (paper sign, negative definite), float64 [n][n] (symmetric)."""
+        th = self._theta(theta)
+        H = torch.empty(self.n_theta, self.n_theta, dtype=torch.float64, device=th.device)
+        nat.mnl_hessian(self.h, th.data_ptr(), H.data_ptr())
+        return H
+
+    def newton_step(self, theta):
+        """One Newton-Raphson iteration; theta (float64 CUDA) is updated in place."""
+        info = nat.mnl_newton_step(self.h, self._theta(theta).data_ptr())
+        return nat.struct_dict(info)
+
+    def fit(self, theta0=None, **opts):
+        o = nat.mnl_fit_opts_default()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        th = self._theta(theta0).clone() if theta0 is not None else self._theta(None)
+        info = nat.mnl_fit(self.h, o, th.data_ptr())
+        return th, nat.struct_dict(info)
+
+    def close(self):
+        if getattr(self, "h", None):
+            nat.mnl_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

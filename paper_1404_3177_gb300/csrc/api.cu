@@ -1,0 +1,630 @@
+// C ABI of libmnl: handle lifetime, workspaces and the Newton-Raphson driver
+// (Sec. 3.1 eq. "NR update" with step halving; stopping rules of Sec. 2.3).
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <new>
+#include <cstring>
+#include <vector>
+
+#include "mnl_internal.cuh"
+
+using namespace mnl;
+
+struct mnl_handle {
+  mnl_dims dims;
+  Shape S;
+  int prec;
+  OpType op;
+  bool fp64;
+  cudaStream_t st;
+  int dev, nsm;
+  // data
+  const float *X, *Y, *Z;
+  const int32_t *choice;
+  bool owns_data, data_ready;
+  void *owned[4];
+  // pass
+  PassPlan pfull, pll;
+  double *part_full, *part_ll;
+  void *P, *zbar;
+  double *scal;    // device scalars
+  double *grad, *delta, *tscale;
+  int *status, *err;
+  // Hessian
+  int64_t ldn, mc_pad;
+  int nt1d;
+  void *At, *Ad;
+  size_t op_bytes;
+  TileLists tl;
+  std::vector<int2> h_main, h_band;
+  void *main_part, *band_part, *z_part;
+  int main_split, band_split, z_split;
+  TcPlan tc_main, tc_band;
+  double *F;
+  // host mirrors (pinned)
+  double *h_scal;
+  int *h_flags;
+  cudaEvent_t ev[12];
+  int launches;
+  std::vector<void *> allocs;
+};
+
+namespace {
+
+enum Scal { kL = 0, kLabs = 1, kGinf = 2, kLt = 4, kLtabs = 5, kStepInf = 6, kThetaInf = 7, kNscal = 16 };
+
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+int cuda_fail(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) return MNL_ERR_OOM;
+  if (e == cudaErrorNotSupported) return MNL_ERR_UNSUPPORTED;
+  return MNL_ERR_CUDA;
+}
+
+int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// Below this many observations MNL_BF16 forms the Hessian operands in TF32.
+constexpr int64_t kBf16MinRows = 1024;
+
+bool dims_ok(const mnl_dims *d) {
+  return d && d->N >= 1 && d->K >= 2 && d->p >= 0 && d->d >= 0 && d->f >= 0 && (d->p + d->d + d->f) >= 1 &&
+         (d->gamma_base == 0 || d->gamma_base == 1);
+}
+
+struct Sizes {
+  size_t P, zbar, part_full, part_ll, ops, main_part, band_part, z_part, F, owned;
+  size_t total() const { return P + zbar + part_full + part_ll + 2 * ops + main_part + band_part + z_part + F + owned; }
+};
+
+void band_tiles(const Shape &S, int nt1d, std::vector<int2> &band, std::vector<int> &band_of) {
+  band.clear();
+  band_of.assign((size_t)nt1d * nt1d, -1);
+  if (S.q == 0 || nt1d == 0) return;  // no class coefficients, no class blocks
+  for (int k = 1; k < S.K; ++k) {
+    const int64_t c0 = (int64_t)(k - 1) * S.q, c1 = (int64_t)k * S.q - 1;
+    const int lo = (int)(c0 / kTile), hi = (int)(c1 / kTile);
+    for (int ti = lo; ti <= hi; ++ti)
+      for (int tj = lo; tj <= ti; ++tj)
+        if (band_of[(size_t)ti * nt1d + tj] < 0) {
+          band_of[(size_t)ti * nt1d + tj] = (int)band.size();
+          band.push_back(make_int2(ti, tj));
+        }
+  }
+}
+
+int simt_split(int ntiles, int64_t nchunks, int nsm) {
+  int s = (int)((2 * nsm + ntiles - 1) / ntiles);
+  s = std::max(1, std::min<int>(s, (int)std::max<int64_t>(1, nchunks / 64)));
+  return std::min(s, 64);
+}
+
+Sizes plan_sizes(const mnl_dims &d, int prec_in, bool owned, int nsm, int *main_split, int *band_split, int *z_split,
+                 PassPlan *pf, PassPlan *pl, int64_t *ldn, int64_t *mc_pad, int *nt1d, int *nband) {
+  const Shape S = make_shape(d);
+  const int prec = (prec_in == MNL_BF16 && d.N < kBf16MinRows) ? MNL_TF32 : prec_in;
+  const bool fp64 = prec == MNL_FP64;
+  const size_t tsz = fp64 ? 8 : 4;
+  const size_t esz = prec == MNL_FP64 ? 8 : prec == MNL_TF32 ? 4 : 2;
+  Sizes z{};
+  *pf = plan_pass(S, fp64, true, nsm);
+  *pl = plan_pass(S, fp64, false, nsm);
+  z.P = (size_t)S.N * S.K * tsz;
+  z.zbar = (size_t)S.N * S.f * tsz;
+  z.part_full = (size_t)pf->grid * (2 + S.nout) * 8;
+  z.part_ll = (size_t)pl->grid * 2 * 8;
+  *ldn = round_up(S.N, 64);
+  *mc_pad = round_up(S.mc, kTile);
+  *nt1d = (int)(*mc_pad / kTile);
+  z.ops = (size_t)(*mc_pad) * (*ldn) * esz;
+  const int nmain = (*nt1d) * (*nt1d + 1) / 2;
+  std::vector<int2> band;
+  std::vector<int> band_of;
+  band_tiles(S, *nt1d, band, band_of);
+  *nband = (int)band.size();
+  const size_t csz = fp64 ? 8 : 4;
+  if (fp64) {
+    *main_split = simt_split(nmain, *ldn / 16, nsm);
+    *band_split = simt_split(*nband, *ldn / 16, nsm);
+  } else {
+    // same rule as make_tc_plan (balanced persistent units, >= 8 K-blocks per split)
+    const int bk = prec == MNL_TF32 ? kBkTf32 : kBkBf16;
+    const int kb = (int)(*ldn / bk);
+    auto pick = [&](int ntiles) {
+      int best = 1;
+      double be = -1;
+      const int mx = std::max(1, std::min(16, kb / 8));
+      for (int s = 1; s <= mx; ++s) {
+        const int units = ntiles * s, g = std::min(units, nsm), waves = (units + g - 1) / g;
+        const double eff = (double)units / ((double)g * waves) * (g / (double)nsm);
+        if (eff > be + 0.02) { be = eff; best = s; }
+      }
+      return best;
+    };
+    *main_split = nmain ? pick(nmain) : 1;
+    *band_split = *nband ? pick(*nband) : 1;
+  }
+  z.main_part = (size_t)(*main_split) * nmain * kTile * kTile * csz;
+  z.band_part = (size_t)(*band_split) * (*nband) * kTile * kTile * csz;
+  *z_split = (int)std::max<int64_t>(1, std::min<int64_t>((2 * nsm + S.K - 1) / S.K, S.N / 512));
+  const size_t nz = (size_t)S.q * S.f + (size_t)S.f * S.f;
+  z.z_part = S.f ? (size_t)(*z_split) * S.K * nz * tsz : 0;
+  z.F = (size_t)S.n * S.n * 8;
+  z.owned = owned ? ((size_t)S.N * S.p + (size_t)S.N * S.K * (S.d + S.f)) * 4 + (size_t)S.N * 4 : 0;
+  return z;
+}
+
+template <typename T>
+int dalloc(mnl_handle *h, T **p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return MNL_OK;
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) { cudaGetLastError(); return e == cudaErrorMemoryAllocation ? MNL_ERR_OOM : MNL_ERR_CUDA; }
+  h->allocs.push_back(q);
+  *p = reinterpret_cast<T *>(q);
+  return MNL_OK;
+}
+
+void free_all(mnl_handle *h) {
+  for (void *p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  if (h->h_scal) cudaFreeHost(h->h_scal);
+  if (h->h_flags) cudaFreeHost(h->h_flags);
+  for (auto &e : h->ev) if (e) cudaEventDestroy(e);
+  h->h_scal = nullptr;
+  h->h_flags = nullptr;
+}
+
+int validate(mnl_handle *h) {
+  CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
+  CK(launch_validate(h->S, h->X, h->Y, h->Z, h->choice, h->status, h->st));
+  CK(cudaMemcpyAsync(h->h_flags, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (h->h_flags[0] & 1) return MNL_ERR_INVALID_ARG;
+  if (h->h_flags[0] & 2) return MNL_ERR_NONFINITE;
+  h->data_ready = true;
+  return MNL_OK;
+}
+
+// l (and g, P, zbar when full) at theta (+ t delta when delta given) -> scal[base], scal[base+1], grad.
+int run_pass(mnl_handle *h, const double *theta, bool full, const double *delta, int base) {
+  PassIO io{};
+  io.X = h->X; io.Y = h->Y; io.Z = h->Z; io.choice = h->choice;
+  io.theta = theta; io.delta = delta; io.tscale = h->tscale;
+  io.P = h->P; io.zbar = h->zbar;
+  const PassPlan &pl = full ? h->pfull : h->pll;
+  io.partials = full ? h->part_full : h->part_ll;
+  CK(launch_pass(h->S, pl, h->fp64, full, io, h->st));
+  CK(launch_pass_reduce(h->S, pl.grid, full, io.partials, h->scal + base, full ? h->grad : nullptr, h->st));
+  h->launches += 2;
+  return MNL_OK;
+}
+
+// Optional event between kernels (per-kernel timing of a step).
+int mark(mnl_handle *h, cudaEvent_t *ev) {
+  if (ev) CK(cudaEventRecord(*ev, h->st));
+  return MNL_OK;
+}
+
+// F = -H from P, zbar (the last full pass).  ev: 4 events recorded after the
+// operand build, the A^T A contraction, the diagonal class blocks and the Z blocks.
+int run_hessian(mnl_handle *h, cudaEvent_t *ev = nullptr) {
+  const Shape &S = h->S;
+  const int nmain = (int)h->h_main.size();
+  int rc;
+  if (S.mc > 0) {
+    CK(launch_build_operands(S, h->op, h->X, h->Y, h->P, h->At, h->Ad, h->ldn, h->st));
+    if ((rc = mark(h, ev ? ev + 0 : nullptr))) return rc;
+    if (h->fp64) {
+      CK(launch_syrk_f64(reinterpret_cast<const double *>(h->At), h->ldn, S.N, h->tl.main, nmain, h->main_split,
+                         reinterpret_cast<double *>(h->main_part), h->st));
+      if ((rc = mark(h, ev ? ev + 1 : nullptr))) return rc;
+      CK(launch_syrk_f64(reinterpret_cast<const double *>(h->Ad), h->ldn, S.N, h->tl.band, h->tl.nband,
+                         h->band_split, reinterpret_cast<double *>(h->band_part), h->st));
+    } else {
+      CK(launch_syrk_tc(h->op, h->tc_main, h->tl.main, nmain, reinterpret_cast<float *>(h->main_part), h->err, h->st));
+      if ((rc = mark(h, ev ? ev + 1 : nullptr))) return rc;
+      CK(launch_syrk_tc(h->op, h->tc_band, h->tl.band, h->tl.nband, reinterpret_cast<float *>(h->band_part), h->err,
+                        h->st));
+    }
+    h->launches += 3;
+    if ((rc = mark(h, ev ? ev + 2 : nullptr))) return rc;
+  } else {
+    for (int i = 0; i < 3; ++i)
+      if ((rc = mark(h, ev ? ev + i : nullptr))) return rc;
+  }
+  if (S.f > 0) {
+    CK(launch_zblocks(S, h->fp64, h->X, h->Y, h->Z, h->P, h->zbar, h->z_split, h->z_part, h->st));
+    h->launches += 1;
+  }
+  if ((rc = mark(h, ev ? ev + 3 : nullptr))) return rc;
+  AssembleIO io{};
+  io.main_part = h->main_part; io.main_split = h->main_split;
+  io.band_part = h->band_part; io.band_split = h->band_split;
+  io.z_part = h->z_part; io.z_split = h->z_split;
+  io.tl = &h->tl;
+  io.fp64 = h->fp64;
+  CK(launch_assemble(S, io, nmain, h->F, h->st));
+  h->launches += 1;
+  return MNL_OK;
+}
+
+double noise_tol(const mnl_handle *h, double labs) {
+  const double u = h->fp64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
+  return 8.0 * u * labs;
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) { cudaGetLastError(); return 0.f; }
+  return ms;
+}
+
+// One Newton iteration.  With gtol > 0 the gradient is checked before the
+// Hessian is formed; *converged is set and theta left unchanged if it is met.
+int step_impl(mnl_handle *h, double *theta, mnl_step_info *info, double gtol, bool *converged, int max_halvings) {
+  const int64_t n = h->S.n;
+  mnl_step_info loc{};
+  if (converged) *converged = false;
+  h->launches = 0;
+  CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->st));
+  CK(cudaMemsetAsync(h->scal, 0, kNscal * sizeof(double), h->st));
+  CK(cudaEventRecord(h->ev[0], h->st));
+  int rc = run_pass(h, theta, true, nullptr, kL);
+  if (rc) return rc;
+  CK(launch_vec_absmax(n, h->grad, h->scal + kGinf, h->st));
+  h->launches += 1;
+  CK(cudaEventRecord(h->ev[1], h->st));
+  if (gtol > 0) {
+    CK(cudaMemcpyAsync(h->h_scal, h->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (!std::isfinite(h->h_scal[kL]) || !std::isfinite(h->h_scal[kGinf])) return MNL_ERR_NONFINITE;
+    if (h->h_scal[kGinf] < gtol) {
+      loc.loglik_old = loc.loglik_new = h->h_scal[kL];
+      loc.grad_inf = h->h_scal[kGinf];
+      loc.t_pass_ms = elapsed(h->ev[0], h->ev[1]);
+      if (info) *info = loc;
+      if (converged) *converged = true;
+      return MNL_OK;
+    }
+  }
+  rc = run_hessian(h, h->ev + 5);
+  if (rc) return rc;
+  CK(cudaEventRecord(h->ev[2], h->st));
+  CK(launch_cholesky(n, h->F, h->status, h->st));
+  h->launches += (int)(3 * ((n + 63) / 64) - 2);
+  CK(cudaEventRecord(h->ev[9], h->st));
+  CK(launch_cholesky_solve(n, h->F, h->grad, h->delta, h->status, h->st));
+  h->launches += 1;
+  CK(cudaEventRecord(h->ev[3], h->st));
+  CK(cudaMemcpyAsync(h->h_scal, h->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(h->h_flags, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(h->h_flags + 1, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (h->h_flags[1]) return MNL_ERR_TIMEOUT;
+  const double l0 = h->h_scal[kL], labs = h->h_scal[kLabs], ginf = h->h_scal[kGinf];
+  if (!std::isfinite(l0) || !std::isfinite(ginf)) return MNL_ERR_NONFINITE;
+  if (h->h_flags[0] & 4) return MNL_ERR_NOT_PD;
+  const double tau = noise_tol(h, labs);
+  // Step halving (Sec. 3.1).
+  double t = 1.0, lt = 0.0;
+  int j = 0, evals = 0;
+  bool accepted = false;
+  for (j = 0; j <= max_halvings; ++j) {
+    h->h_scal[8] = t;
+    CK(cudaMemcpyAsync(h->tscale, h->h_scal + 8, sizeof(double), cudaMemcpyHostToDevice, h->st));
+    rc = run_pass(h, theta, false, h->delta, kLt);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(h->h_scal + kLt, h->scal + kLt, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    ++evals;
+    lt = h->h_scal[kLt];
+    if (std::isfinite(lt) && lt >= l0 - tau) { accepted = true; break; }
+    t *= 0.5;
+  }
+  CK(cudaEventRecord(h->ev[4], h->st));
+  if (!accepted) return MNL_ERR_LINESEARCH;
+  CK(launch_axpy_theta(n, theta, h->delta, h->tscale, h->scal + kStepInf, h->st));
+  h->launches += 1;
+  CK(cudaMemcpyAsync(h->h_scal + kStepInf, h->scal + kStepInf, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  loc.loglik_old = l0;
+  loc.loglik_new = lt;
+  loc.grad_inf = ginf;
+  loc.step_inf = h->h_scal[kStepInf];
+  loc.theta_inf = h->h_scal[kThetaInf];
+  loc.step_scale = t;
+  loc.ls_noise = tau;
+  loc.halvings = j;
+  loc.ls_evals = evals;
+  loc.t_pass_ms = elapsed(h->ev[0], h->ev[1]);
+  loc.t_hess_ms = elapsed(h->ev[1], h->ev[2]);
+  loc.t_chol_ms = elapsed(h->ev[2], h->ev[3]);
+  loc.t_ls_ms = elapsed(h->ev[3], h->ev[4]);
+  loc.t_build_ms = elapsed(h->ev[1], h->ev[5]);
+  loc.t_syrk_ms = elapsed(h->ev[5], h->ev[6]);
+  loc.t_band_ms = elapsed(h->ev[6], h->ev[7]);
+  loc.t_zblk_ms = elapsed(h->ev[7], h->ev[8]);
+  loc.t_asm_ms = elapsed(h->ev[8], h->ev[2]);
+  loc.t_factor_ms = elapsed(h->ev[2], h->ev[9]);
+  loc.t_solve_ms = elapsed(h->ev[9], h->ev[3]);
+  loc.launches = h->launches;
+  if (info) *info = loc;
+  return MNL_OK;
+}
+
+int check_handle(const mnl_handle *h) {
+  if (!h) return MNL_ERR_INVALID_ARG;
+  if (!h->data_ready) return MNL_ERR_INVALID_ARG;
+  return MNL_OK;
+}
+
+int set_device(const mnl_handle *h) {
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) { cudaGetLastError(); return MNL_ERR_CUDA; }
+  if (cur != h->dev && cudaSetDevice(h->dev) != cudaSuccess) { cudaGetLastError(); return MNL_ERR_CUDA; }
+  return MNL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t mnl_num_params(const mnl_dims *d) {
+  if (!dims_ok(d)) return -1;
+  return (int64_t)(d->K - 1) * d->p + (int64_t)(d->gamma_base ? d->K : d->K - 1) * d->d + d->f;
+}
+
+const char *mnl_status_string(int s) {
+  switch (s) {
+    case MNL_OK: return "ok";
+    case MNL_ERR_INVALID_ARG: return "invalid argument";
+    case MNL_ERR_OOM: return "device allocation failed";
+    case MNL_ERR_CUDA: return "CUDA error";
+    case MNL_ERR_NOT_PD: return "negative Hessian not positive definite (singular design)";
+    case MNL_ERR_NONFINITE: return "non-finite value in data, log-likelihood or gradient";
+    case MNL_ERR_LINESEARCH: return "line search found no non-decreasing step";
+    case MNL_MAXITER: return "maximum number of iterations reached";
+    case MNL_ERR_TIMEOUT: return "a bounded device wait timed out";
+    case MNL_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+void mnl_fit_opts_default(mnl_fit_opts *o) {
+  if (!o) return;
+  o->maxiter = 50;
+  o->max_halvings = 30;
+  o->gtol = 1e-8;
+  o->ftol = 0.0;
+  o->steptol = -1.0;
+}
+
+size_t mnl_workspace_bytes(const mnl_dims *d, int precision) {
+  if (!dims_ok(d) || precision < 0 || precision > 2) return 0;
+  int nsm = 148, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  else cudaGetLastError();
+  int ms, bs, zs, nt1d, nband;
+  PassPlan pf, pl;
+  int64_t ldn, mcp;
+  Sizes z = plan_sizes(*d, precision, false, nsm, &ms, &bs, &zs, &pf, &pl, &ldn, &mcp, &nt1d, &nband);
+  return z.total();
+}
+
+int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *stream, mnl_handle **out) {
+  if (!out) return MNL_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!dims_ok(dims) || precision < 0 || precision > 2) return MNL_ERR_INVALID_ARG;
+  if (dims->gamma_base != 0) return MNL_ERR_UNSUPPORTED;
+  if (data) {
+    if (!data->choice || (dims->p > 0 && !data->X) || (dims->d > 0 && !data->Y) || (dims->f > 0 && !data->Z))
+      return MNL_ERR_INVALID_ARG;
+  }
+  mnl_handle *h = new (std::nothrow) mnl_handle();
+  if (!h) return MNL_ERR_OOM;
+  h->dims = *dims;
+  h->S = make_shape(*dims);
+  h->prec = precision;
+  h->op = precision == MNL_FP64 ? OpType::F64 : precision == MNL_TF32 ? OpType::TF32 : OpType::BF16;
+  // Too few observations for unbiased BF16 rounding to average out: TF32 operands.
+  if (h->op == OpType::BF16 && dims->N < kBf16MinRows) h->op = OpType::TF32;
+  h->fp64 = precision == MNL_FP64;
+  h->st = reinterpret_cast<cudaStream_t>(stream);
+  int rc = MNL_OK;
+  auto fail = [&](int code) {
+    free_all(h);
+    delete h;
+    return code;
+  };
+  if (cudaGetDevice(&h->dev) != cudaSuccess) { cudaGetLastError(); return fail(MNL_ERR_CUDA); }
+  cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev);
+  int nband = 0;
+  Sizes z = plan_sizes(*dims, precision, data == nullptr, h->nsm, &h->main_split, &h->band_split, &h->z_split,
+                       &h->pfull, &h->pll, &h->ldn, &h->mc_pad, &h->nt1d, &nband);
+  if (!h->pfull.ok || !h->pll.ok) return fail(MNL_ERR_UNSUPPORTED);
+  if (h->S.f > 0 && (size_t)h->S.q * h->S.f + (size_t)h->S.f * h->S.f > 4096) return fail(MNL_ERR_UNSUPPORTED);
+  for (auto &e : h->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return fail(MNL_ERR_CUDA); }
+  if (cudaMallocHost(&h->h_scal, 32 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&h->h_flags, 4 * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MNL_ERR_OOM);
+  }
+  const Shape &S = h->S;
+  const size_t tsz = h->fp64 ? 8 : 4;
+  if ((rc = dalloc(h, &h->P, z.P)) || (rc = dalloc(h, &h->zbar, z.zbar)) ||
+      (rc = dalloc(h, &h->part_full, z.part_full)) || (rc = dalloc(h, &h->part_ll, z.part_ll)) ||
+      (rc = dalloc(h, &h->scal, kNscal * sizeof(double))) || (rc = dalloc(h, &h->grad, S.n * 8)) ||
+      (rc = dalloc(h, &h->delta, S.n * 8)) || (rc = dalloc(h, &h->tscale, 8)) ||
+      (rc = dalloc(h, &h->status, 16)) || (rc = dalloc(h, &h->err, 16)) || (rc = dalloc(h, &h->At, z.ops)) ||
+      (rc = dalloc(h, &h->Ad, z.ops)) || (rc = dalloc(h, &h->main_part, z.main_part)) ||
+      (rc = dalloc(h, &h->band_part, z.band_part)) || (rc = dalloc(h, &h->z_part, z.z_part)) ||
+      (rc = dalloc(h, &h->F, z.F)))
+    return fail(rc);
+  (void)tsz;
+  h->op_bytes = z.ops;
+  if (z.ops) {
+    if (cudaMemsetAsync(h->At, 0, z.ops, h->st) != cudaSuccess || cudaMemsetAsync(h->Ad, 0, z.ops, h->st) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MNL_ERR_CUDA);
+    }
+  }
+  // tile lists
+  for (int ti = 0; ti < h->nt1d; ++ti)
+    for (int tj = 0; tj <= ti; ++tj) h->h_main.push_back(make_int2(ti, tj));
+  std::vector<int> band_of;
+  band_tiles(S, h->nt1d, h->h_band, band_of);
+  h->tl.nmain = (int)h->h_main.size();
+  h->tl.nband = (int)h->h_band.size();
+  if ((rc = dalloc(h, &h->tl.main, h->h_main.size() * sizeof(int2))) ||
+      (rc = dalloc(h, &h->tl.band, h->h_band.size() * sizeof(int2))) ||
+      (rc = dalloc(h, &h->tl.band_of, band_of.size() * sizeof(int))))
+    return fail(rc);
+  if ((!h->h_main.empty() && cudaMemcpy(h->tl.main, h->h_main.data(), h->h_main.size() * sizeof(int2),
+                                        cudaMemcpyHostToDevice) != cudaSuccess) ||
+      (!h->h_band.empty() && cudaMemcpy(h->tl.band, h->h_band.data(), h->h_band.size() * sizeof(int2),
+                                        cudaMemcpyHostToDevice) != cudaSuccess) ||
+      (!band_of.empty() &&
+       cudaMemcpy(h->tl.band_of, band_of.data(), band_of.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)) {
+    cudaGetLastError();
+    return fail(MNL_ERR_CUDA);
+  }
+  if (!h->fp64 && S.mc > 0) {
+    cudaError_t e = make_tc_plan(h->op, h->At, h->mc_pad, h->ldn, S.N, h->tl.nmain, h->nsm, &h->tc_main);
+    if (e == cudaSuccess) e = make_tc_plan(h->op, h->Ad, h->mc_pad, h->ldn, S.N, h->tl.nband, h->nsm, &h->tc_band);
+    if (e != cudaSuccess) return fail(cuda_fail(e));
+    if (h->tc_main.nsplit != h->main_split || h->tc_band.nsplit != h->band_split) return fail(MNL_ERR_CUDA);
+  }
+  // data
+  if (data) {
+    h->X = data->X; h->Y = data->Y; h->Z = data->Z; h->choice = data->choice;
+    h->owns_data = false;
+    if ((rc = validate(h))) return fail(rc);
+  } else {
+    h->owns_data = true;
+    float *X = nullptr, *Y = nullptr, *Z = nullptr;
+    int32_t *c = nullptr;
+    if ((rc = dalloc(h, &X, (size_t)S.N * S.p * 4)) || (rc = dalloc(h, &Y, (size_t)S.N * S.K * S.d * 4)) ||
+        (rc = dalloc(h, &Z, (size_t)S.N * S.K * S.f * 4)) || (rc = dalloc(h, &c, (size_t)S.N * 4)))
+      return fail(rc);
+    h->X = X; h->Y = Y; h->Z = Z; h->choice = c;
+    h->data_ready = false;
+  }
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) { cudaGetLastError(); return fail(MNL_ERR_CUDA); }
+  *out = h;
+  return MNL_OK;
+}
+
+int mnl_upload(mnl_handle *h, const mnl_data *hd) {
+  if (!h || !hd || !h->owns_data) return MNL_ERR_INVALID_ARG;
+  const Shape &S = h->S;
+  if (!hd->choice || (S.p > 0 && !hd->X) || (S.d > 0 && !hd->Y) || (S.f > 0 && !hd->Z)) return MNL_ERR_INVALID_ARG;
+  int rc = set_device(h);
+  if (rc) return rc;
+  if (S.p) CK(cudaMemcpyAsync(const_cast<float *>(h->X), hd->X, (size_t)S.N * S.p * 4, cudaMemcpyHostToDevice, h->st));
+  if (S.d)
+    CK(cudaMemcpyAsync(const_cast<float *>(h->Y), hd->Y, (size_t)S.N * S.K * S.d * 4, cudaMemcpyHostToDevice, h->st));
+  if (S.f)
+    CK(cudaMemcpyAsync(const_cast<float *>(h->Z), hd->Z, (size_t)S.N * S.K * S.f * 4, cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(const_cast<int32_t *>(h->choice), hd->choice, (size_t)S.N * 4, cudaMemcpyHostToDevice, h->st));
+  return validate(h);
+}
+
+int mnl_loglik_grad(mnl_handle *h, const double *theta, double *loglik, double *grad) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!theta) return MNL_ERR_INVALID_ARG;
+  if ((rc = set_device(h))) return rc;
+  rc = run_pass(h, theta, grad != nullptr, nullptr, kL);
+  if (rc) return rc;
+  if (grad) CK(cudaMemcpyAsync(grad, h->grad, h->S.n * 8, cudaMemcpyDeviceToDevice, h->st));
+  if (loglik) {
+    CK(cudaMemcpyAsync(h->h_scal, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    *loglik = h->h_scal[0];
+  }
+  return MNL_OK;
+}
+
+int mnl_hessian(mnl_handle *h, const double *theta, double *H) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!theta || !H) return MNL_ERR_INVALID_ARG;
+  if ((rc = set_device(h))) return rc;
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->st));
+  if ((rc = run_pass(h, theta, true, nullptr, kL))) return rc;
+  if ((rc = run_hessian(h))) return rc;
+  CK(launch_export_hessian(h->S.n, h->F, H, h->st));
+  return MNL_OK;
+}
+
+int mnl_newton_step(mnl_handle *h, double *theta, mnl_step_info *info) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!theta) return MNL_ERR_INVALID_ARG;
+  if ((rc = set_device(h))) return rc;
+  return step_impl(h, theta, info, 0.0, nullptr, 30);
+}
+
+int mnl_fit(mnl_handle *h, const mnl_fit_opts *opts, double *theta, mnl_fit_info *info) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!theta) return MNL_ERR_INVALID_ARG;
+  if ((rc = set_device(h))) return rc;
+  mnl_fit_opts o;
+  mnl_fit_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.maxiter < 0 || o.max_halvings < 0) return MNL_ERR_INVALID_ARG;
+  const double steptol = o.steptol >= 0 ? o.steptol : (h->fp64 ? 1e-10 : 1e-7);
+  mnl_fit_info fi{};
+  const auto t0 = std::chrono::steady_clock::now();
+  rc = MNL_MAXITER;
+  for (int it = 0; it < o.maxiter; ++it) {
+    mnl_step_info si{};
+    bool conv = false;
+    int s = step_impl(h, theta, &si, o.gtol, &conv, o.max_halvings);
+    fi.t_pass_ms += si.t_pass_ms;
+    fi.t_hess_ms += si.t_hess_ms;
+    fi.t_chol_ms += si.t_chol_ms;
+    fi.t_ls_ms += si.t_ls_ms;
+    if (s != MNL_OK) { rc = s; break; }
+    fi.grad_inf = si.grad_inf;
+    if (conv) {
+      fi.loglik = si.loglik_old;
+      fi.stop_reason = MNL_STOP_GTOL;
+      rc = MNL_OK;
+      break;
+    }
+    fi.iters = it + 1;
+    fi.ls_evals += si.ls_evals;
+    fi.loglik = si.loglik_new;
+    fi.dloglik = si.loglik_new - si.loglik_old;
+    fi.step_rel = si.step_inf / std::max(1.0, si.theta_inf);
+    if (o.ftol > 0 && std::fabs(fi.dloglik) < o.ftol) { fi.stop_reason = MNL_STOP_FTOL; rc = MNL_OK; break; }
+    if (steptol > 0 && fi.step_rel <= steptol) { fi.stop_reason = MNL_STOP_STEPTOL; rc = MNL_OK; break; }
+  }
+  if (rc == MNL_MAXITER) fi.stop_reason = MNL_STOP_MAXITER;
+  fi.status = rc;
+  fi.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = fi;
+  return rc;
+}
+
+int mnl_destroy(mnl_handle *h) {
+  if (!h) return MNL_OK;
+  set_device(h);
+  cudaStreamSynchronize(h->st);
+  cudaGetLastError();
+  free_all(h);
+  delete h;
+  return MNL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,152 @@
+// Internal declarations shared by the CUDA translation units of libmnl.
+//
+// Coefficient layout (eq. "theta vec", gamma_0 fixed at 0):
+//   theta = [beta_1..beta_{K-1} (p each) | gamma_1..gamma_{K-1} (d each) | alpha (f)]
+// Hessian operand layout ("class-major"): the class columns of
+//   A = [P_1 o M_1 | ... | P_{K-1} o M_{K-1}],  M_k = [X, Y_k]  (q = p + d columns per class)
+// are numbered c = (k-1) q + l, l < p for X columns, l >= p for Y columns.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/mnl.h"
+
+namespace mnl {
+
+// Operand / output tile edge of every Hessian contraction.
+constexpr int kTile = 128;
+// Rows of the N dimension consumed per pipeline stage by the tensor-core SYRK
+// (one 128-byte swizzle row per operand row).
+constexpr int kBkBf16 = 64;
+constexpr int kBkTf32 = 32;
+
+struct Shape {
+  int64_t N;
+  int K, p, d, f;
+  int q;        // p + d
+  int64_t nb;   // (K-1) p
+  int64_t ng;   // (K-1) d
+  int64_t mc;   // (K-1) q  : class coefficients
+  int64_t n;    // n_theta = mc + f
+  int64_t nout; // raw gradient accumulators: (K-1) q + K f
+};
+
+inline Shape make_shape(const mnl_dims &d) {
+  Shape s;
+  s.N = d.N; s.K = d.K; s.p = d.p; s.d = d.d; s.f = d.f;
+  s.q = d.p + d.d;
+  s.nb = (int64_t)(d.K - 1) * d.p;
+  s.ng = (int64_t)(d.K - 1) * d.d;
+  s.mc = s.nb + s.ng;
+  s.n = s.mc + d.f;
+  s.nout = s.mc + (int64_t)d.K * d.f;
+  return s;
+}
+
+// theta index (class part) -> class k (1..K-1) and local column l (0..q-1).
+__host__ __device__ inline void theta_class_local(const Shape &s, int64_t a, int &k, int &l) {
+  if (a < s.nb) { k = (int)(a / s.p) + 1; l = (int)(a % s.p); }
+  else { const int64_t r = a - s.nb; k = (int)(r / s.d) + 1; l = s.p + (int)(r % s.d); }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (each defined in the .cu file that owns the kernel).
+// ---------------------------------------------------------------------------
+
+struct PassIO {
+  const float *X, *Y, *Z;
+  const int32_t *choice;
+  const double *theta;   // [n]
+  const double *delta;   // [n] or nullptr: coefficients are theta + (*tscale) * delta
+  const double *tscale;  // device scalar (used when delta != nullptr)
+  void *P;               // [N][K] T, FULL mode only
+  void *zbar;            // [N][f] T, FULL mode only
+  double *partials;      // [grid][2 + nout] (FULL) or [grid][2] (loglik only)
+};
+
+// Configuration of the fused utility/softmax/log-likelihood/gradient pass.
+struct PassPlan {
+  int grid, block, rows, npt;   // CTAs, threads, rows per tile, outputs per thread
+  size_t smem;
+  bool ok;
+};
+PassPlan plan_pass(const Shape &s, bool fp64, bool full, int num_sms);
+cudaError_t launch_pass(const Shape &s, const PassPlan &pl, bool fp64, bool full, const PassIO &io, cudaStream_t st);
+
+// Fixed-order FP64 reduction of the pass partials.
+//   out: [0] l, [1] sum |l_i|, [2] max|g|; grad (θ order) when full.
+cudaError_t launch_pass_reduce(const Shape &s, int grid, bool full, const double *partials, double *scal,
+                               double *grad, cudaStream_t st);
+
+// Data validation: status bits |= 1 (choice out of range), 2 (non-finite data).
+cudaError_t launch_validate(const Shape &s, const float *X, const float *Y, const float *Z, const int32_t *choice,
+                            int *status, cudaStream_t st);
+
+// Hessian operands At [mc_pad][ldn] (class-major rows, observation columns):
+//   At  [c][i] = P_ik m_ik[l]                   (c = (k-1)q + l)
+//   Ad  [c][i] = sqrt(P_ik (1 - P_ik)) m_ik[l]
+// T = double (FP64), float rounded to TF32 (TF32), or bf16 (BF16).
+enum class OpType { F64 = 0, TF32 = 1, BF16 = 2 };
+cudaError_t launch_build_operands(const Shape &s, OpType t, const float *X, const float *Y, const void *P,
+                                  void *At, void *Ad, int64_t ldn, cudaStream_t st);
+
+// Tile lists (pairs (ti, tj), ti >= tj) of the two contractions.
+struct TileLists {
+  int nmain, nband;
+  int2 *main;      // all lower-triangle tiles, index ti(ti+1)/2 + tj
+  int2 *band;      // tiles meeting a diagonal class block
+  int *band_of;    // [2 * ntiles1d]: band index of (ti, ti) at 2ti, of (ti, ti-1) at 2ti+1, or -1
+};
+
+// FP64 CUDA-core SYRK: out[(s * ntiles + t)][128][128] = sum over split s of At[a] At[b]^T.
+cudaError_t launch_syrk_f64(const double *At, int64_t ldn, int64_t N, const int2 *tiles, int ntiles, int nsplit,
+                            double *out, cudaStream_t st);
+
+// tcgen05 tensor-core SYRK (BF16 or TF32 operands, FP32 accumulation in TMEM).
+struct TcPlan {
+  CUtensorMap map;
+  int nsplit, kblocks, grid;
+  size_t smem;
+};
+cudaError_t make_tc_plan(OpType t, const void *At, int64_t rows_pad, int64_t ldn, int64_t N, int ntiles,
+                         int num_sms, TcPlan *out);
+cudaError_t launch_syrk_tc(OpType t, const TcPlan &pl, const int2 *tiles, int ntiles, float *out, int *err,
+                           cudaStream_t st);
+
+// Z blocks (FP32 or FP64 accumulation), per class k = 0..K-1 and N split:
+//   cross_k  = sum_i P_ik m_ik (z_ik - zbar_i)^T        [q][f]  (k >= 1)
+//   aa_k     = sum_i P_ik (z_ik - zbar_i)(z_ik - zbar_i)^T [f][f] (lower)
+// out[(s * K + k)][q*f + f*f]
+cudaError_t launch_zblocks(const Shape &s, bool fp64, const float *X, const float *Y, const float *Z, const void *P,
+                           const void *zbar, int nsplit, void *out, cudaStream_t st);
+
+// Assemble F = -H (n x n, column-major, lower triangle and diagonal) from the
+// contraction partials.  main/band partials are FP32 (tensor path) or FP64.
+struct AssembleIO {
+  const void *main_part; int main_split;
+  const void *band_part; int band_split;
+  const void *z_part;    int z_split;
+  const TileLists *tl;   // device pointers inside
+  bool fp64;
+};
+cudaError_t launch_assemble(const Shape &s, const AssembleIO &io, int nmain, double *F, cudaStream_t st);
+
+// Mirror the lower triangle of F into a full symmetric matrix H = -F (column-major).
+cudaError_t launch_export_hessian(int64_t n, const double *F, double *H, cudaStream_t st);
+
+// Blocked FP64 Cholesky of F (lower, column-major, ld = n) in place, then
+// solve F x = b.  status |= 4 when a pivot is not positive or not finite.
+cudaError_t launch_cholesky(int64_t n, double *F, int *status, cudaStream_t st);
+cudaError_t launch_cholesky_solve(int64_t n, const double *L, const double *b, double *x, const int *status,
+                                  cudaStream_t st);
+
+// Small FP64 vector kernels.
+cudaError_t launch_axpy_theta(int64_t n, double *theta, const double *delta, const double *tscale, double *scal_out,
+                              cudaStream_t st);
+cudaError_t launch_vec_absmax(int64_t n, const double *v, double *out, cudaStream_t st);
+
+}  // namespace mnl

@@ -1,0 +1,364 @@
+// Tensor-core SYRK for the class blocks of the negative Hessian (Sec. 3.3,
+// eq. "hessian block"):  C = A^T A  over the observations, A = At^T.
+//
+// At is stored class-major, [rows_pad][ldn], one operand row per Hessian
+// column, observations contiguous ("K-major" for the MMA).  Every work unit is
+// one 128 x 128 output tile (ti, tj), ti >= tj, over one contiguous range
+// ("split") of the observations; partial tiles are written in float32 and
+// reduced in fixed order by the assembly kernel (no float atomics).
+//
+// Per CTA (one per SM, persistent, 6 warps):
+//   warp 0 (one lane): TMA producer, 128-row x 128-byte boxes with the
+//                      128-byte swizzle into a 6-stage shared-memory ring;
+//                      a diagonal tile loads its single operand once.
+//   warp 1:            TMEM allocation (256 columns = two 128-column FP32
+//                      accumulators); one lane issues tcgen05.mma
+//                      (M = N = 128, K = 16 for BF16 or 8 for TF32) and frees
+//                      ring slots / publishes accumulators with tcgen05.commit.
+//   warps 2-5:         epilogue, tcgen05.ld of 32 TMEM lanes each, written
+//                      transposed so each store instruction covers 128
+//                      contiguous bytes; overlaps the next tile's main loop.
+// Every wait is bounded (2 s on %globaltimer).  A wait that gives up raises a
+// shared abort flag and the error word; every role then leaves its loop,
+// in-flight TMA loads and MMAs are waited for (again bounded), TMEM is freed
+// and the kernel returns.
+#include "mnl_internal.cuh"
+
+namespace mnl {
+namespace {
+
+constexpr int kStages = 6;
+constexpr int kOpBytes = kTile * 128;        // one operand box: 128 rows x 128 bytes
+constexpr int kStageBytes = 2 * kOpBytes;    // A and B operands
+constexpr int kSmemBytes = kStages * kStageBytes + 256 + 1024;
+constexpr int kTmemCols = 2 * kTile;
+constexpr uint64_t kTimeoutNs = 2000000000ull;
+
+// Instruction descriptors (kind::f16 with BF16 inputs / kind::tf32): FP32
+// accumulator, both operands K-major, N = 128, M = 128.
+constexpr uint32_t kIdescBf16 =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTile >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
+constexpr uint32_t kIdescTf32 =
+    (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTile >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
+
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(saddr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase of `parity` to complete.  Returns false when another role
+// raised the abort flag (if honour_abort) or after kTimeoutNs (then raises the
+// abort flag and records `code` in the error word).
+__device__ bool wait_bounded(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *err, int code,
+                             bool honour_abort = true) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 31u) == 0) {
+      if (honour_abort && *abort_flag) return false;
+      if (gtimer() - t0 > kTimeoutNs) {
+        *abort_flag = 1;
+        atomicOr(err, code);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap *map, uint64_t *bar, void *dst, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
+          "r"(saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(saddr(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+               : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand in the 128-byte swizzle
+// layout written by TMA (8-row x 128-byte atoms, 1024 bytes apart).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                   // leading byte offset (not used by this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                   // descriptor version
+  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  return d;
+}
+
+template <bool TF32>
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  if (TF32) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kIdescTf32), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kIdescBf16), "r"(accumulate)
+        : "memory");
+  }
+}
+
+__device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Error word bits.
+constexpr int kErrProducer = 1, kErrMma = 2, kErrEpilogue = 4, kErrDrain = 8;
+
+template <bool TF32>
+__global__ void __launch_bounds__(192, 1) syrk_tc_kernel(const __grid_constant__ CUtensorMap map,
+                                                         const int2 *__restrict__ tiles, int ntiles, int nsplit,
+                                                         int kblocks, float *__restrict__ out, int *__restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
+  uint64_t *empty = full + kStages;
+  uint64_t *tfull = empty + kStages;
+  uint64_t *tempty = tfull + 2;
+  uint64_t *drain = tempty + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int total = ntiles * nsplit;
+  constexpr int kBk = TF32 ? kBkTf32 : kBkBf16;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 4); }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      int stage = 0;
+      uint32_t phase = 0;
+      int last_par[kStages];
+      for (int s = 0; s < kStages; ++s) last_par[s] = -1;
+      bool ok = true;
+      for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
+        const int sp = u / ntiles, t = u % ntiles;
+        const int2 tl = tiles[t];
+        const int kb0 = (int)((int64_t)kblocks * sp / nsplit), kb1 = (int)((int64_t)kblocks * (sp + 1) / nsplit);
+        const bool diag = tl.x == tl.y;
+        for (int kb = kb0; kb < kb1; ++kb) {
+          if (!wait_bounded(&empty[stage], phase ^ 1u, abort_flag, err, kErrProducer)) { ok = false; break; }
+          uint8_t *dst = smem + stage * kStageBytes;
+          mbar_arrive_expect_tx(&full[stage], diag ? kOpBytes : 2 * kOpBytes);
+          tma_load_2d(&map, &full[stage], dst, kb * kBk, tl.x * kTile);
+          if (!diag) tma_load_2d(&map, &full[stage], dst + kOpBytes, kb * kBk, tl.y * kTile);
+          last_par[stage] = (int)phase;
+          if (++stage == kStages) { stage = 0; phase ^= 1u; }
+        }
+      }
+      // No TMA write may still be pending when the CTA exits.
+      for (int s = 0; s < kStages; ++s)
+        if (last_par[s] >= 0) wait_bounded(&full[s], (uint32_t)last_par[s], abort_flag, err, kErrDrain, false);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t acc_ph[2] = {0u, 0u};
+      int local = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < total && ok; u += gridDim.x, ++local) {
+        const int sp = u / ntiles, t = u % ntiles;
+        const int2 tl = tiles[t];
+        const int kb0 = (int)((int64_t)kblocks * sp / nsplit), kb1 = (int)((int64_t)kblocks * (sp + 1) / nsplit);
+        const bool diag = tl.x == tl.y;
+        const int b = local & 1;
+        if (!wait_bounded(&tempty[b], acc_ph[b] ^ 1u, abort_flag, err, kErrMma)) break;
+        acc_ph[b] ^= 1u;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(b * kTile);
+        for (int kb = kb0; kb < kb1; ++kb) {
+          if (!wait_bounded(&full[stage], phase, abort_flag, err, kErrMma)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t a_addr = saddr(smem + stage * kStageBytes);
+          const uint32_t b_addr = diag ? a_addr : a_addr + kOpBytes;
+          const uint64_t ad = sw128_desc(a_addr), bd = sw128_desc(b_addr);
+#pragma unroll
+          for (int k = 0; k < 4; ++k)  // 4 x 32 bytes along K inside the 128-byte row
+            tc_mma<TF32>(d_tmem, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), (kb > kb0 || k > 0) ? 1u : 0u);
+          tc_commit(&empty[stage]);
+          if (++stage == kStages) { stage = 0; phase ^= 1u; }
+        }
+        if (!ok) break;
+        tc_commit(&tfull[b]);
+      }
+      // Every MMA issued by this thread has completed before TMEM is freed.
+      tc_commit(drain);
+      wait_bounded(drain, 0u, abort_flag, err, kErrDrain, false);
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int quarter = warp & 3;  // this warp may access TMEM lanes 32*quarter .. +31
+    uint32_t acc_ph[2] = {0u, 0u};
+    int local = 0;
+    for (int u = blockIdx.x; u < total; u += gridDim.x, ++local) {
+      const int sp = u / ntiles, t = u % ntiles;
+      const int b = local & 1;
+      int ok = 0;
+      if (lane == 0) ok = wait_bounded(&tfull[b], acc_ph[b], abort_flag, err, kErrEpilogue) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      acc_ph[b] ^= 1u;
+      tc_fence_after();
+      // Tile stored transposed: out[col][row], row = MMA M index (operand tile ti).
+      float *dst = out + ((int64_t)sp * ntiles + t) * kTile * kTile + quarter * 32 + lane;
+#pragma unroll 1
+      for (int c0 = 0; c0 < kTile; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kTile + c0), v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) dst[(int64_t)(c0 + j) * kTile] = __uint_as_float(v[j]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled get_encoder() {
+  static EncodeTiled fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  }
+  return fn;
+}
+
+}  // namespace
+
+cudaError_t make_tc_plan(OpType t, const void *At, int64_t rows_pad, int64_t ldn, int64_t N, int ntiles,
+                         int num_sms, TcPlan *out) {
+  (void)N;
+  if (t == OpType::F64) return cudaErrorInvalidValue;
+  EncodeTiled enc = get_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const bool tf32 = t == OpType::TF32;
+  const int bk = tf32 ? kBkTf32 : kBkBf16;
+  const size_t esz = tf32 ? 4 : 2;
+  if (ldn % bk != 0 || (ldn * esz) % 16 != 0 || rows_pad % kTile != 0 ||
+      (reinterpret_cast<uintptr_t>(At) & 15) != 0)
+    return cudaErrorInvalidValue;
+  cuuint64_t dims[2] = {(cuuint64_t)ldn, (cuuint64_t)rows_pad};
+  cuuint64_t strides[1] = {(cuuint64_t)(ldn * esz)};
+  cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)kTile};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(&out->map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                   const_cast<void *>(At), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  out->kblocks = (int)(ldn / bk);
+  // Splits of the observation range: balance units over the SMs, keep >= 8 K-blocks per split.
+  int best = 1;
+  double best_eff = -1.0;
+  const int max_split = std::max(1, std::min(16, out->kblocks / 8));
+  for (int s = 1; s <= max_split; ++s) {
+    const int units = ntiles * s;
+    const int g = std::min(units, num_sms);
+    const int waves = (units + g - 1) / g;
+    const double eff = (double)units / ((double)g * waves) * (g / (double)num_sms);
+    if (eff > best_eff + 0.02) { best_eff = eff; best = s; }
+  }
+  out->nsplit = best;
+  out->grid = std::min(ntiles * best, num_sms);
+  out->smem = kSmemBytes;
+  return cudaSuccess;
+}
+
+cudaError_t launch_syrk_tc(OpType t, const TcPlan &pl, const int2 *tiles, int ntiles, float *out, int *err,
+                           cudaStream_t st) {
+  cudaError_t e;
+  if (t == OpType::TF32) {
+    if ((e = cudaFuncSetAttribute(syrk_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)))
+      return e;
+    syrk_tc_kernel<true><<<pl.grid, 192, kSmemBytes, st>>>(pl.map, tiles, ntiles, pl.nsplit, pl.kblocks, out, err);
+  } else {
+    if ((e = cudaFuncSetAttribute(syrk_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)))
+      return e;
+    syrk_tc_kernel<false><<<pl.grid, 192, kSmemBytes, st>>>(pl.map, tiles, ntiles, pl.nsplit, pl.kblocks, out, err);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace mnl
