@@ -206,6 +206,38 @@ MNL_API int mnl_fit(mnl_handle *h, const mnl_fit_opts *opts, double *theta, mnl_
 /* Free the handle and every device buffer it owns (NULL is a no-op). */
 MNL_API int mnl_destroy(mnl_handle *h);
 
+/* Log-likelihood and gradient, as mnl_loglik_grad, without allocating any
+ * device memory.  The paper has no counterpart: this is for callers that
+ * cannot call cudaMalloc when they need l and g - code whose device memory
+ * is owned by an arena or pool, plug-ins of hosts that forbid allocation
+ * after start-up, latency-critical loops where an allocation could block or
+ * fail.  It creates no handle; every input and output belongs to the caller.
+ *   dims, data  as for mnl_create (DEVICE pointers).  The data are not
+ *               validated: choices must lie in [0, K) and values be finite.
+ *   precision   MNL_FP64: the pass runs in float64; MNL_TF32 / MNL_BF16:
+ *               float32 with compensated sums (the Hessian precision does not
+ *               matter here).
+ *   theta       DEVICE [n_theta] float64.
+ *   loglik      DEVICE, one float64.
+ *   grad        DEVICE [n_theta] float64.
+ *   P           DEVICE [N][K] choice probabilities (float64 for MNL_FP64,
+ *               float32 otherwise).
+ *   zbar        DEVICE [N][f] expected Z per observation, sum_k P_ik Z_ik
+ *               (same type as P); NULL when f = 0.
+ *   stream      cudaStream_t (as void*); the call only enqueues work.
+ * Scratch: a fixed 4 MiB array inside the library holds the partial sums
+ * between the two kernels of the pass; every GPU that loads the library keeps
+ * it until the process exits.  Problems needing more than that, i.e. with
+ * (K-1)(p+d) + K f > 524284, or with K > 256, return MNL_ERR_UNSUPPORTED.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array: calls that can overlap on the GPU (other
+ * streams, other threads) race and corrupt each other's results, so order
+ * them, e.g. on one stream.  Nothing in the array needs to start at zero;
+ * every call overwrites what it later reads. */
+MNL_API int mnl_loglik_grad_noalloc(const mnl_dims *dims, const mnl_data *data, int precision, const double *theta,
+                                    double *loglik, double *grad, void *P, void *zbar, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

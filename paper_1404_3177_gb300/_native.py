@@ -32,6 +32,7 @@ MNL_STOP_GTOL, MNL_STOP_FTOL, MNL_STOP_STEPTOL, MNL_STOP_MAXITER = 1, 2, 3, 4
 EXPORTS = (
     "mnl_num_params", "mnl_status_string", "mnl_workspace_bytes", "mnl_fit_opts_default", "mnl_create",
     "mnl_upload", "mnl_loglik_grad", "mnl_hessian", "mnl_newton_step", "mnl_fit", "mnl_destroy",
+    "mnl_loglik_grad_noalloc",
 )
 
 
@@ -113,6 +114,9 @@ def load() -> C.CDLL:
         lib.mnl_fit.argtypes = [vp, C.POINTER(mnl_fit_opts), vp, C.POINTER(mnl_fit_info)]
         lib.mnl_destroy.restype = i32
         lib.mnl_destroy.argtypes = [vp]
+        lib.mnl_loglik_grad_noalloc.restype = i32
+        lib.mnl_loglik_grad_noalloc.argtypes = [C.POINTER(mnl_dims), C.POINTER(mnl_data), i32, vp, vp, vp, vp, vp,
+                                                vp]
         _lib = lib
         return lib
 
@@ -189,3 +193,12 @@ def mnl_fit(handle: int, opts: mnl_fit_opts | None, theta_ptr: int) -> mnl_fit_i
 
 def mnl_destroy(handle: int) -> None:
     _check(load().mnl_destroy(C.c_void_p(handle)), "mnl_destroy")
+
+
+def mnl_loglik_grad_noalloc(dims: mnl_dims, data: mnl_data, precision: int, theta_ptr: int, loglik_ptr: int,
+                            grad_ptr: int, P_ptr: int, zbar_ptr: int | None, stream: int | None) -> None:
+    """Enqueue l, g (and P, zbar) into caller-owned device buffers; allocates nothing."""
+    rc = load().mnl_loglik_grad_noalloc(C.byref(dims), C.byref(data), precision, C.c_void_p(theta_ptr),
+                                        C.c_void_p(loglik_ptr), C.c_void_p(grad_ptr), C.c_void_p(P_ptr),
+                                        C.c_void_p(zbar_ptr) if zbar_ptr else None, C.c_void_p(stream or 0))
+    _check(rc, "mnl_loglik_grad_noalloc")
