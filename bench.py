@@ -35,6 +35,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "newton_iters_per_s"
+# CUDA-core peaks measured on this machine's GB300 (152 SMs at 2070 MHz) with a
+# dependent-chain-free FMA microbenchmark: float64 DFMA 1.06, float64 DMMA 1.10,
+# float32 FFMA 71.0 TFLOP/s (cuBLAS DGEMM 1.10, SGEMM 69.8).
+FP64_TFLOPS = 1.06
+FP32_TFLOPS = 71.0
 UNIT = "iter/s"
 WORKLOAD = "c2_N200000_K50_p50_d5_f5"
 CONFIG_NOTE = "inputs larger than L2 (no flush)"
@@ -223,7 +228,7 @@ def run_ours(args, world, rank, local):
     X, Y, Z, c = (t.to(dev) for t in (Xh, Yh, Zh, ch))
     n = prob.n_theta
     stream = torch.cuda.current_stream()
-    m = MNL(X, Y, Z, c, precision=args.precision)
+    m = MNL(X, Y, Z, c, precision=args.precision, solve=args.solve)
     theta0 = torch.zeros(n, dtype=torch.float64, device=dev)
     theta = theta0.clone()
 
@@ -257,7 +262,25 @@ def run_ours(args, world, rank, local):
     value = world * args.steps / (ms_max / 1000.0)
 
     # e2e: through the C ABI with host buffers (H2D of the inputs + one Newton step + D2H of theta)
-    mh = MNL.with_host_upload(prob.N, prob.K, prob.p, prob.d, prob.f, precision=args.precision)
+    # the same step with the float64 Cholesky solve, for comparison (not the headline)
+    alt = {}
+    if args.solve != "fp64" and args.precision != "fp64":
+        from paper_1404_3177_gb300 import _native as nat
+        nat.mnl_set_solve(m.h, nat.MNL_SOLVE_FP64)
+        step()
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        alt_infos = [step() for _ in range(3)]
+        a1.record(stream)
+        torch.cuda.synchronize()
+        alt = {"solve": "fp64", "ms_per_step": a0.elapsed_time(a1) / 3,
+               "cholesky_ms": statistics.median(i["t_factor_ms"] for i in alt_infos),
+               "solve_ms": statistics.median(i["t_solve_ms"] for i in alt_infos)}
+        nat.mnl_set_solve(m.h, nat.SOLVES[args.solve])
+
+    mh = MNL.with_host_upload(prob.N, prob.K, prob.p, prob.d, prob.f, precision=args.precision, solve=args.solve)
     theta_h = torch.zeros(n, dtype=torch.float64).pin_memory()
     out_h = torch.empty(n, dtype=torch.float64).pin_memory()
 
@@ -292,12 +315,13 @@ def run_ours(args, world, rank, local):
         "syrk_diag_blocks": med("t_band_ms"), "z_blocks": med("t_zblk_ms"), "assemble": med("t_asm_ms"),
         "cholesky": med("t_factor_ms"), "solve": med("t_solve_ms"), "line_search": med("t_ls_ms"),
     }
+    mixed_used = infos[-1]["solve_mode"] == 2
     dominant = max(kern, key=kern.get)
     syrk_flops = float(N) * mc * (mc + 1)
     pass_bytes = 4.0 * N * (prob.p + K * (prob.d + f) + 1) + 4.0 * N * K + 4.0 * N * f
     chol_flops = n ** 3 / 3.0
     if args.precision == "fp64":
-        syrk_peak, syrk_unit, syrk_bound = pk.get("fp64_tflops"), "TFLOP/s", "alu"
+        syrk_peak, syrk_unit, syrk_bound = FP64_TFLOPS, "TFLOP/s", "alu"
     elif args.precision == "tf32":
         syrk_peak = pk["bf16_tflops_sustained"] / 2.0 if pk.get("bf16_tflops_sustained") else None
         syrk_unit, syrk_bound = "TFLOP/s", "tensor"
@@ -309,7 +333,8 @@ def run_ours(args, world, rank, local):
         "pass": {"bound": "hbm", "achieved": pass_bytes / (kern["pass"] * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
                  "unit": "GB/s", "traffic": None},
         "cholesky": {"bound": "alu", "achieved": chol_flops / (kern["cholesky"] * 1e-3) / 1e12,
-                     "peak": pk.get("fp64_tflops"), "unit": "TFLOP/s", "traffic": None},
+                     "peak": FP32_TFLOPS if mixed_used else FP64_TFLOPS, "unit": "TFLOP/s", "traffic": None,
+                     "arith": "f32 factor + f64 refinement" if mixed_used else "f64"},
     }
     for r in rooflines.values():
         r["frac"] = (r["achieved"] / r["peak"]) if r.get("peak") else None
@@ -322,7 +347,8 @@ def run_ours(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": t_step * 1000, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"bf16": "bf16+f32+f64", "tf32": "tf32+f32+f64", "fp64": "f64"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": args.precision, "n_theta": n, "note": CONFIG_NOTE},
+        "config": {"workload": WORKLOAD, "precision": args.precision, "solve": args.solve, "n_theta": n,
+                   "note": CONFIG_NOTE},
         "roofline": roof,
         "kernels_ms": {k: round(v, 4) for k, v in kern.items()},
         "kernel_rooflines": rooflines,
@@ -331,6 +357,10 @@ def run_ours(args, world, rank, local):
                 "d2h_bytes_per_step": int(d2h)},
         "clocks": clocks,
         "ls_evals_per_step": med("ls_evals"),
+        "solve_mode_used": {1: "fp64", 2: "mixed"}.get(infos[-1]["solve_mode"]),
+        "refine_steps": med("refine_steps"),
+        "fallbacks": int(sum(i["fallback"] for i in infos)),
+        "fp64_solve_variant": alt or None,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob, args.ref_rows)
@@ -345,6 +375,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["bf16", "tf32", "fp64"])
+    ap.add_argument("--solve", default="auto", choices=["auto", "fp64", "mixed"],
+                    help="Newton solve: float64 Cholesky, or float32 factor + float64 refinement")
     ap.add_argument("--ref-rows", type=int, default=20000, help="observations in the oracle's bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

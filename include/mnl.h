@@ -108,10 +108,13 @@ typedef struct mnl_step_info {
    * pass = utilities/softmax/l/g; hess = every Hessian kernel; chol = factor + solve; ls = line search. */
   float t_pass_ms, t_hess_ms, t_chol_ms, t_ls_ms;
   /* Inside the Hessian and solve phases: operand build, A^T A contraction (all class blocks),
-   * diagonal class blocks, Z blocks, assembly, Cholesky factorisation, triangular solves. */
-  float t_build_ms, t_syrk_ms, t_band_ms, t_zblk_ms, t_asm_ms, t_factor_ms, t_solve_ms;
-  int32_t launches;  /* kernels this library launched for the step   */
-  int32_t pad;
+   * diagonal class blocks, Z blocks, assembly, factorisation (the whole mixed solve for
+   * MNL_SOLVE_MIXED), triangular solves, float64 fallback of a mixed solve (0 when not taken). */
+  float t_build_ms, t_syrk_ms, t_band_ms, t_zblk_ms, t_asm_ms, t_factor_ms, t_solve_ms, t_fallback_ms;
+  int32_t launches;    /* kernels this library launched for the step        */
+  int32_t solve_mode;  /* MNL_SOLVE_FP64 or MNL_SOLVE_MIXED, as used          */
+  int32_t refine_steps;/* refinement steps of a mixed solve                 */
+  int32_t fallback;    /* 1 when a mixed solve fell back to float64          */
 } mnl_step_info;
 
 typedef struct mnl_fit_opts {
@@ -202,6 +205,19 @@ MNL_API int mnl_newton_step(mnl_handle *h, double *theta, mnl_step_info *info);
  * Returns MNL_OK when a tolerance was met, MNL_MAXITER when maxiter ran out
  * (theta holds the last iterate), or an error of mnl_newton_step. */
 MNL_API int mnl_fit(mnl_handle *h, const mnl_fit_opts *opts, double *theta, mnl_fit_info *info);
+
+/* How mnl_newton_step / mnl_fit solve (-H) delta = g.
+ *   MNL_SOLVE_FP64:  blocked float64 Cholesky and float64 triangular solves.
+ *   MNL_SOLVE_MIXED: float32 Cholesky of -H and float64 iterative refinement
+ *                    (residuals g - (-H) delta in float64) until the correction
+ *                    is below 1e-12 of delta or stagnates below 1e-8 of it;
+ *                    if the float32 factorisation or the refinement fails, the
+ *                    step falls back to MNL_SOLVE_FP64.  On GB300 float64 runs
+ *                    at about 1/67 of the float32 rate, which makes this the
+ *                    faster route to a float64-accurate step.
+ *   MNL_SOLVE_AUTO (default): FP64 for MNL_FP64 handles, MIXED otherwise. */
+enum { MNL_SOLVE_AUTO = 0, MNL_SOLVE_FP64 = 1, MNL_SOLVE_MIXED = 2 };
+MNL_API int mnl_set_solve(mnl_handle *h, int mode);
 
 /* Free the handle and every device buffer it owns (NULL is a no-op). */
 MNL_API int mnl_destroy(mnl_handle *h);

@@ -32,8 +32,11 @@ MNL_STOP_GTOL, MNL_STOP_FTOL, MNL_STOP_STEPTOL, MNL_STOP_MAXITER = 1, 2, 3, 4
 EXPORTS = (
     "mnl_num_params", "mnl_status_string", "mnl_workspace_bytes", "mnl_fit_opts_default", "mnl_create",
     "mnl_upload", "mnl_loglik_grad", "mnl_hessian", "mnl_newton_step", "mnl_fit", "mnl_destroy",
-    "mnl_loglik_grad_noalloc",
+    "mnl_loglik_grad_noalloc", "mnl_set_solve",
 )
+
+MNL_SOLVE_AUTO, MNL_SOLVE_FP64, MNL_SOLVE_MIXED = 0, 1, 2
+SOLVES = {"auto": MNL_SOLVE_AUTO, "fp64": MNL_SOLVE_FP64, "mixed": MNL_SOLVE_MIXED}
 
 
 class mnl_dims(C.Structure):
@@ -52,8 +55,9 @@ class mnl_step_info(C.Structure):
                 ("t_pass_ms", C.c_float), ("t_hess_ms", C.c_float), ("t_chol_ms", C.c_float),
                 ("t_ls_ms", C.c_float), ("t_build_ms", C.c_float), ("t_syrk_ms", C.c_float),
                 ("t_band_ms", C.c_float), ("t_zblk_ms", C.c_float), ("t_asm_ms", C.c_float),
-                ("t_factor_ms", C.c_float), ("t_solve_ms", C.c_float), ("launches", C.c_int32),
-                ("pad", C.c_int32)]
+                ("t_factor_ms", C.c_float), ("t_solve_ms", C.c_float), ("t_fallback_ms", C.c_float),
+                ("launches", C.c_int32), ("solve_mode", C.c_int32), ("refine_steps", C.c_int32),
+                ("fallback", C.c_int32)]
 
 
 class mnl_fit_opts(C.Structure):
@@ -114,6 +118,8 @@ def load() -> C.CDLL:
         lib.mnl_fit.argtypes = [vp, C.POINTER(mnl_fit_opts), vp, C.POINTER(mnl_fit_info)]
         lib.mnl_destroy.restype = i32
         lib.mnl_destroy.argtypes = [vp]
+        lib.mnl_set_solve.restype = i32
+        lib.mnl_set_solve.argtypes = [vp, i32]
         lib.mnl_loglik_grad_noalloc.restype = i32
         lib.mnl_loglik_grad_noalloc.argtypes = [C.POINTER(mnl_dims), C.POINTER(mnl_data), i32, vp, vp, vp, vp, vp,
                                                 vp]
@@ -189,6 +195,10 @@ def mnl_fit(handle: int, opts: mnl_fit_opts | None, theta_ptr: int) -> mnl_fit_i
                         C.byref(info))
     _check(rc, "mnl_fit")
     return info
+
+
+def mnl_set_solve(handle: int, mode: int) -> None:
+    _check(load().mnl_set_solve(C.c_void_p(handle), mode), "mnl_set_solve")
 
 
 def mnl_destroy(handle: int) -> None:

@@ -20,13 +20,14 @@ class MNL:
     """
 
     def __init__(self, X=None, Y=None, Z=None, choice=None, *, K=None, precision="bf16", stream=None,
-                 host_owned_dims=None):
+                 host_owned_dims=None, solve="auto"):
         self.precision = nat.PRECISIONS[precision]
         self._stream = (stream or torch.cuda.current_stream()).cuda_stream
         if host_owned_dims is not None:
             self.dims = host_owned_dims
             self._keep = ()
             self.h = nat.mnl_create(self.dims, None, self.precision, self._stream)
+            nat.mnl_set_solve(self.h, nat.SOLVES[solve])
             return
         if choice is None:
             raise ValueError("choice is required")
@@ -48,11 +49,12 @@ class MNL:
         self.dims = nat.mnl_dims(N, K, p, d, f, 0)
         data = nat.mnl_data(_ptr(X), _ptr(Y), _ptr(Z), _ptr(choice))
         self.h = nat.mnl_create(self.dims, data, self.precision, self._stream)
+        nat.mnl_set_solve(self.h, nat.SOLVES[solve])
 
     @classmethod
-    def with_host_upload(cls, N, K, p, d, f, *, precision="bf16", stream=None):
+    def with_host_upload(cls, N, K, p, d, f, *, precision="bf16", stream=None, solve="auto"):
         """A handle that owns its device copies of the data; fill it with ``upload``."""
-        return cls(precision=precision, stream=stream, host_owned_dims=nat.mnl_dims(N, K, p, d, f, 0))
+        return cls(precision=precision, stream=stream, host_owned_dims=nat.mnl_dims(N, K, p, d, f, 0), solve=solve)
 
     def upload(self, X=None, Y=None, Z=None, choice=None):
         """Copy host tensors (pinned for speed) into the handle's own device buffers."""

@@ -42,6 +42,10 @@ struct mnl_handle {
   int main_split, band_split, z_split;
   TcPlan tc_main, tc_band;
   double *F;
+  // solve
+  int solve_mode;  // MNL_SOLVE_FP64 or MNL_SOLVE_MIXED (resolved)
+  double *dinv, *rwork, *ref;
+  float *F32, *dinv32, *fwork;
   // host mirrors (pinned)
   double *h_scal;
   int *h_flags;
@@ -70,6 +74,8 @@ int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
 // Below this many observations MNL_BF16 forms the Hessian operands in TF32.
 constexpr int64_t kBf16MinRows = 1024;
+// Refinement steps of a mixed solve at most (each skipped once converged).
+constexpr int kRefineIters = 5;
 
 bool dims_ok(const mnl_dims *d) {
   return d && d->N >= 1 && d->K >= 2 && d->p >= 0 && d->d >= 0 && d->f >= 0 && (d->p + d->d + d->f) >= 1 &&
@@ -77,8 +83,10 @@ bool dims_ok(const mnl_dims *d) {
 }
 
 struct Sizes {
-  size_t P, zbar, part_full, part_ll, ops, main_part, band_part, z_part, F, owned;
-  size_t total() const { return P + zbar + part_full + part_ll + 2 * ops + main_part + band_part + z_part + F + owned; }
+  size_t P, zbar, part_full, part_ll, ops, main_part, band_part, z_part, F, owned, solve;
+  size_t total() const {
+    return P + zbar + part_full + part_ll + 2 * ops + main_part + band_part + z_part + F + owned + solve;
+  }
 };
 
 void band_tiles(const Shape &S, int nt1d, std::vector<int2> &band, std::vector<int> &band_of) {
@@ -115,7 +123,7 @@ Sizes plan_sizes(const mnl_dims &d, int prec_in, bool owned, int nsm, int *main_
   *pl = plan_pass(S, fp64, false, nsm);
   z.P = (size_t)S.N * S.K * tsz;
   z.zbar = (size_t)S.N * S.f * tsz;
-  z.part_full = (size_t)pf->grid * (2 + S.nout) * 8;
+  z.part_full = (size_t)pf->grid * (2 + S.n) * 8;
   z.part_ll = (size_t)pl->grid * 2 * 8;
   *ldn = round_up(S.N, 64);
   *mc_pad = round_up(S.mc, kTile);
@@ -150,10 +158,13 @@ Sizes plan_sizes(const mnl_dims &d, int prec_in, bool owned, int nsm, int *main_
   }
   z.main_part = (size_t)(*main_split) * nmain * kTile * kTile * csz;
   z.band_part = (size_t)(*band_split) * (*nband) * kTile * kTile * csz;
-  *z_split = (int)std::max<int64_t>(1, std::min<int64_t>((2 * nsm + S.K - 1) / S.K, S.N / 512));
-  const size_t nz = (size_t)S.q * S.f + (size_t)S.f * S.f;
-  z.z_part = S.f ? (size_t)(*z_split) * S.K * nz * tsz : 0;
+  const int64_t nzt = zblocks_outputs(S);
+  const int64_t zchunks = (nzt + 8191) / 8192;
+  *z_split = (int)std::max<int64_t>(1, std::min<int64_t>((2 * nsm + zchunks - 1) / zchunks, S.N / 256));
+  z.z_part = S.f ? (size_t)(*z_split) * nzt * tsz : 0;
   z.F = (size_t)S.n * S.n * 8;
+  // dinv, rwork, ref (float64); F32, dinv32, fwork (float32)
+  z.solve = ((size_t)S.n + mixed_solve_rwork_doubles(S.n) + 4) * 8 + ((size_t)S.n * S.n + 2 * (size_t)S.n) * 4;
   z.owned = owned ? ((size_t)S.N * S.p + (size_t)S.N * S.K * (S.d + S.f)) * 4 + (size_t)S.N * 4 : 0;
   return z;
 }
@@ -275,6 +286,7 @@ int step_impl(mnl_handle *h, double *theta, mnl_step_info *info, double gtol, bo
   CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
   CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->st));
   CK(cudaMemsetAsync(h->scal, 0, kNscal * sizeof(double), h->st));
+  CK(cudaMemsetAsync(h->ref, 0, 4 * sizeof(double), h->st));
   CK(cudaEventRecord(h->ev[0], h->st));
   int rc = run_pass(h, theta, true, nullptr, kL);
   if (rc) return rc;
@@ -297,19 +309,44 @@ int step_impl(mnl_handle *h, double *theta, mnl_step_info *info, double gtol, bo
   rc = run_hessian(h, h->ev + 5);
   if (rc) return rc;
   CK(cudaEventRecord(h->ev[2], h->st));
-  CK(launch_cholesky(n, h->F, h->status, h->st));
-  h->launches += (int)(3 * ((n + 63) / 64) - 2);
-  CK(cudaEventRecord(h->ev[9], h->st));
-  CK(launch_cholesky_solve(n, h->F, h->grad, h->delta, h->status, h->st));
-  h->launches += 1;
+  int nl = 0;
+  const bool mixed = h->solve_mode == MNL_SOLVE_MIXED;
+  if (mixed) {
+    CK(launch_mixed_solve(n, h->F, h->F32, h->dinv32, h->grad, h->delta, h->rwork, h->fwork, h->ref, h->status,
+                          kRefineIters, h->st, &nl));
+    h->launches += nl;
+    CK(cudaEventRecord(h->ev[9], h->st));
+  } else {
+    CK(launch_cholesky(n, h->F, h->dinv, h->status, h->st));
+    h->launches += cholesky_launches(n);
+    CK(cudaEventRecord(h->ev[9], h->st));
+    CK(launch_cholesky_solve(n, h->F, h->dinv, h->grad, h->delta, h->status, h->st, &nl));
+    h->launches += nl;
+  }
   CK(cudaEventRecord(h->ev[3], h->st));
   CK(cudaMemcpyAsync(h->h_scal, h->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   CK(cudaMemcpyAsync(h->h_flags, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   CK(cudaMemcpyAsync(h->h_flags + 1, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  if (mixed) CK(cudaMemcpyAsync(h->h_scal + 12, h->ref, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
   if (h->h_flags[1]) return MNL_ERR_TIMEOUT;
   const double l0 = h->h_scal[kL], labs = h->h_scal[kLabs], ginf = h->h_scal[kGinf];
   if (!std::isfinite(l0) || !std::isfinite(ginf)) return MNL_ERR_NONFINITE;
+  loc.solve_mode = h->solve_mode;
+  if (mixed) loc.refine_steps = (int)h->h_scal[14];
+  float t_fallback = 0.f;
+  if (mixed && (h->h_flags[0] & (8 | 16))) {
+    // float32 factor or refinement failed: float64 Cholesky of the intact F
+    loc.fallback = 1;
+    CK(cudaEventRecord(h->ev[10], h->st));
+    CK(launch_cholesky(n, h->F, h->dinv, h->status, h->st));
+    CK(launch_cholesky_solve(n, h->F, h->dinv, h->grad, h->delta, h->status, h->st, &nl));
+    h->launches += cholesky_launches(n) + nl;
+    CK(cudaEventRecord(h->ev[11], h->st));
+    CK(cudaMemcpyAsync(h->h_flags, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    t_fallback = elapsed(h->ev[10], h->ev[11]);
+  }
   if (h->h_flags[0] & 4) return MNL_ERR_NOT_PD;
   const double tau = noise_tol(h, labs);
   // Step halving (Sec. 3.1).
@@ -345,7 +382,7 @@ int step_impl(mnl_handle *h, double *theta, mnl_step_info *info, double gtol, bo
   loc.ls_evals = evals;
   loc.t_pass_ms = elapsed(h->ev[0], h->ev[1]);
   loc.t_hess_ms = elapsed(h->ev[1], h->ev[2]);
-  loc.t_chol_ms = elapsed(h->ev[2], h->ev[3]);
+  loc.t_chol_ms = elapsed(h->ev[2], h->ev[3]) + t_fallback;
   loc.t_ls_ms = elapsed(h->ev[3], h->ev[4]);
   loc.t_build_ms = elapsed(h->ev[1], h->ev[5]);
   loc.t_syrk_ms = elapsed(h->ev[5], h->ev[6]);
@@ -354,6 +391,7 @@ int step_impl(mnl_handle *h, double *theta, mnl_step_info *info, double gtol, bo
   loc.t_asm_ms = elapsed(h->ev[8], h->ev[2]);
   loc.t_factor_ms = elapsed(h->ev[2], h->ev[9]);
   loc.t_solve_ms = elapsed(h->ev[9], h->ev[3]);
+  loc.t_fallback_ms = t_fallback;
   loc.launches = h->launches;
   if (info) *info = loc;
   return MNL_OK;
@@ -449,7 +487,7 @@ int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *
   Sizes z = plan_sizes(*dims, precision, data == nullptr, h->nsm, &h->main_split, &h->band_split, &h->z_split,
                        &h->pfull, &h->pll, &h->ldn, &h->mc_pad, &h->nt1d, &nband);
   if (!h->pfull.ok || !h->pll.ok) return fail(MNL_ERR_UNSUPPORTED);
-  if (h->S.f > 0 && (size_t)h->S.q * h->S.f + (size_t)h->S.f * h->S.f > 4096) return fail(MNL_ERR_UNSUPPORTED);
+
   for (auto &e : h->ev)
     if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return fail(MNL_ERR_CUDA); }
   if (cudaMallocHost(&h->h_scal, 32 * sizeof(double)) != cudaSuccess ||
@@ -466,8 +504,12 @@ int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *
       (rc = dalloc(h, &h->status, 16)) || (rc = dalloc(h, &h->err, 16)) || (rc = dalloc(h, &h->At, z.ops)) ||
       (rc = dalloc(h, &h->Ad, z.ops)) || (rc = dalloc(h, &h->main_part, z.main_part)) ||
       (rc = dalloc(h, &h->band_part, z.band_part)) || (rc = dalloc(h, &h->z_part, z.z_part)) ||
-      (rc = dalloc(h, &h->F, z.F)))
+      (rc = dalloc(h, &h->F, z.F)) || (rc = dalloc(h, &h->dinv, S.n * 8)) ||
+      (rc = dalloc(h, &h->rwork, mixed_solve_rwork_doubles(S.n) * 8)) || (rc = dalloc(h, &h->ref, 4 * 8)) ||
+      (rc = dalloc(h, &h->F32, (size_t)S.n * S.n * 4)) || (rc = dalloc(h, &h->dinv32, S.n * 4)) ||
+      (rc = dalloc(h, &h->fwork, S.n * 4)))
     return fail(rc);
+  h->solve_mode = h->fp64 ? MNL_SOLVE_FP64 : MNL_SOLVE_MIXED;
   (void)tsz;
   h->op_bytes = z.ops;
   if (z.ops) {
@@ -615,6 +657,12 @@ int mnl_fit(mnl_handle *h, const mnl_fit_opts *opts, double *theta, mnl_fit_info
   fi.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = fi;
   return rc;
+}
+
+int mnl_set_solve(mnl_handle *h, int mode) {
+  if (!h || mode < MNL_SOLVE_AUTO || mode > MNL_SOLVE_MIXED) return MNL_ERR_INVALID_ARG;
+  h->solve_mode = mode == MNL_SOLVE_AUTO ? (h->fp64 ? MNL_SOLVE_FP64 : MNL_SOLVE_MIXED) : mode;
+  return MNL_OK;
 }
 
 int mnl_destroy(mnl_handle *h) {

@@ -28,12 +28,13 @@ namespace {
 // P_ik (an intercept-only model, indicator columns) would give every product
 // the same rounding error; unbiased rounding turns that into independent
 // errors that average out over the observations.  The random bits are a hash
-// of (operand, column, observation), so results are reproducible.
+// of (operand, column, observation pair), so results are reproducible.
 template <OpType OT>
 struct OpStore;
 template <>
 struct OpStore<OpType::F64> {
-  __device__ static void put(void *base, int64_t idx, double a, double b, uint32_t, uint32_t) {
+  using CT = double;
+  __device__ static void put(void *base, int64_t idx, double a, double b, uint32_t) {
     *reinterpret_cast<double2 *>(reinterpret_cast<double *>(base) + idx) = make_double2(a, b);
   }
 };
@@ -44,30 +45,27 @@ __device__ __forceinline__ float to_tf32(float x) {
 }
 template <>
 struct OpStore<OpType::TF32> {
-  __device__ static void put(void *base, int64_t idx, double a, double b, uint32_t, uint32_t) {
-    *reinterpret_cast<float2 *>(reinterpret_cast<float *>(base) + idx) =
-        make_float2(to_tf32((float)a), to_tf32((float)b));
+  using CT = float;
+  __device__ static void put(void *base, int64_t idx, float a, float b, uint32_t) {
+    *reinterpret_cast<float2 *>(reinterpret_cast<float *>(base) + idx) = make_float2(to_tf32(a), to_tf32(b));
   }
 };
-__device__ __forceinline__ uint16_t bf16_stochastic(float x, uint32_t r) {
-  const uint32_t u = __float_as_uint(x) + (r & 0xFFFFu);
-  return (uint16_t)(u >> 16);
-}
 template <>
 struct OpStore<OpType::BF16> {
-  __device__ static void put(void *base, int64_t idx, double a, double b, uint32_t ra, uint32_t rb) {
-    const uint32_t lo = bf16_stochastic((float)a, ra), hi = bf16_stochastic((float)b, rb);
-    *reinterpret_cast<uint32_t *>(reinterpret_cast<__nv_bfloat16 *>(base) + idx) = lo | (hi << 16);
+  using CT = float;
+  // r: 32 random bits, 16 for each of the two values.
+  __device__ static void put(void *base, int64_t idx, float a, float b, uint32_t r) {
+    const uint32_t ua = __float_as_uint(a) + (r & 0xFFFFu);
+    const uint32_t ub = __float_as_uint(b) + (r >> 16);
+    *reinterpret_cast<uint32_t *>(reinterpret_cast<__nv_bfloat16 *>(base) + idx) = (ua >> 16) | (ub & 0xFFFF0000u);
   }
 };
 
-// 32-bit mix of (salt, column, observation) (a murmur3-style finaliser).
+// 32 random bits from (salt, column, observation).
 __device__ __forceinline__ uint32_t mix3(uint32_t s, uint32_t c, uint32_t i) {
-  uint32_t h = s * 0x9E3779B9u ^ c * 0x85EBCA6Bu ^ i * 0xC2B2AE35u;
-  h ^= h >> 16; h *= 0x7FEB352Du;
-  h ^= h >> 15; h *= 0x846CA68Bu;
-  h ^= h >> 16;
-  return h;
+  uint32_t h = (i * 0x9E3779B1u) ^ (c * 0x85EBCA77u) ^ (s * 0xC2B2AE3Du);
+  h = (h ^ (h >> 16)) * 0x7FEB352Du;
+  return h ^ (h >> 15);
 }
 
 struct BuildDims {
@@ -77,55 +75,61 @@ struct BuildDims {
   int kc;  // classes per Y staging chunk
 };
 
-// P is float64 in FP64 mode, float32 otherwise.
+// Shared memory (row strides made odd so that lanes reading every other row
+// hit distinct banks): Ps[ob][K|1], Ws[ob][K|1] (P and sqrt(P(1-P)), compute
+// type), Xs[ob][p|1], Ys[ob][(kc*d)|1] (float32).
 template <OpType OT, typename PT>
 __global__ void __launch_bounds__(256) build_operands_kernel(BuildDims D, const float *__restrict__ X,
                                                              const float *__restrict__ Y,
                                                              const PT *__restrict__ P, void *At, void *Ad) {
+  using CT = typename OpStore<OT>::CT;
   extern __shared__ __align__(16) unsigned char smem[];
   const int K = D.K, p = D.p, d = D.d, q = D.q, OB = D.ob;
-  PT *Ps = reinterpret_cast<PT *>(smem);
-  float *Xs = reinterpret_cast<float *>(smem + (((size_t)OB * K * sizeof(PT) + 15) & ~(size_t)15));
-  float *Ys = Xs + (((size_t)OB * p + 3) & ~(size_t)3);
+  const int SP = K | 1, SX = p | 1;
+  CT *Ps = reinterpret_cast<CT *>(smem);
+  CT *Ws = Ps + (size_t)OB * SP;
+  float *Xs = reinterpret_cast<float *>(smem + ((2 * (size_t)OB * SP * sizeof(CT) + 15) & ~(size_t)15));
+  float *Ys = Xs + (((size_t)OB * SX + 3) & ~(size_t)3);
   const int64_t i0 = (int64_t)blockIdx.x * OB;
   const int nobs = (int)min((int64_t)OB, D.N - i0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
 
-  for (int e = tid; e < nobs * K; e += blockDim.x) Ps[e] = P[i0 * K + e];
-  for (int e = tid; e < nobs * p; e += blockDim.x) Xs[e] = X[i0 * p + e];
+  for (int e = tid; e < OB * K; e += blockDim.x) {
+    const int r = e / K, k = e % K;
+    const CT pk = r < nobs ? (CT)P[i0 * K + e] : (CT)0;
+    const CT w = pk * ((CT)1 - pk);
+    Ps[r * SP + k] = pk;
+    Ws[r * SP + k] = w > (CT)0 ? sqrt(w) : (CT)0;
+  }
+  for (int e = tid; e < OB * p; e += blockDim.x) {
+    const int r = e / p, l = e % p;
+    Xs[r * SX + l] = r < nobs ? X[i0 * p + e] : 0.f;
+  }
 
   for (int k0 = 1; k0 < K; k0 += D.kc) {
     const int k1 = min(K, k0 + D.kc);
+    const int w = (k1 - k0) * d, SY = w | 1;
     __syncthreads();
     if (d) {
-      const int w = (k1 - k0) * d;
-      for (int e = tid; e < nobs * w; e += blockDim.x) {
+      for (int e = tid; e < OB * w; e += blockDim.x) {
         const int r = e / w, c = e % w;
-        Ys[(size_t)r * w + c] = Y[((i0 + r) * K + k0) * d + c];
+        Ys[r * SY + c] = r < nobs ? Y[((i0 + r) * K + k0) * d + c] : 0.f;
       }
     }
     __syncthreads();
-    const int w = (k1 - k0) * d;
     const int ncols = (k1 - k0) * q;
     for (int cc = warp; cc < ncols; cc += nw) {
       const int k = k0 + cc / q, l = cc % q;
       const int64_t c = (int64_t)(k - 1) * q + l;
+      const float *mcol = l < p ? Xs + l : Ys + (k - k0) * d + (l - p);
+      const int mstride = l < p ? SX : SY;
       for (int r = 2 * lane; r < OB; r += 64) {
-        double av[2] = {0.0, 0.0}, dv[2] = {0.0, 0.0};
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int rr = r + h;
-          if (rr < nobs) {
-            const double pk = (double)Ps[(size_t)rr * K + k];
-            const double m = l < p ? (double)Xs[(size_t)rr * p + l] : (double)Ys[(size_t)rr * w + (k - k0) * d + (l - p)];
-            av[h] = pk * m;
-            const double wv = pk * (1.0 - pk);
-            dv[h] = (wv > 0.0 ? sqrt(wv) : 0.0) * m;
-          }
-        }
-        const uint32_t ii = (uint32_t)(i0 + r), cc32 = (uint32_t)c;
-        OpStore<OT>::put(At, c * D.ldn + i0 + r, av[0], av[1], mix3(1u, cc32, ii), mix3(1u, cc32, ii + 1));
-        OpStore<OT>::put(Ad, c * D.ldn + i0 + r, dv[0], dv[1], mix3(2u, cc32, ii), mix3(2u, cc32, ii + 1));
+        const CT m0 = (CT)mcol[r * mstride], m1 = (CT)mcol[(r + 1) * mstride];
+        const CT p0 = Ps[r * SP + k], p1 = Ps[(r + 1) * SP + k];
+        const CT w0 = Ws[r * SP + k], w1 = Ws[(r + 1) * SP + k];
+        const uint32_t ii = (uint32_t)(i0 + r), c32 = (uint32_t)c;
+        OpStore<OT>::put(At, c * D.ldn + i0 + r, p0 * m0, p1 * m1, mix3(1u, c32, ii));
+        OpStore<OT>::put(Ad, c * D.ldn + i0 + r, w0 * m0, w1 * m1, mix3(2u, c32, ii));
       }
     }
   }
@@ -190,65 +194,106 @@ __global__ void __launch_bounds__(256, 1) syrk_f64_kernel(const double *__restri
 }
 
 // ---------------------------------------------------------------------------
-// Z blocks: per (split, class) partial sums of the cross and alpha-alpha terms.
+// Z blocks.  With W_ikj = P_ik (z_ikj - zbar_ij) (a centred, probability
+// weighted Z), the cross and alpha-alpha blocks are
+//   C_X[l][k f + j] = sum_i x_il W_ikj                 (beta_k x alpha)
+//   C_Y[k][l][j]    = sum_i y_ikl W_ikj                (gamma_k x alpha)
+//   A[j1][j2]       = sum_i sum_k W_ikj1 (z_ikj2 - zbar_ij2)
+// Output vector per split: [C_X: p*K*f | C_Y: K*d*f | A: f*f] (k = 0 entries
+// of C_X and C_Y are computed but not used).  A CTA stages a tile of rows
+// (X, Y, Z, P, zbar contiguous in memory), forms W and z - zbar in shared
+// memory and adds the tile to the outputs it owns; grid.y splits the output
+// vector when one CTA cannot own all of it.
 // ---------------------------------------------------------------------------
 
-constexpr int kZRows = 32;
-constexpr int kZSlots = 16;  // outputs per thread (q f + f f <= 4096)
+constexpr int kZSlots = 16;   // outputs per thread
+constexpr int kZThreads = 512;
+
+struct ZDims {
+  int64_t N;
+  int K, p, d, f;
+  int rows;     // rows per tile
+  int nsplit;   // row splits (grid.x)
+  int64_t nzt;  // outputs per split
+};
 
 template <typename T>
-__global__ void __launch_bounds__(256) zblocks_kernel(int64_t N, int K, int p, int d, int f, int nsplit,
-                                                      const float *__restrict__ X, const float *__restrict__ Y,
-                                                      const float *__restrict__ Z, const T *__restrict__ P,
-                                                      const T *__restrict__ zbar, T *__restrict__ out) {
+__global__ void __launch_bounds__(kZThreads) zblocks_kernel(ZDims D, const float *__restrict__ X,
+                                                            const float *__restrict__ Y, const float *__restrict__ Z,
+                                                            const T *__restrict__ P, const T *__restrict__ zbar,
+                                                            T *__restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int q = p + d, nz = q * f + f * f;
-  T *ms = reinterpret_cast<T *>(smem);      // [kZRows][q]
-  T *zs = ms + (size_t)kZRows * q;          // [kZRows][f]
-  T *ws = zs + (size_t)kZRows * f;          // [kZRows]
-  const int s = blockIdx.x, k = blockIdx.y, tid = threadIdx.x;
-  const int64_t r0 = N * s / nsplit, r1 = N * (s + 1) / nsplit;
+  const int K = D.K, p = D.p, d = D.d, f = D.f, R = D.rows;
+  const int Kf = K * f, Kd = K * d;
+  T *Ws = reinterpret_cast<T *>(smem);          // [R][K f]
+  T *Zc = Ws + (size_t)R * Kf;                   // [R][K f]
+  float *Xs = reinterpret_cast<float *>(Zc + (size_t)R * Kf);  // [R][p]
+  float *Ys = Xs + (size_t)R * p;                // [R][K d]
+  const int tid = threadIdx.x;
+  const int64_t r0 = D.N * blockIdx.x / D.nsplit, r1 = D.N * (blockIdx.x + 1) / D.nsplit;
+  const int64_t obase = (int64_t)blockIdx.y * kZThreads * kZSlots;
+  const int64_t nx = (int64_t)p * Kf, ny = (int64_t)Kd * f;
+  // Slot decoding, once: kind (0 C_X, 1 C_Y, 2 A, 3 none), the two operand
+  // offsets inside a staged row, and their row strides.
+  int kind[kZSlots], ou[kZSlots], ov[kZSlots];
+#pragma unroll
+  for (int sl = 0; sl < kZSlots; ++sl) {
+    const int64_t o = obase + tid + (int64_t)sl * blockDim.x;
+    if (o >= D.nzt) { kind[sl] = 3; ou[sl] = ov[sl] = 0; }
+    else if (o < nx) { kind[sl] = 0; ou[sl] = (int)(o / Kf); ov[sl] = (int)(o % Kf); }
+    else if (o < nx + ny) {
+      const int e = (int)(o - nx), k = e / (d * f), l = (e / f) % d, j = e % f;
+      kind[sl] = 1; ou[sl] = k * d + l; ov[sl] = k * f + j;
+    } else {
+      const int e = (int)(o - nx - ny);
+      kind[sl] = 2; ou[sl] = e / f; ov[sl] = e % f;
+    }
+  }
   T acc[kZSlots];
 #pragma unroll
   for (int sl = 0; sl < kZSlots; ++sl) acc[sl] = 0;
-  for (int64_t rb = r0; rb < r1; rb += kZRows) {
-    const int nr = (int)min((int64_t)kZRows, r1 - rb);
+  for (int64_t rb = r0; rb < r1; rb += R) {
+    const int nr = (int)min((int64_t)R, r1 - rb);
     __syncthreads();
-    for (int e = tid; e < nr * q; e += blockDim.x) {
-      const int r = e / q, l = e % q;
+    for (int e = tid; e < nr * K; e += blockDim.x) {
+      const int r = e / K, k = e % K;
       const int64_t i = rb + r;
-      ms[e] = l < p ? (T)X[i * p + l] : (T)Y[(i * K + k) * d + (l - p)];
+      const T pk = P[i * K + k];
+      const float *z = Z + i * Kf + k * f;
+      const T *zb = zbar + i * f;
+      T *zc = Zc + r * Kf + k * f, *ws = Ws + r * Kf + k * f;
+      for (int j = 0; j < f; ++j) {
+        const T c = (T)z[j] - zb[j];
+        zc[j] = c;
+        ws[j] = pk * c;
+      }
     }
-    for (int e = tid; e < nr * f; e += blockDim.x) {
-      const int r = e / f, j = e % f;
-      const int64_t i = rb + r;
-      zs[e] = (T)Z[(i * K + k) * f + j] - zbar[i * f + j];
-    }
-    for (int r = tid; r < nr; r += blockDim.x) ws[r] = P[(rb + r) * K + k];
+    for (int e = tid; e < nr * p; e += blockDim.x) Xs[e] = X[rb * p + e];
+    for (int e = tid; e < nr * Kd; e += blockDim.x) Ys[e] = Y[rb * Kd + e];
     __syncthreads();
 #pragma unroll
     for (int sl = 0; sl < kZSlots; ++sl) {
-      const int o = tid + sl * blockDim.x;
-      if (o < nz) {
-        T a = 0;
-        if (o < q * f) {
-          if (k > 0) {
-            const int l = o / f, j = o % f;
-            for (int r = 0; r < nr; ++r) a = fma(ws[r] * ms[r * q + l], zs[r * f + j], a);
-          }
-        } else {
-          const int e = o - q * f, j1 = e / f, j2 = e % f;
-          for (int r = 0; r < nr; ++r) a = fma(ws[r] * zs[r * f + j1], zs[r * f + j2], a);
-        }
-        acc[sl] += a;
+      T a = 0;
+      if (kind[sl] == 0) {
+        const float *u = Xs + ou[sl];
+        const T *v = Ws + ov[sl];
+        for (int r = 0; r < nr; ++r) a = fma((T)u[r * p], v[r * Kf], a);
+      } else if (kind[sl] == 1) {
+        const float *u = Ys + ou[sl];
+        const T *v = Ws + ov[sl];
+        for (int r = 0; r < nr; ++r) a = fma((T)u[r * Kd], v[r * Kf], a);
+      } else if (kind[sl] == 2) {
+        for (int r = 0; r < nr; ++r)
+          for (int k = 0; k < K; ++k) a = fma(Ws[r * Kf + k * f + ou[sl]], Zc[r * Kf + k * f + ov[sl]], a);
       }
+      acc[sl] += a;
     }
   }
-  T *o = out + ((int64_t)s * K + k) * nz;
+  T *o = out + (int64_t)blockIdx.x * D.nzt;
 #pragma unroll
   for (int sl = 0; sl < kZSlots; ++sl) {
-    const int oo = tid + sl * blockDim.x;
-    if (oo < nz) o[oo] = acc[sl];
+    const int64_t oo = obase + tid + (int64_t)sl * blockDim.x;
+    if (oo < D.nzt) o[oo] = acc[sl];
   }
 }
 
@@ -263,9 +308,9 @@ __global__ void assemble_kernel(Shape S, const CT *__restrict__ mainp, int mspli
   const int64_t n = S.n;
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t c = blockIdx.y + (int64_t)gridDim.y * blockIdx.z;
-  if (r >= n || c >= n || r < c) return;
+  if (r >= n || c >= n || r < c) return;  // (r, c) in the lower triangle; both mirror entries are written
   const int q = S.q, f = S.f, K = S.K;
-  const int nz = q * f + f * f;
+  const int64_t nx = (int64_t)S.p * K * f, ny = (int64_t)K * S.d * f, nzt = nx + ny + (int64_t)f * f;
   double v = 0.0;
   if (r < S.mc) {
     int kr, lr, kc, lc;
@@ -286,16 +331,16 @@ __global__ void assemble_kernel(Shape S, const CT *__restrict__ mainp, int mspli
     const int j = (int)(r - S.mc);
     int kc, lc;
     theta_class_local(S, c, kc, lc);
-    for (int s = 0; s < zsplit; ++s) v += (double)zp[((int64_t)s * K + kc) * nz + lc * f + j];
+    const int64_t off = lc < S.p ? (int64_t)lc * K * f + (int64_t)kc * f + j
+                                 : nx + (int64_t)kc * S.d * f + (int64_t)(lc - S.p) * f + j;
+    for (int s = 0; s < zsplit; ++s) v += (double)zp[s * nzt + off];
   } else {
     const int j1 = (int)(r - S.mc), j2 = (int)(c - S.mc);
-    for (int k = 0; k < K; ++k) {
-      double vk = 0.0;
-      for (int s = 0; s < zsplit; ++s) vk += (double)zp[((int64_t)s * K + k) * nz + q * f + j1 * f + j2];
-      v += vk;
-    }
+    const int64_t off = nx + ny + (int64_t)j1 * f + j2;
+    for (int s = 0; s < zsplit; ++s) v += (double)zp[s * nzt + off];
   }
   F[c * n + r] = v;
+  F[r * n + c] = v;
 }
 
 __global__ void export_hessian_kernel(int64_t n, const double *__restrict__ F, double *__restrict__ H) {
@@ -319,11 +364,11 @@ cudaError_t launch_build_operands(const Shape &s, OpType t, const float *X, cons
                                   void *Ad, int64_t ldn, cudaStream_t st) {
   BuildDims D;
   D.N = s.N; D.ldn = ldn; D.K = s.K; D.p = s.p; D.d = s.d; D.q = s.q;
-  const size_t psz = t == OpType::F64 ? 8 : 4;
+  const size_t csz = t == OpType::F64 ? 8 : 4;
   D.ob = 64;
   auto smem_for = [&](int ob, int kc) {
-    return (((size_t)ob * s.K * psz + 15) & ~(size_t)15) + (((size_t)ob * s.p + 3) & ~(size_t)3) * 4 +
-           (size_t)ob * kc * s.d * 4;
+    return ((2 * (size_t)ob * (s.K | 1) * csz + 15) & ~(size_t)15) + (((size_t)ob * (s.p | 1) + 3) & ~(size_t)3) * 4 +
+           (size_t)ob * ((kc * s.d) | 1) * 4;
   };
   D.kc = s.K - 1;
   while (D.kc > 1 && smem_for(D.ob, D.kc) > 160 * 1024) D.kc = (D.kc + 1) / 2;
@@ -363,23 +408,45 @@ cudaError_t launch_syrk_f64(const double *At, int64_t ldn, int64_t N, const int2
   return cudaGetLastError();
 }
 
+int64_t zblocks_outputs(const Shape &s) {
+  return (int64_t)s.p * s.K * s.f + (int64_t)s.K * s.d * s.f + (int64_t)s.f * s.f;
+}
+
+size_t zblocks_smem(const Shape &s, int rows, bool fp64) {
+  const size_t tsz = fp64 ? 8 : 4;
+  return (size_t)rows * (2 * (size_t)s.K * s.f * tsz + ((size_t)s.p + (size_t)s.K * s.d) * 4);
+}
+
+int zblocks_rows(const Shape &s, bool fp64) {
+  int rows = 32;
+  while (rows > 1 && zblocks_smem(s, rows, fp64) > 110 * 1024) rows /= 2;
+  return rows;
+}
+
 cudaError_t launch_zblocks(const Shape &s, bool fp64, const float *X, const float *Y, const float *Z, const void *P,
                            const void *zbar, int nsplit, void *out, cudaStream_t st) {
-  const int nz = s.q * s.f + s.f * s.f;
-  if (nz > 256 * kZSlots) return cudaErrorInvalidValue;
-  const size_t tsz = fp64 ? 8 : 4;
-  const size_t smem = ((size_t)kZRows * (s.q + s.f) + kZRows) * tsz;
-  dim3 grid(nsplit, s.K);
+  ZDims D;
+  D.N = s.N; D.K = s.K; D.p = s.p; D.d = s.d; D.f = s.f;
+  D.rows = zblocks_rows(s, fp64);
+  D.nsplit = nsplit;
+  D.nzt = zblocks_outputs(s);
+  const size_t smem = zblocks_smem(s, D.rows, fp64);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  const int chunks = (int)((D.nzt + (int64_t)kZThreads * kZSlots - 1) / ((int64_t)kZThreads * kZSlots));
+  dim3 grid(nsplit, chunks);
+  cudaError_t e;
   if (fp64) {
-    zblocks_kernel<double><<<grid, 256, smem, st>>>(s.N, s.K, s.p, s.d, s.f, nsplit, X, Y, Z,
-                                                    reinterpret_cast<const double *>(P),
-                                                    reinterpret_cast<const double *>(zbar),
-                                                    reinterpret_cast<double *>(out));
+    if ((e = cudaFuncSetAttribute(zblocks_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+      return e;
+    zblocks_kernel<double><<<grid, kZThreads, smem, st>>>(D, X, Y, Z, reinterpret_cast<const double *>(P),
+                                                          reinterpret_cast<const double *>(zbar),
+                                                          reinterpret_cast<double *>(out));
   } else {
-    zblocks_kernel<float><<<grid, 256, smem, st>>>(s.N, s.K, s.p, s.d, s.f, nsplit, X, Y, Z,
-                                                   reinterpret_cast<const float *>(P),
-                                                   reinterpret_cast<const float *>(zbar),
-                                                   reinterpret_cast<float *>(out));
+    if ((e = cudaFuncSetAttribute(zblocks_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+      return e;
+    zblocks_kernel<float><<<grid, kZThreads, smem, st>>>(D, X, Y, Z, reinterpret_cast<const float *>(P),
+                                                         reinterpret_cast<const float *>(zbar),
+                                                         reinterpret_cast<float *>(out));
   }
   return cudaGetLastError();
 }

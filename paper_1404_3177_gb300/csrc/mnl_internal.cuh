@@ -65,7 +65,7 @@ struct PassIO {
   const double *tscale;  // device scalar (used when delta != nullptr)
   void *P;               // [N][K] T, FULL mode only
   void *zbar;            // [N][f] T, FULL mode only
-  double *partials;      // [grid][2 + nout] (FULL) or [grid][2] (loglik only)
+  double *partials;      // [grid][2 + n] (FULL) or [grid][2] (loglik only)
 };
 
 // Configuration of the fused utility/softmax/log-likelihood/gradient pass.
@@ -99,7 +99,7 @@ struct TileLists {
   int nmain, nband;
   int2 *main;      // all lower-triangle tiles, index ti(ti+1)/2 + tj
   int2 *band;      // tiles meeting a diagonal class block
-  int *band_of;    // [2 * ntiles1d]: band index of (ti, ti) at 2ti, of (ti, ti-1) at 2ti+1, or -1
+  int *band_of;    // [nt1d][nt1d]: index in `band` of tile (ti, tj), or -1
 };
 
 // FP64 CUDA-core SYRK: out[(s * ntiles + t)][128][128] = sum over split s of At[a] At[b]^T.
@@ -117,15 +117,14 @@ cudaError_t make_tc_plan(OpType t, const void *At, int64_t rows_pad, int64_t ldn
 cudaError_t launch_syrk_tc(OpType t, const TcPlan &pl, const int2 *tiles, int ntiles, float *out, int *err,
                            cudaStream_t st);
 
-// Z blocks (FP32 or FP64 accumulation), per class k = 0..K-1 and N split:
-//   cross_k  = sum_i P_ik m_ik (z_ik - zbar_i)^T        [q][f]  (k >= 1)
-//   aa_k     = sum_i P_ik (z_ik - zbar_i)(z_ik - zbar_i)^T [f][f] (lower)
-// out[(s * K + k)][q*f + f*f]
+// Z blocks (FP32 or FP64 accumulation) per observation split s:
+// out[s][zblocks_outputs()] = [C_X: p*K*f | C_Y: K*d*f | A: f*f] (see hessian.cu).
+int64_t zblocks_outputs(const Shape &s);
 cudaError_t launch_zblocks(const Shape &s, bool fp64, const float *X, const float *Y, const float *Z, const void *P,
                            const void *zbar, int nsplit, void *out, cudaStream_t st);
 
-// Assemble F = -H (n x n, column-major, lower triangle and diagonal) from the
-// contraction partials.  main/band partials are FP32 (tensor path) or FP64.
+// Assemble F = -H (n x n, column-major, both triangles) from the contraction
+// partials.  main/band partials are FP32 (tensor path) or FP64.
 struct AssembleIO {
   const void *main_part; int main_split;
   const void *band_part; int band_split;
@@ -138,11 +137,21 @@ cudaError_t launch_assemble(const Shape &s, const AssembleIO &io, int nmain, dou
 // Mirror the lower triangle of F into a full symmetric matrix H = -F (column-major).
 cudaError_t launch_export_hessian(int64_t n, const double *F, double *H, cudaStream_t st);
 
-// Blocked FP64 Cholesky of F (lower, column-major, ld = n) in place, then
-// solve F x = b.  status |= 4 when a pivot is not positive or not finite.
-cudaError_t launch_cholesky(int64_t n, double *F, int *status, cudaStream_t st);
-cudaError_t launch_cholesky_solve(int64_t n, const double *L, const double *b, double *x, const int *status,
-                                  cudaStream_t st);
+// Blocked FP64 Cholesky of F (lower, column-major, ld = n) in place (dinv[j] =
+// 1/L_jj), then solve F x = b.  status |= 4 when a pivot is not positive or
+// not finite.
+int cholesky_launches(int64_t n);
+cudaError_t launch_cholesky(int64_t n, double *F, double *dinv, int *status, cudaStream_t st);
+cudaError_t launch_cholesky_solve(int64_t n, const double *L, const double *dinv, const double *b, double *x,
+                                  const int *status, cudaStream_t st, int *launches);
+// Mixed solve: float32 factor of F (F kept intact, both triangles) and float64
+// iterative refinement of F delta = g.  status |= 8 when the float32 factor
+// fails, 16 when the refinement does not converge (use the FP64 path then).
+// rwork: mixed_solve_rwork_doubles(n); fwork: n floats; ref: 4 doubles.
+size_t mixed_solve_rwork_doubles(int64_t n);
+cudaError_t launch_mixed_solve(int64_t n, const double *F, float *F32, float *dinv32, const double *g, double *delta,
+                               double *rwork, float *fwork, double *ref, int *status, int iters, cudaStream_t st,
+                               int *launches);
 
 // Small FP64 vector kernels.
 cudaError_t launch_axpy_theta(int64_t n, double *theta, const double *delta, const double *tscale, double *scal_out,

@@ -63,7 +63,7 @@ extern "C" MNL_API int mnl_loglik_grad_noalloc(const mnl_dims *dims, const mnl_d
   PassPlan pl = plan_pass(S, fp64, true, nsm);
   if (!pl.ok) return MNL_ERR_UNSUPPORTED;
   // Fit the CTA partials into the fixed scratch: fewer CTAs when needed.
-  const size_t per_cta = 2 + (size_t)S.nout;
+  const size_t per_cta = 2 + (size_t)S.n;
   if (2 + per_cta > kScratchDoubles) return MNL_ERR_UNSUPPORTED;
   const size_t max_grid = (kScratchDoubles - 2) / per_cta;
   if ((size_t)pl.grid > max_grid) pl.grid = (int)max_grid;

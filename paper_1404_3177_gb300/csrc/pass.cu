@@ -251,7 +251,8 @@ __global__ void __launch_bounds__(512) pass_kernel(PassDims D, PassIO io) {
     red[warp * 2 + 1] = labs.value();
   }
   __syncthreads();
-  double *out = io.partials + (int64_t)blockIdx.x * (FULL ? 2 + D.nout : 2);
+  // Partials row: [l, sum |l_i|, g (theta order: class coefficients, then alpha)].
+  double *out = io.partials + (int64_t)blockIdx.x * (FULL ? 2 + D.mc + f : 2);
   if (tid == 0) {
     double a = 0.0, b = 0.0;
     for (int w = 0; w < nwarps; ++w) { a += red[w * 2]; b += red[w * 2 + 1]; }
@@ -259,40 +260,50 @@ __global__ void __launch_bounds__(512) pass_kernel(PassDims D, PassIO io) {
     out[1] = b;
   }
   if (FULL) {
+    // alpha: this CTA's K partial sums per generic column, added over k in fixed order
+    double *az = reinterpret_cast<double *>(Xs);  // the tile area is free now (>= K f doubles)
+    __syncthreads();
 #pragma unroll
     for (int sl = 0; sl < NPT; ++sl) {
       const int64_t o = tid + (int64_t)sl * blockDim.x;
-      if (o < D.nout) out[2 + o] = acc[sl].value();
+      if (o < D.mc) out[2 + o] = acc[sl].value();
+      else if (o < D.nout) az[o - D.mc] = acc[sl].value();
+    }
+    __syncthreads();
+    for (int j = tid; j < f; j += blockDim.x) {
+      double sa = 0.0;
+      for (int k = 0; k < K; ++k) sa += az[k * f + j];
+      out[2 + D.mc + j] = sa;
     }
   }
 }
 
-// Fixed-order float64 reduction of the CTA partials.
-__global__ void pass_reduce_kernel(PassDims D, int grid, int full, const double *__restrict__ part,
-                                   double *__restrict__ scal, double *__restrict__ grad) {
-  const int64_t stride = full ? 2 + D.nout : 2;
-  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int g = 0; g < grid; ++g) { a += part[g * stride]; b += part[g * stride + 1]; }
-    scal[0] = a;
-    scal[1] = b;
-  }
-  if (!full) return;
+// Fixed-order float64 reduction of the CTA partials: one thread per output,
+// four interleaved accumulators (so four loads are in flight), added in a
+// fixed order at the end.
+__global__ void __launch_bounds__(128) pass_reduce_kernel(PassDims D, int grid, int full,
+                                                          const double *__restrict__ part, double *__restrict__ scal,
+                                                          double *__restrict__ grad) {
   const int64_t n = D.mc + D.f;
-  if (o >= n) return;
-  double s = 0.0;
-  if (o < D.mc) {
-    for (int g = 0; g < grid; ++g) s += part[g * stride + 2 + o];
-  } else {
-    const int j = (int)(o - D.mc);
-    for (int k = 0; k < D.K; ++k) {
-      double sk = 0.0;
-      for (int g = 0; g < grid; ++g) sk += part[g * stride + 2 + D.mc + (int64_t)k * D.f + j];
-      s += sk;
-    }
+  const int64_t stride = full ? 2 + n : 2;
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.x == 0 && threadIdx.x < 2) {
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    int g = 0;
+    for (; g + 4 <= grid; g += 4)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s[u] += part[(g + u) * stride + threadIdx.x];
+    for (; g < grid; ++g) s[0] += part[g * stride + threadIdx.x];
+    scal[threadIdx.x] = (s[0] + s[1]) + (s[2] + s[3]);
   }
-  grad[o] = s;
+  if (!full || o >= n) return;
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  int g = 0;
+  for (; g + 4 <= grid; g += 4)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s[u] += part[(g + u) * stride + 2 + o];
+  for (; g < grid; ++g) s[0] += part[g * stride + 2 + o];
+  grad[o] = (s[0] + s[1]) + (s[2] + s[3]);
 }
 
 __global__ void validate_kernel(int64_t N, int K, int p, int d, int f, const float *X, const float *Y, const float *Z,
@@ -395,7 +406,7 @@ cudaError_t launch_pass_reduce(const Shape &s, int grid, bool full, const double
                                double *grad, cudaStream_t st) {
   const PassDims D = dims_of(s, 1);
   const int64_t n = full ? s.n : 1;
-  const int threads = 256;
+  const int threads = 128;
   const int blocks = (int)((n + threads - 1) / threads);
   pass_reduce_kernel<<<blocks, threads, 0, st>>>(D, grid, full ? 1 : 0, partials, scal, grad);
   return cudaGetLastError();

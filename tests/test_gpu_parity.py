@@ -281,3 +281,36 @@ def test_unsupported_requests(MNL):
     with pytest.raises(nat.MnlError) as e:
         nat.mnl_create(nat.mnl_dims(10, 4, 2, 1, 0, 1), None, nat.MNL_BF16, 0)
     assert e.value.status == nat.MNL_ERR_UNSUPPORTED
+
+
+# ---------------------------------------------------------------------------
+# Newton solve: float64 Cholesky vs float32 factor + float64 refinement
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16"])
+def test_mixed_and_fp64_solves_agree(MNL, prec):
+    prob = s1()
+    steps = {}
+    for solve in ("fp64", "mixed"):
+        with MNL(**dev(prob), precision=prec, solve=solve) as m:
+            th = torch.zeros(m.n_theta, dtype=torch.float64, device="cuda")
+            info = m.newton_step(th)
+            steps[solve] = (th.cpu().numpy(), info)
+    a, ia = steps["fp64"]
+    b, ib = steps["mixed"]
+    assert ia["solve_mode"] == 1 and ib["solve_mode"] == 2 and ib["fallback"] == 0 and ib["refine_steps"] >= 1
+    assert np.abs(a - b).max() <= 1e-10 * np.abs(a).max(), np.abs(a - b).max() / np.abs(a).max()
+
+
+def test_mixed_solve_falls_back_to_fp64_on_ill_conditioned_design(MNL):
+    prob = datagen.make_problem(3000, 3, 3, 0, 0, 9, theta_sd=0.3)
+    rng = np.random.default_rng(4)
+    prob.X[:, 2] = (prob.X[:, 1] + 1e-5 * rng.standard_normal(prob.N)).astype(np.float32)  # cond(-H) ~ 1e10
+    out = {}
+    for solve in ("fp64", "mixed"):
+        with MNL(**dev(prob), precision="fp64", solve=solve) as m:
+            th = torch.zeros(m.n_theta, dtype=torch.float64, device="cuda")
+            info = m.newton_step(th)
+            out[solve] = (th.cpu().numpy(), info)
+    assert out["mixed"][1]["fallback"] == 1
+    assert np.array_equal(out["fp64"][0], out["mixed"][0])
