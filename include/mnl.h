@@ -222,6 +222,63 @@ MNL_API int mnl_set_solve(mnl_handle *h, int mode);
 /* Free the handle and every device buffer it owns (NULL is a no-op). */
 MNL_API int mnl_destroy(mnl_handle *h);
 
+/* ------------------------------------------------------------------------
+ * Batched fits: many independent problems of uneven N, K, p, d, f advanced
+ * together (Sec. 3.1 Newton-Raphson with step halving, per problem).  Every
+ * Newton phase is one grouped kernel launch over all problems still
+ * iterating; one iteration is captured once as a CUDA graph and replayed.
+ * ------------------------------------------------------------------------ */
+typedef struct mnl_batch mnl_batch;
+
+typedef struct mnl_batch_problem_info {
+  int32_t status;      /* MNL_OK (a tolerance was met), MNL_MAXITER, or an MNL_ERR_* */
+  int32_t stop_reason; /* MNL_STOP_* (0 after an error)                          */
+  int32_t iters;       /* Newton iterations taken                                 */
+  int32_t ls_evals;    /* log-likelihood evaluations in line searches             */
+  double loglik;       /* l at the returned theta                                 */
+  double grad_inf;     /* max|g| at the last gradient evaluation                  */
+} mnl_batch_problem_info;
+
+typedef struct mnl_batch_info {
+  mnl_batch_problem_info *problems; /* HOST [count] or NULL, filled by mnl_batch_fit */
+  int32_t iterations;  /* Newton iterations of the slowest problem      */
+  int32_t converged;   /* problems that met a tolerance                 */
+  int32_t failed;      /* problems that ended with an error             */
+  int32_t pass_rows;   /* observations per tile of the grouped pass (autotuned) */
+  double t_total_ms;   /* wall time of mnl_batch_fit                    */
+  double t_graph_ms;   /* device time of the replayed iteration graphs  */
+} mnl_batch_info;
+
+/* Create a batch of `count` problems.
+ *   dims[i], data[i]  as for mnl_create, DEVICE pointers that must stay valid
+ *                     and unchanged until mnl_batch_destroy (not validated).
+ *   precision         as for mnl_create; the Newton solves run per problem in
+ *                     one CTA (float32 factor + float64 refinement for TF32 /
+ *                     BF16, float64 for MNL_FP64).
+ *   stream            cudaStream_t (as void*): mnl_batch_fit orders its work
+ *                     after, and before, the caller's work on this stream (it
+ *                     runs on an internal stream so it can capture a graph).
+ * Allocates every workspace (one arena) and autotunes the pass tile height
+ * (timed once; cached per batch shape in the process and, if the environment
+ * variable MNL_TUNE_CACHE names a file, in that file).  Limits: n_theta <= 1400
+ * per problem, K <= 256; else MNL_ERR_UNSUPPORTED. */
+MNL_API int mnl_batch_create(int count, const mnl_dims *dims, const mnl_data *data, int precision, void *stream,
+                             mnl_batch **out);
+
+/* Total number of coefficients; offsets (HOST [count], may be NULL) receives
+ * where problem i's coefficients start in the packed theta vector. */
+MNL_API int64_t mnl_batch_num_params(const mnl_batch *b, int64_t *offsets);
+
+/* Fit every problem from the start values in theta (DEVICE, packed, float64,
+ * mnl_batch_num_params entries; estimates are written back in place).
+ * opts: as for mnl_fit (NULL: defaults).  info (HOST, may be NULL).
+ * Returns MNL_OK when every problem met a tolerance, else the status of the
+ * first problem that ended with an error, else MNL_MAXITER; per-problem
+ * results are in info->problems.  Synchronises. */
+MNL_API int mnl_batch_fit(mnl_batch *b, const mnl_fit_opts *opts, double *theta, mnl_batch_info *info);
+
+MNL_API int mnl_batch_destroy(mnl_batch *b);
+
 /* Log-likelihood and gradient, as mnl_loglik_grad, without allocating any
  * device memory.  The paper has no counterpart: this is for callers that
  * cannot call cudaMalloc when they need l and g - code whose device memory

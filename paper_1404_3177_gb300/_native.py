@@ -32,7 +32,8 @@ MNL_STOP_GTOL, MNL_STOP_FTOL, MNL_STOP_STEPTOL, MNL_STOP_MAXITER = 1, 2, 3, 4
 EXPORTS = (
     "mnl_num_params", "mnl_status_string", "mnl_workspace_bytes", "mnl_fit_opts_default", "mnl_create",
     "mnl_upload", "mnl_loglik_grad", "mnl_hessian", "mnl_newton_step", "mnl_fit", "mnl_destroy",
-    "mnl_loglik_grad_noalloc", "mnl_set_solve",
+    "mnl_loglik_grad_noalloc", "mnl_set_solve", "mnl_batch_create", "mnl_batch_num_params", "mnl_batch_fit",
+    "mnl_batch_destroy",
 )
 
 MNL_SOLVE_AUTO, MNL_SOLVE_FP64, MNL_SOLVE_MIXED = 0, 1, 2
@@ -70,6 +71,17 @@ class mnl_fit_info(C.Structure):
                 ("loglik", C.c_double), ("grad_inf", C.c_double), ("dloglik", C.c_double),
                 ("step_rel", C.c_double), ("t_total_ms", C.c_double), ("t_pass_ms", C.c_double),
                 ("t_hess_ms", C.c_double), ("t_chol_ms", C.c_double), ("t_ls_ms", C.c_double)]
+
+
+class mnl_batch_problem_info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("stop_reason", C.c_int32), ("iters", C.c_int32), ("ls_evals", C.c_int32),
+                ("loglik", C.c_double), ("grad_inf", C.c_double)]
+
+
+class mnl_batch_info(C.Structure):
+    _fields_ = [("problems", C.POINTER(mnl_batch_problem_info)), ("iterations", C.c_int32),
+                ("converged", C.c_int32), ("failed", C.c_int32), ("pass_rows", C.c_int32),
+                ("t_total_ms", C.c_double), ("t_graph_ms", C.c_double)]
 
 
 def struct_dict(s: C.Structure) -> dict:
@@ -118,6 +130,14 @@ def load() -> C.CDLL:
         lib.mnl_fit.argtypes = [vp, C.POINTER(mnl_fit_opts), vp, C.POINTER(mnl_fit_info)]
         lib.mnl_destroy.restype = i32
         lib.mnl_destroy.argtypes = [vp]
+        lib.mnl_batch_create.restype = i32
+        lib.mnl_batch_create.argtypes = [i32, C.POINTER(mnl_dims), C.POINTER(mnl_data), i32, vp, C.POINTER(vp)]
+        lib.mnl_batch_num_params.restype = i64
+        lib.mnl_batch_num_params.argtypes = [vp, C.POINTER(C.c_int64)]
+        lib.mnl_batch_fit.restype = i32
+        lib.mnl_batch_fit.argtypes = [vp, C.POINTER(mnl_fit_opts), vp, C.POINTER(mnl_batch_info)]
+        lib.mnl_batch_destroy.restype = i32
+        lib.mnl_batch_destroy.argtypes = [vp]
         lib.mnl_set_solve.restype = i32
         lib.mnl_set_solve.argtypes = [vp, i32]
         lib.mnl_loglik_grad_noalloc.restype = i32
@@ -212,3 +232,33 @@ def mnl_loglik_grad_noalloc(dims: mnl_dims, data: mnl_data, precision: int, thet
                                         C.c_void_p(loglik_ptr), C.c_void_p(grad_ptr), C.c_void_p(P_ptr),
                                         C.c_void_p(zbar_ptr) if zbar_ptr else None, C.c_void_p(stream or 0))
     _check(rc, "mnl_loglik_grad_noalloc")
+
+
+def mnl_batch_create(dims: list, data: list, precision: int, stream: int | None) -> int:
+    n = len(dims)
+    da = (mnl_dims * n)(*dims)
+    dd = (mnl_data * n)(*data)
+    h = C.c_void_p()
+    _check(load().mnl_batch_create(n, da, dd, precision, C.c_void_p(stream or 0), C.byref(h)), "mnl_batch_create")
+    return h.value
+
+
+def mnl_batch_num_params(handle: int, count: int):
+    offs = (C.c_int64 * count)()
+    total = load().mnl_batch_num_params(C.c_void_p(handle), offs)
+    return int(total), [int(v) for v in offs]
+
+
+def mnl_batch_fit(handle: int, opts: mnl_fit_opts | None, theta_ptr: int, count: int):
+    probs = (mnl_batch_problem_info * count)()
+    info = mnl_batch_info()
+    info.problems = probs
+    rc = load().mnl_batch_fit(C.c_void_p(handle), C.byref(opts) if opts is not None else None,
+                              C.c_void_p(theta_ptr), C.byref(info))
+    if rc not in (MNL_OK, MNL_MAXITER) and info.iterations == 0:
+        raise MnlError(rc, "mnl_batch_fit")
+    return rc, info, [struct_dict(p) for p in probs]
+
+
+def mnl_batch_destroy(handle: int) -> None:
+    _check(load().mnl_batch_destroy(C.c_void_p(handle)), "mnl_batch_destroy")

@@ -115,3 +115,58 @@ class MNL:
 
     def __exit__(self, *a):
         self.close()
+
+
+class MNLBatch:
+    """Many independent problems fitted together (one grouped launch per Newton phase).
+
+    ``problems`` is a list of dicts with CUDA tensors X, Y, Z, choice (None for
+    an empty block) and K; they must outlive this object.
+    """
+
+    def __init__(self, problems, *, precision="bf16", stream=None):
+        self.precision = nat.PRECISIONS[precision]
+        self._stream = (stream or torch.cuda.current_stream()).cuda_stream
+        dims, data, keep = [], [], []
+        for pr in problems:
+            X, Y, Z, c = pr.get("X"), pr.get("Y"), pr.get("Z"), pr["choice"]
+            K = Y.shape[1] if Y is not None else Z.shape[1] if Z is not None else pr["K"]
+            dims.append(nat.mnl_dims(c.shape[0], K, X.shape[1] if X is not None else 0,
+                                     Y.shape[2] if Y is not None else 0, Z.shape[2] if Z is not None else 0, 0))
+            data.append(nat.mnl_data(_ptr(X), _ptr(Y), _ptr(Z), _ptr(c)))
+            keep.append((X, Y, Z, c))
+        self._keep = keep
+        self.count = len(dims)
+        self.h = nat.mnl_batch_create(dims, data, self.precision, self._stream)
+        self.n_total, self.offsets = nat.mnl_batch_num_params(self.h, self.count)
+        self.sizes = [nat.mnl_num_params(d) for d in dims]
+
+    def fit(self, theta0=None, **opts):
+        """Returns (packed float64 theta, summary dict, per-problem dicts, status)."""
+        o = nat.mnl_fit_opts_default()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        th = torch.zeros(self.n_total, dtype=torch.float64, device="cuda") if theta0 is None else theta0.clone()
+        rc, info, per = nat.mnl_batch_fit(self.h, o, th.data_ptr(), self.count)
+        summary = {k: getattr(info, k) for k, _ in info._fields_ if k != "problems"}
+        return th, summary, per, rc
+
+    def split(self, theta):
+        return [theta[o:o + n] for o, n in zip(self.offsets, self.sizes)]
+
+    def close(self):
+        if getattr(self, "h", None):
+            nat.mnl_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

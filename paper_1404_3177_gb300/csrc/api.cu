@@ -40,7 +40,9 @@ struct mnl_handle {
   std::vector<int2> h_main, h_band;
   void *main_part, *band_part, *z_part;
   int main_split, band_split, z_split;
-  TcPlan tc_main, tc_band;
+  CUtensorMap *maps;       // device: [0] At, [1] Ad (tensor-core modes)
+  SyrkUnit *units_main, *units_band;
+  int nunits_main, nunits_band, grid_main, grid_band;
   double *F;
   // solve
   int solve_mode;  // MNL_SOLVE_FP64 or MNL_SOLVE_MIXED (resolved)
@@ -139,22 +141,9 @@ Sizes plan_sizes(const mnl_dims &d, int prec_in, bool owned, int nsm, int *main_
     *main_split = simt_split(nmain, *ldn / 16, nsm);
     *band_split = simt_split(*nband, *ldn / 16, nsm);
   } else {
-    // same rule as make_tc_plan (balanced persistent units, >= 8 K-blocks per split)
-    const int bk = prec == MNL_TF32 ? kBkTf32 : kBkBf16;
-    const int kb = (int)(*ldn / bk);
-    auto pick = [&](int ntiles) {
-      int best = 1;
-      double be = -1;
-      const int mx = std::max(1, std::min(16, kb / 8));
-      for (int s = 1; s <= mx; ++s) {
-        const int units = ntiles * s, g = std::min(units, nsm), waves = (units + g - 1) / g;
-        const double eff = (double)units / ((double)g * waves) * (g / (double)nsm);
-        if (eff > be + 0.02) { be = eff; best = s; }
-      }
-      return best;
-    };
-    *main_split = nmain ? pick(nmain) : 1;
-    *band_split = *nband ? pick(*nband) : 1;
+    const int kb = tc_kblocks(prec == MNL_TF32 ? OpType::TF32 : OpType::BF16, *ldn);
+    *main_split = nmain ? tc_pick_split(nmain, kb, nsm) : 1;
+    *band_split = *nband ? tc_pick_split(*nband, kb, nsm) : 1;
   }
   z.main_part = (size_t)(*main_split) * nmain * kTile * kTile * csz;
   z.band_part = (size_t)(*band_split) * (*nband) * kTile * kTile * csz;
@@ -238,10 +227,11 @@ int run_hessian(mnl_handle *h, cudaEvent_t *ev = nullptr) {
       CK(launch_syrk_f64(reinterpret_cast<const double *>(h->Ad), h->ldn, S.N, h->tl.band, h->tl.nband,
                          h->band_split, reinterpret_cast<double *>(h->band_part), h->st));
     } else {
-      CK(launch_syrk_tc(h->op, h->tc_main, h->tl.main, nmain, reinterpret_cast<float *>(h->main_part), h->err, h->st));
+      CK(launch_syrk_tc(h->op, h->maps, h->units_main, h->nunits_main, nullptr, h->grid_main,
+                        reinterpret_cast<float *>(h->main_part), h->err, h->st));
       if ((rc = mark(h, ev ? ev + 1 : nullptr))) return rc;
-      CK(launch_syrk_tc(h->op, h->tc_band, h->tl.band, h->tl.nband, reinterpret_cast<float *>(h->band_part), h->err,
-                        h->st));
+      CK(launch_syrk_tc(h->op, h->maps, h->units_band, h->nunits_band, nullptr, h->grid_band,
+                        reinterpret_cast<float *>(h->band_part), h->err, h->st));
     }
     h->launches += 3;
     if ((rc = mark(h, ev ? ev + 2 : nullptr))) return rc;
@@ -539,10 +529,42 @@ int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *
     return fail(MNL_ERR_CUDA);
   }
   if (!h->fp64 && S.mc > 0) {
-    cudaError_t e = make_tc_plan(h->op, h->At, h->mc_pad, h->ldn, S.N, h->tl.nmain, h->nsm, &h->tc_main);
-    if (e == cudaSuccess) e = make_tc_plan(h->op, h->Ad, h->mc_pad, h->ldn, S.N, h->tl.nband, h->nsm, &h->tc_band);
+    CUtensorMap hm[2];
+    cudaError_t e = encode_operand_map(h->op, h->At, h->mc_pad, h->ldn, &hm[0]);
+    if (e == cudaSuccess) e = encode_operand_map(h->op, h->Ad, h->mc_pad, h->ldn, &hm[1]);
     if (e != cudaSuccess) return fail(cuda_fail(e));
-    if (h->tc_main.nsplit != h->main_split || h->tc_band.nsplit != h->band_split) return fail(MNL_ERR_CUDA);
+    // Units: split-major, so CTAs running at the same time read the same observation range (L2 reuse).
+    const int kb = tc_kblocks(h->op, h->ldn);
+    auto make_units = [&](const std::vector<int2> &tiles, int nsplit, int map) {
+      std::vector<SyrkUnit> u;
+      for (int sp = 0; sp < nsplit; ++sp)
+        for (size_t t = 0; t < tiles.size(); ++t) {
+          SyrkUnit w;
+          w.map = map; w.problem = 0; w.ti = tiles[t].x; w.tj = tiles[t].y;
+          w.kb0 = (int)((int64_t)kb * sp / nsplit);
+          w.kb1 = (int)((int64_t)kb * (sp + 1) / nsplit);
+          w.out_off = ((int64_t)sp * (int64_t)tiles.size() + (int64_t)t) * kTile * kTile;
+          u.push_back(w);
+        }
+      return u;
+    };
+    const std::vector<SyrkUnit> um = make_units(h->h_main, h->main_split, 0);
+    const std::vector<SyrkUnit> ub = make_units(h->h_band, h->band_split, 1);
+    h->nunits_main = (int)um.size();
+    h->nunits_band = (int)ub.size();
+    h->grid_main = std::min(h->nunits_main, h->nsm);
+    h->grid_band = std::min(h->nunits_band, h->nsm);
+    if ((rc = dalloc(h, &h->maps, sizeof(hm))) || (rc = dalloc(h, &h->units_main, um.size() * sizeof(SyrkUnit))) ||
+        (rc = dalloc(h, &h->units_band, ub.size() * sizeof(SyrkUnit))))
+      return fail(rc);
+    if (cudaMemcpy(h->maps, hm, sizeof(hm), cudaMemcpyHostToDevice) != cudaSuccess ||
+        (!um.empty() && cudaMemcpy(h->units_main, um.data(), um.size() * sizeof(SyrkUnit), cudaMemcpyHostToDevice) !=
+                            cudaSuccess) ||
+        (!ub.empty() && cudaMemcpy(h->units_band, ub.data(), ub.size() * sizeof(SyrkUnit), cudaMemcpyHostToDevice) !=
+                            cudaSuccess)) {
+      cudaGetLastError();
+      return fail(MNL_ERR_CUDA);
+    }
   }
   // data
   if (data) {

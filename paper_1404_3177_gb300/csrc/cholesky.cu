@@ -468,6 +468,224 @@ __global__ void vec_absmax_kernel(int64_t n, const double *v, double *out) {
   if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
 }
 
+// ---------------------------------------------------------------------------
+// Batched solves: one CTA factors and solves one problem (n up to a few
+// thousand).  Right-looking Cholesky by panels of W columns: the panel rows
+// are staged in shared memory, warp 0 factors the W x W diagonal block, every
+// thread solves one panel row against it, and the trailing lower triangle
+// takes the rank-W update in 4 x 4 register blocks.  L^T is written to the
+// upper triangle so both triangular solves read contiguous columns.
+// ---------------------------------------------------------------------------
+
+constexpr int kCtaThreads = 256;
+
+template <typename T, int W>
+__device__ bool cta_cholesky(T *__restrict__ A, int64_t n, T *__restrict__ Ps, T *__restrict__ dinv) {
+  __shared__ int bad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) bad = 0;
+  for (int64_t j0 = 0; j0 < n; j0 += W) {
+    const int nb = (int)min((int64_t)W, n - j0);
+    const int64_t m = n - j0;  // panel rows
+    __syncthreads();
+    for (int64_t e = tid; e < m * nb; e += blockDim.x) {
+      const int k = (int)(e / m);
+      const int64_t rr = e % m;
+      Ps[rr * W + k] = A[(j0 + k) * n + j0 + rr];
+    }
+    __syncthreads();
+    if (warp == 0) {  // diagonal block, lane = row
+      for (int c = 0; c < nb; ++c) {
+        T lcc = (T)1;
+        if (lane == c) {
+          const T piv = Ps[c * W + c];
+          if (!(piv > (T)0) || !isfinite(piv)) bad = 1;
+          else lcc = sqrt(piv);
+          Ps[c * W + c] = lcc;
+          dinv[c] = (T)1 / lcc;
+        }
+        __syncwarp();
+        const T ri = dinv[c];
+        if (lane > c && lane < nb) Ps[lane * W + c] *= ri;
+        __syncwarp();
+        if (lane > c && lane < nb) {
+          const T lrc = Ps[lane * W + c];
+          for (int cc = c + 1; cc <= lane; ++cc) Ps[lane * W + cc] -= lrc * Ps[cc * W + c];
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int64_t rr = nb + tid; rr < m; rr += blockDim.x) {  // rows below: solve against the block
+      T x[W];
+#pragma unroll
+      for (int c = 0; c < W; ++c) x[c] = c < nb ? Ps[rr * W + c] : (T)0;
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        if (c < nb) {
+          T v = x[c];
+#pragma unroll
+          for (int t = 0; t < c; ++t) v -= x[t] * Ps[c * W + t];
+          x[c] = v * dinv[c];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < W; ++c)
+        if (c < nb) Ps[rr * W + c] = x[c];
+    }
+    __syncthreads();
+    // panel back to A: L (lower) and L^T (upper)
+    for (int64_t e = tid; e < m * nb; e += blockDim.x) {
+      const int k = (int)(e / m);
+      const int64_t rr = e % m;
+      if (rr >= k) {
+        const T v = Ps[rr * W + k];
+        A[(j0 + k) * n + j0 + rr] = v;
+        A[(j0 + rr) * n + j0 + k] = v;
+      }
+    }
+    // trailing update in 4 x 4 blocks: A[r][c] -= sum_k L[r][k] L[c][k], c <= r
+    const int64_t mt = m - nb;
+    const int64_t nb4 = (mt + 3) / 4;
+    const int64_t nblk = nb4 * (nb4 + 1) / 2;
+    for (int64_t t = tid; t < nblk; t += blockDim.x) {
+      int64_t bi = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+      while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+      while (bi * (bi + 1) / 2 > t) --bi;
+      const int64_t bj = t - bi * (bi + 1) / 2;
+      T acc[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = (T)0;
+      const int64_t r0 = nb + bi * 4, c0 = nb + bj * 4;
+      for (int k = 0; k < nb; ++k) {
+        T a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          a[u] = r0 + u < m ? Ps[(r0 + u) * W + k] : (T)0;
+          b[u] = c0 + u < m ? Ps[(c0 + u) * W + k] : (T)0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int64_t r = r0 + u, c = c0 + v;
+          if (r < m && c < m && r >= c) A[(j0 + c) * n + j0 + r] -= acc[u][v];
+        }
+    }
+    __syncthreads();
+    if (bad) return false;
+  }
+  __syncthreads();
+  return bad == 0;
+}
+
+// x <- (L L^T)^{-1} x for a factor with L^T in the upper triangle; x in shared memory.
+template <typename T, typename V>
+__device__ void cta_chol_solve(const T *__restrict__ A, int64_t n, V *__restrict__ x) {
+  const int tid = threadIdx.x;
+  for (int64_t j = 0; j < n; ++j) {  // forward, one column at a time (n is small)
+    __syncthreads();
+    const V xj = x[j] / (V)A[j * n + j];
+    __syncthreads();
+    if (tid == 0) x[j] = xj;
+    for (int64_t r = j + 1 + tid; r < n; r += blockDim.x) x[r] -= (V)A[j * n + r] * xj;
+  }
+  for (int64_t j = n - 1; j >= 0; --j) {  // backward with U = L^T: column j of U lies above the diagonal
+    __syncthreads();
+    const V xj = x[j] / (V)A[j * n + j];
+    __syncthreads();
+    if (tid == 0) x[j] = xj;
+    for (int64_t r = tid; r < j; r += blockDim.x) x[r] -= (V)A[j * n + r] * xj;
+  }
+  __syncthreads();
+}
+
+__device__ double cta_max_abs(const double *v, int64_t n, double *red) {
+  double m = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(v[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  double r = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, red[w]);
+  __syncthreads();
+  return r;
+}
+
+// One CTA per active problem: delta = F^{-1} g.  MIXED: float32 factor +
+// float64 refinement (stops as in the single-problem mixed solve), falling back
+// to a float64 factor in the same CTA; else float64 factor.  Sets
+// status[b] = MNL_ERR_NOT_PD when -H is not positive definite.
+template <bool MIXED>
+__global__ void __launch_bounds__(kCtaThreads) grouped_chol_solve_kernel(const GroupProblem *__restrict__ probs,
+                                                                         const int *__restrict__ active, int iters,
+                                                                         int *__restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[32];
+  __shared__ float dinv32[32];
+  __shared__ double dinv64[16];
+  const int b = blockIdx.x;
+  if (active[b] == 0) return;
+  const GroupProblem &g = probs[b];
+  const int64_t n = g.n;
+  double *xs = reinterpret_cast<double *>(smem);  // [n] solution work vector
+  double *ds = xs + n;                            // [n] correction
+  unsigned char *panel = smem + (((size_t)2 * n * sizeof(double) + 15) & ~(size_t)15);
+  bool done = false;
+  if (MIXED) {
+    for (int64_t e = threadIdx.x; e < n * n; e += blockDim.x) g.F32[e] = (float)g.F[e];
+    __syncthreads();
+    if (cta_cholesky<float, 32>(g.F32, n, reinterpret_cast<float *>(panel), dinv32)) {
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) xs[i] = g.grad[i];
+      cta_chol_solve<float, double>(g.F32, n, xs);
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) g.delta[i] = xs[i];
+      double prev = cta_max_abs(xs, n, red);
+      int steps = 0;
+      bool ok = false;
+      for (int it = 0; it < iters; ++it) {
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {  // r = g - F delta (float64)
+          double sacc = 0.0;
+          for (int64_t j = 0; j < n; ++j) sacc = fma(g.F[j * n + i], g.delta[j], sacc);
+          ds[i] = g.grad[i] - sacc;
+        }
+        cta_chol_solve<float, double>(g.F32, n, ds);
+        const double dn = cta_max_abs(ds, n, red);
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) xs[i] = g.delta[i] + ds[i];
+        const double xn = cta_max_abs(xs, n, red);
+        ++steps;
+        const bool improving = dn < 0.5 * prev;
+        if (improving || dn <= 1e-12 * xn)
+          for (int64_t i = threadIdx.x; i < n; i += blockDim.x) g.delta[i] = xs[i];
+        __syncthreads();
+        if (dn <= 1e-12 * xn) { ok = true; break; }
+        if (!improving) { ok = dn <= 1e-8 * xn; break; }
+        prev = dn;
+      }
+      if (threadIdx.x == 0) g.scal[kGsRefine] = steps;
+      done = ok;
+    }
+    __syncthreads();
+  }
+  if (!done) {  // float64 factor (and the fallback of the mixed solve)
+    if (!cta_cholesky<double, 16>(g.F, n, reinterpret_cast<double *>(panel), dinv64)) {
+      if (threadIdx.x == 0) status[b] = MNL_ERR_NOT_PD;
+      return;
+    }
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) xs[i] = g.grad[i];
+    cta_chol_solve<double, double>(g.F, n, xs);
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) g.delta[i] = xs[i];
+  }
+}
+
 }  // namespace
 
 int cholesky_launches(int64_t n) { return (int)(3 * ((n + kNb - 1) / kNb) - 2); }
@@ -541,6 +759,33 @@ cudaError_t launch_axpy_theta(int64_t n, double *theta, const double *delta, con
 cudaError_t launch_vec_absmax(int64_t n, const double *v, double *out, cudaStream_t st) {
   const int blocks = (int)std::min<int64_t>(64, (n + 255) / 256);
   vec_absmax_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, st>>>(n, v, out);
+  return cudaGetLastError();
+}
+
+}  // namespace mnl
+
+namespace mnl {
+
+size_t grouped_chol_smem(int64_t nmax) {
+  const size_t vec = (((size_t)2 * nmax * sizeof(double) + 15) & ~(size_t)15);
+  const size_t p32 = (size_t)nmax * 32 * sizeof(float), p64 = (size_t)nmax * 16 * sizeof(double);
+  return vec + std::max(p32, p64);
+}
+
+cudaError_t launch_grouped_chol_solve(bool mixed, const GroupProblem *probs, int nprob, const int *active,
+                                      int iters, int *status, size_t smem, cudaStream_t st) {
+  cudaError_t e;
+  if (mixed) {
+    if ((e = cudaFuncSetAttribute(grouped_chol_solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)))
+      return e;
+    grouped_chol_solve_kernel<true><<<nprob, kCtaThreads, smem, st>>>(probs, active, iters, status);
+  } else {
+    if ((e = cudaFuncSetAttribute(grouped_chol_solve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)))
+      return e;
+    grouped_chol_solve_kernel<false><<<nprob, kCtaThreads, smem, st>>>(probs, active, iters, status);
+  }
   return cudaGetLastError();
 }
 

@@ -79,9 +79,9 @@ struct BuildDims {
 // hit distinct banks): Ps[ob][K|1], Ws[ob][K|1] (P and sqrt(P(1-P)), compute
 // type), Xs[ob][p|1], Ys[ob][(kc*d)|1] (float32).
 template <OpType OT, typename PT>
-__global__ void __launch_bounds__(256) build_operands_kernel(BuildDims D, const float *__restrict__ X,
-                                                             const float *__restrict__ Y,
-                                                             const PT *__restrict__ P, void *At, void *Ad) {
+__device__ __forceinline__ void build_block(const BuildDims &D, const float *__restrict__ X,
+                                            const float *__restrict__ Y, const PT *__restrict__ P, void *At,
+                                            void *Ad, int64_t blk) {
   using CT = typename OpStore<OT>::CT;
   extern __shared__ __align__(16) unsigned char smem[];
   const int K = D.K, p = D.p, d = D.d, q = D.q, OB = D.ob;
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(256) build_operands_kernel(BuildDims D, const 
   CT *Ws = Ps + (size_t)OB * SP;
   float *Xs = reinterpret_cast<float *>(smem + ((2 * (size_t)OB * SP * sizeof(CT) + 15) & ~(size_t)15));
   float *Ys = Xs + (((size_t)OB * SX + 3) & ~(size_t)3);
-  const int64_t i0 = (int64_t)blockIdx.x * OB;
+  const int64_t i0 = blk * OB;
   const int nobs = (int)min((int64_t)OB, D.N - i0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
 
@@ -135,6 +135,26 @@ __global__ void __launch_bounds__(256) build_operands_kernel(BuildDims D, const 
   }
 }
 
+template <OpType OT, typename PT>
+__global__ void __launch_bounds__(256) build_operands_kernel(BuildDims D, const float *__restrict__ X,
+                                                             const float *__restrict__ Y,
+                                                             const PT *__restrict__ P, void *At, void *Ad) {
+  build_block<OT, PT>(D, X, Y, P, At, Ad, blockIdx.x);
+}
+
+template <OpType OT, typename PT>
+__global__ void __launch_bounds__(256) grouped_build_kernel(const GroupProblem *__restrict__ probs,
+                                                            const GroupItem *__restrict__ items,
+                                                            const int *__restrict__ active) {
+  const GroupItem it = items[blockIdx.x];
+  if (active[it.problem] == 0) return;
+  const GroupProblem &g = probs[it.problem];
+  BuildDims D;
+  D.N = g.N; D.ldn = g.ldn; D.K = g.K; D.p = g.p; D.d = g.d; D.q = g.p + g.d;
+  D.ob = g.build_ob; D.kc = g.build_kc;
+  build_block<OT, PT>(D, g.X, g.Y, reinterpret_cast<const PT *>(g.P), g.At, g.Ad, it.idx);
+}
+
 // ---------------------------------------------------------------------------
 // FP64 CUDA-core SYRK tile: C[a][b] = sum_i At[a0+a][i] At[b0+b][i], 128 x 128,
 // stored transposed (out[b][a]) like the tensor-core tiles.  256 threads,
@@ -144,23 +164,19 @@ __global__ void __launch_bounds__(256) build_operands_kernel(BuildDims D, const 
 
 constexpr int kKc = 16;  // observations per shared-memory chunk
 
-__global__ void __launch_bounds__(256, 1) syrk_f64_kernel(const double *__restrict__ At, int64_t ldn, int64_t nchunks,
-                                                          const int2 *__restrict__ tiles, int ntiles, int nsplit,
-                                                          double *__restrict__ out) {
+// One 128 x 128 tile (ti, tj) over observation chunks [c0, c1) into o (transposed).
+__device__ __forceinline__ void syrk_f64_tile(const double *__restrict__ At, int64_t ldn, int ti, int tj, int64_t c0,
+                                              int64_t c1, double *__restrict__ o) {
   __shared__ double As[kKc][kTile + 1];
   __shared__ double Bs[kKc][kTile + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int unit = blockIdx.x;
-  const int s = unit / ntiles, t = unit % ntiles;
-  const int2 tl = tiles[t];
-  const int64_t a0 = (int64_t)tl.x * kTile, b0 = (int64_t)tl.y * kTile;
-  const int64_t c0 = nchunks * s / nsplit, c1 = nchunks * (s + 1) / nsplit;
+  const int64_t a0 = (int64_t)ti * kTile, b0 = (int64_t)tj * kTile;
   double acc[8][8];
 #pragma unroll
   for (int v = 0; v < 8; ++v)
 #pragma unroll
     for (int u = 0; u < 8; ++u) acc[v][u] = 0.0;
-  const bool diag = tl.x == tl.y;
+  const bool diag = ti == tj;
   for (int64_t ch = c0; ch < c1; ++ch) {
     const int64_t i = ch * kKc;
     __syncthreads();
@@ -186,11 +202,32 @@ __global__ void __launch_bounds__(256, 1) syrk_f64_kernel(const double *__restri
         for (int u = 0; u < 8; ++u) acc[v][u] = fma(av[v], bv[u], acc[v][u]);
     }
   }
-  double *o = out + ((int64_t)s * ntiles + t) * kTile * kTile;
 #pragma unroll
   for (int v = 0; v < 8; ++v)
 #pragma unroll
     for (int u = 0; u < 8; ++u) o[(ty + 16 * u) * kTile + tx + 16 * v] = acc[v][u];
+}
+
+__global__ void __launch_bounds__(256, 1) syrk_f64_kernel(const double *__restrict__ At, int64_t ldn, int64_t nchunks,
+                                                          const int2 *__restrict__ tiles, int ntiles, int nsplit,
+                                                          double *__restrict__ out) {
+  const int s = blockIdx.x / ntiles, t = blockIdx.x % ntiles;
+  const int2 tl = tiles[t];
+  syrk_f64_tile(At, ldn, tl.x, tl.y, nchunks * s / nsplit, nchunks * (s + 1) / nsplit,
+                out + ((int64_t)s * ntiles + t) * kTile * kTile);
+}
+
+// Grouped float64 contraction: one CTA per unit; map 0 selects the problem's
+// At operand, map 1 its Ad operand; kb0/kb1 count chunks of kKc observations.
+__global__ void __launch_bounds__(256, 1) grouped_syrk_f64_kernel(const GroupProblem *__restrict__ probs,
+                                                                  const SyrkUnit *__restrict__ units,
+                                                                  const int *__restrict__ active,
+                                                                  double *__restrict__ out) {
+  const SyrkUnit w = units[blockIdx.x];
+  if (active[w.problem] == 0) return;
+  const GroupProblem &g = probs[w.problem];
+  const double *At = reinterpret_cast<const double *>(w.map == 0 ? g.At : g.Ad);
+  syrk_f64_tile(At, g.ldn, w.ti, w.tj, w.kb0, w.kb1, out + w.out_off);
 }
 
 // ---------------------------------------------------------------------------
@@ -218,10 +255,10 @@ struct ZDims {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kZThreads) zblocks_kernel(ZDims D, const float *__restrict__ X,
-                                                            const float *__restrict__ Y, const float *__restrict__ Z,
-                                                            const T *__restrict__ P, const T *__restrict__ zbar,
-                                                            T *__restrict__ out) {
+__device__ __forceinline__ void zblocks_item(const ZDims &D, const float *__restrict__ X,
+                                             const float *__restrict__ Y, const float *__restrict__ Z,
+                                             const T *__restrict__ P, const T *__restrict__ zbar, int split,
+                                             int chunk, T *__restrict__ out_row) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int K = D.K, p = D.p, d = D.d, f = D.f, R = D.rows;
   const int Kf = K * f, Kd = K * d;
@@ -230,8 +267,8 @@ __global__ void __launch_bounds__(kZThreads) zblocks_kernel(ZDims D, const float
   float *Xs = reinterpret_cast<float *>(Zc + (size_t)R * Kf);  // [R][p]
   float *Ys = Xs + (size_t)R * p;                // [R][K d]
   const int tid = threadIdx.x;
-  const int64_t r0 = D.N * blockIdx.x / D.nsplit, r1 = D.N * (blockIdx.x + 1) / D.nsplit;
-  const int64_t obase = (int64_t)blockIdx.y * kZThreads * kZSlots;
+  const int64_t r0 = D.N * split / D.nsplit, r1 = D.N * (split + 1) / D.nsplit;
+  const int64_t obase = (int64_t)chunk * kZThreads * kZSlots;
   const int64_t nx = (int64_t)p * Kf, ny = (int64_t)Kd * f;
   // Slot decoding, once: kind (0 C_X, 1 C_Y, 2 A, 3 none), the two operand
   // offsets inside a staged row, and their row strides.
@@ -289,26 +326,50 @@ __global__ void __launch_bounds__(kZThreads) zblocks_kernel(ZDims D, const float
       acc[sl] += a;
     }
   }
-  T *o = out + (int64_t)blockIdx.x * D.nzt;
 #pragma unroll
   for (int sl = 0; sl < kZSlots; ++sl) {
     const int64_t oo = obase + tid + (int64_t)sl * blockDim.x;
-    if (oo < D.nzt) o[oo] = acc[sl];
+    if (oo < D.nzt) out_row[oo] = acc[sl];
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kZThreads) zblocks_kernel(ZDims D, const float *__restrict__ X,
+                                                            const float *__restrict__ Y, const float *__restrict__ Z,
+                                                            const T *__restrict__ P, const T *__restrict__ zbar,
+                                                            T *__restrict__ out) {
+  zblocks_item<T>(D, X, Y, Z, P, zbar, blockIdx.x, blockIdx.y, out + (int64_t)blockIdx.x * D.nzt);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kZThreads) grouped_zblocks_kernel(const GroupProblem *__restrict__ probs,
+                                                                    const GroupItem *__restrict__ items,
+                                                                    const int *__restrict__ active,
+                                                                    T *__restrict__ zpart) {
+  const GroupItem it = items[blockIdx.x];
+  if (active[it.problem] == 0) return;
+  const GroupProblem &g = probs[it.problem];
+  ZDims D;
+  D.N = g.N; D.K = g.K; D.p = g.p; D.d = g.d; D.f = g.f;
+  D.rows = g.zrows;
+  D.nsplit = g.zsplit;
+  D.nzt = (int64_t)g.p * g.K * g.f + (int64_t)g.K * g.d * g.f + (int64_t)g.f * g.f;
+  const int chunks = (int)((D.nzt + (int64_t)kZThreads * kZSlots - 1) / ((int64_t)kZThreads * kZSlots));
+  const int split = it.idx / chunks, chunk = it.idx % chunks;
+  zblocks_item<T>(D, g.X, g.Y, g.Z, reinterpret_cast<const T *>(g.P), reinterpret_cast<const T *>(g.zbar), split,
+                  chunk, zpart + g.z_off + (int64_t)split * D.nzt);
 }
 
 // ---------------------------------------------------------------------------
 // Assembly of F (lower triangle, column-major) in theta order.
 // ---------------------------------------------------------------------------
 
+// F(r, c), r >= c, from the partial sums.
 template <typename CT, typename ZT>
-__global__ void assemble_kernel(Shape S, const CT *__restrict__ mainp, int msplit, int nmain,
-                                const CT *__restrict__ bandp, int bsplit, int nband, const int *__restrict__ band_of,
-                                int nt1d, const ZT *__restrict__ zp, int zsplit, double *__restrict__ F) {
-  const int64_t n = S.n;
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t c = blockIdx.y + (int64_t)gridDim.y * blockIdx.z;
-  if (r >= n || c >= n || r < c) return;  // (r, c) in the lower triangle; both mirror entries are written
+__device__ __forceinline__ double assemble_entry(const Shape &S, const CT *__restrict__ mainp, int msplit, int nmain,
+                                                 const CT *__restrict__ bandp, int bsplit, int nband,
+                                                 const int *__restrict__ band_of, int nt1d,
+                                                 const ZT *__restrict__ zp, int zsplit, int64_t r, int64_t c) {
   const int q = S.q, f = S.f, K = S.K;
   const int64_t nx = (int64_t)S.p * K * f, ny = (int64_t)K * S.d * f, nzt = nx + ny + (int64_t)f * f;
   double v = 0.0;
@@ -339,8 +400,48 @@ __global__ void assemble_kernel(Shape S, const CT *__restrict__ mainp, int mspli
     const int64_t off = nx + ny + (int64_t)j1 * f + j2;
     for (int s = 0; s < zsplit; ++s) v += (double)zp[s * nzt + off];
   }
+  return v;
+}
+
+template <typename CT, typename ZT>
+__global__ void assemble_kernel(Shape S, const CT *__restrict__ mainp, int msplit, int nmain,
+                                const CT *__restrict__ bandp, int bsplit, int nband, const int *__restrict__ band_of,
+                                int nt1d, const ZT *__restrict__ zp, int zsplit, double *__restrict__ F) {
+  const int64_t n = S.n;
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t c = blockIdx.y + (int64_t)gridDim.y * blockIdx.z;
+  if (r >= n || c >= n || r < c) return;  // (r, c) in the lower triangle; both mirror entries are written
+  const double v = assemble_entry<CT, ZT>(S, mainp, msplit, nmain, bandp, bsplit, nband, band_of, nt1d, zp, zsplit,
+                                          r, c);
   F[c * n + r] = v;
   F[r * n + c] = v;
+}
+
+// Grouped assembly: item = (problem, block of kAssembleCols columns); the
+// batched contractions use one observation split (msplit = bsplit = 1).
+template <typename CT, typename ZT>
+__global__ void __launch_bounds__(256) grouped_assemble_kernel(const GroupProblem *__restrict__ probs,
+                                                               const GroupItem *__restrict__ items,
+                                                               const int *__restrict__ active,
+                                                               const CT *__restrict__ mainp,
+                                                               const CT *__restrict__ bandp,
+                                                               const ZT *__restrict__ zpart) {
+  const GroupItem it = items[blockIdx.x];
+  if (active[it.problem] == 0) return;
+  const GroupProblem &g = probs[it.problem];
+  const Shape S = shape_of(g.N, g.K, g.p, g.d, g.f);
+  const int64_t n = S.n;
+  const int nmain = g.nt1d * (g.nt1d + 1) / 2;
+  for (int cc = 0; cc < kAssembleCols; ++cc) {
+    const int64_t c = (int64_t)it.idx * kAssembleCols + cc;
+    if (c >= n) break;
+    for (int64_t r = c + threadIdx.x; r < n; r += blockDim.x) {
+      const double v = assemble_entry<CT, ZT>(S, mainp + g.main_off, 1, nmain, bandp + g.band_off, 1, 0, g.band_of,
+                                              g.nt1d, zpart + g.z_off, g.zsplit, r, c);
+      g.F[c * n + r] = v;
+      g.F[r * n + c] = v;
+    }
+  }
 }
 
 __global__ void export_hessian_kernel(int64_t n, const double *__restrict__ F, double *__restrict__ H) {
@@ -360,20 +461,25 @@ void grid_2d(int64_t rows, int64_t cols, dim3 &grid, dim3 &block) {
 
 }  // namespace
 
+size_t build_smem_bytes(const Shape &s, OpType t, int ob, int kc) {
+  const size_t csz = t == OpType::F64 ? 8 : 4;
+  return ((2 * (size_t)ob * (s.K | 1) * csz + 15) & ~(size_t)15) + (((size_t)ob * (s.p | 1) + 3) & ~(size_t)3) * 4 +
+         (size_t)ob * ((kc * s.d) | 1) * 4;
+}
+
+void build_blocking(const Shape &s, OpType t, int *ob, int *kc) {
+  *ob = 64;
+  *kc = std::max(1, s.K - 1);
+  while (*kc > 1 && build_smem_bytes(s, t, *ob, *kc) > 160 * 1024) *kc = (*kc + 1) / 2;
+  while (*ob > 16 && build_smem_bytes(s, t, *ob, *kc) > 160 * 1024) *ob /= 2;
+}
+
 cudaError_t launch_build_operands(const Shape &s, OpType t, const float *X, const float *Y, const void *P, void *At,
                                   void *Ad, int64_t ldn, cudaStream_t st) {
   BuildDims D;
   D.N = s.N; D.ldn = ldn; D.K = s.K; D.p = s.p; D.d = s.d; D.q = s.q;
-  const size_t csz = t == OpType::F64 ? 8 : 4;
-  D.ob = 64;
-  auto smem_for = [&](int ob, int kc) {
-    return ((2 * (size_t)ob * (s.K | 1) * csz + 15) & ~(size_t)15) + (((size_t)ob * (s.p | 1) + 3) & ~(size_t)3) * 4 +
-           (size_t)ob * ((kc * s.d) | 1) * 4;
-  };
-  D.kc = s.K - 1;
-  while (D.kc > 1 && smem_for(D.ob, D.kc) > 160 * 1024) D.kc = (D.kc + 1) / 2;
-  while (D.ob > 16 && smem_for(D.ob, D.kc) > 160 * 1024) D.ob /= 2;
-  const size_t smem = smem_for(D.ob, D.kc);
+  build_blocking(s, t, &D.ob, &D.kc);
+  const size_t smem = build_smem_bytes(s, t, D.ob, D.kc);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   const int blocks = (int)((s.N + D.ob - 1) / D.ob);
   cudaError_t e;
@@ -400,6 +506,68 @@ cudaError_t launch_build_operands(const Shape &s, OpType t, const float *X, cons
   return cudaGetLastError();
 }
 
+cudaError_t launch_grouped_build(OpType t, const GroupProblem *probs, const GroupItem *items, int nitems,
+                                 const int *active, size_t smem, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  cudaError_t e;
+  switch (t) {
+    case OpType::F64: {
+      auto k = grouped_build_kernel<OpType::F64, double>;
+      if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+      k<<<nitems, 256, smem, st>>>(probs, items, active);
+      break;
+    }
+    case OpType::TF32: {
+      auto k = grouped_build_kernel<OpType::TF32, float>;
+      if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+      k<<<nitems, 256, smem, st>>>(probs, items, active);
+      break;
+    }
+    case OpType::BF16: {
+      auto k = grouped_build_kernel<OpType::BF16, float>;
+      if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+      k<<<nitems, 256, smem, st>>>(probs, items, active);
+      break;
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grouped_zblocks(bool fp64, const GroupProblem *probs, const GroupItem *items, int nitems,
+                                   const int *active, size_t smem, void *zpart, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  cudaError_t e;
+  if (fp64) {
+    if ((e = cudaFuncSetAttribute(grouped_zblocks_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)))
+      return e;
+    grouped_zblocks_kernel<double><<<nitems, kZThreads, smem, st>>>(probs, items, active,
+                                                                     reinterpret_cast<double *>(zpart));
+  } else {
+    if ((e = cudaFuncSetAttribute(grouped_zblocks_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)))
+      return e;
+    grouped_zblocks_kernel<float><<<nitems, kZThreads, smem, st>>>(probs, items, active,
+                                                                    reinterpret_cast<float *>(zpart));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grouped_assemble(bool fp64, const GroupProblem *probs, const GroupItem *items, int nitems,
+                                    const int *active, const void *mainp, const void *bandp, const void *zpart,
+                                    cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  if (fp64)
+    grouped_assemble_kernel<double, double><<<nitems, 256, 0, st>>>(
+        probs, items, active, reinterpret_cast<const double *>(mainp), reinterpret_cast<const double *>(bandp),
+        reinterpret_cast<const double *>(zpart));
+  else
+    grouped_assemble_kernel<float, float><<<nitems, 256, 0, st>>>(
+        probs, items, active, reinterpret_cast<const float *>(mainp), reinterpret_cast<const float *>(bandp),
+        reinterpret_cast<const float *>(zpart));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_syrk_f64(const double *At, int64_t ldn, int64_t N, const int2 *tiles, int ntiles, int nsplit,
                             double *out, cudaStream_t st) {
   (void)N;
@@ -422,6 +590,15 @@ int zblocks_rows(const Shape &s, bool fp64) {
   while (rows > 1 && zblocks_smem(s, rows, fp64) > 110 * 1024) rows /= 2;
   return rows;
 }
+
+cudaError_t launch_grouped_syrk_f64(const GroupProblem *probs, const SyrkUnit *units, int nunits, const int *active,
+                                    double *out, cudaStream_t st) {
+  if (nunits <= 0) return cudaSuccess;
+  grouped_syrk_f64_kernel<<<nunits, 256, 0, st>>>(probs, units, active, out);
+  return cudaGetLastError();
+}
+
+int f64_chunk_rows() { return kKc; }
 
 cudaError_t launch_zblocks(const Shape &s, bool fp64, const float *X, const float *Y, const float *Z, const void *P,
                            const void *zbar, int nsplit, void *out, cudaStream_t st) {

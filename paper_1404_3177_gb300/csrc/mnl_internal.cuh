@@ -12,10 +12,15 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "../../include/mnl.h"
 
 namespace mnl {
+
+// Element type of the Hessian operands: double (FP64), float rounded to TF32,
+// or bf16.
+enum class OpType { F64 = 0, TF32 = 1, BF16 = 2 };
 
 // Operand / output tile edge of every Hessian contraction.
 constexpr int kTile = 128;
@@ -35,17 +40,26 @@ struct Shape {
   int64_t nout; // raw gradient accumulators: (K-1) q + K f
 };
 
-inline Shape make_shape(const mnl_dims &d) {
+__host__ __device__ inline Shape shape_of(int64_t N, int K, int p, int d, int f) {
   Shape s;
-  s.N = d.N; s.K = d.K; s.p = d.p; s.d = d.d; s.f = d.f;
-  s.q = d.p + d.d;
-  s.nb = (int64_t)(d.K - 1) * d.p;
-  s.ng = (int64_t)(d.K - 1) * d.d;
+  s.N = N; s.K = K; s.p = p; s.d = d; s.f = f;
+  s.q = p + d;
+  s.nb = (int64_t)(K - 1) * p;
+  s.ng = (int64_t)(K - 1) * d;
   s.mc = s.nb + s.ng;
-  s.n = s.mc + d.f;
-  s.nout = s.mc + (int64_t)d.K * d.f;
+  s.n = s.mc + f;
+  s.nout = s.mc + (int64_t)K * f;
   return s;
 }
+inline Shape make_shape(const mnl_dims &d) { return shape_of(d.N, d.K, d.p, d.d, d.f); }
+
+// A unit of the tiled contractions: operand (tensor map index, or 0 = At /
+// 1 = Ad for the float64 path), problem, output tile (ti, tj), K-block range
+// [kb0, kb1) and the offset of its 128 x 128 output tile.
+struct SyrkUnit {
+  int map, problem, ti, tj, kb0, kb1;
+  int64_t out_off;
+};
 
 // theta index (class part) -> class k (1..K-1) and local column l (0..q-1).
 __host__ __device__ inline void theta_class_local(const Shape &s, int64_t a, int &k, int &l) {
@@ -77,6 +91,90 @@ struct PassPlan {
 PassPlan plan_pass(const Shape &s, bool fp64, bool full, int num_sms);
 cudaError_t launch_pass(const Shape &s, const PassPlan &pl, bool fp64, bool full, const PassIO &io, cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// Grouped (batched) path: many independent problems, one launch per phase.
+// ---------------------------------------------------------------------------
+
+// Per-problem float64 scalars of a batched fit (GroupProblem::scal).
+enum GroupScal {
+  kGsL = 0, kGsLabs = 1, kGsGinf = 2, kGsLt = 3, kGsLtabs = 4, kGsT = 5, kGsStepInf = 6, kGsThetaInf = 7,
+  kGsLold = 8, kGsLsEvals = 9, kGsIters = 10, kGsRefine = 11, kGsCount = 16
+};
+
+// Everything a grouped kernel needs to know about one problem (device memory).
+struct GroupProblem {
+  int64_t N;
+  int K, p, d, f;
+  int64_t n, mc;                 // n_theta, class coefficients
+  const float *X, *Y, *Z;
+  const int32_t *choice;
+  double *theta, *grad, *delta;  // [n]
+  void *P, *zbar;                // [N][K], [N][f] (float64 in FP64 mode, else float32)
+  void *At, *Ad;                 // Hessian operands [mc_pad][ldn]
+  int64_t ldn, mc_pad;
+  int nt1d, zsplit, zrows;
+  int build_ob, build_kc;        // operand-builder blocking
+  int64_t main_off, band_off, z_off;  // offsets of this problem's contraction partials (elements)
+  int *band_of;                  // [nt1d][nt1d]
+  double *F;                     // [n][n]
+  float *F32;                    // [n][n] (mixed solve)
+  double *rwork;                 // [2 n] (mixed solve)
+  double *scal;                  // [kGsCount]
+};
+
+// One CTA's run of consecutive row tiles of one problem in the grouped pass,
+// with the offsets of its partial row (full pass / log-likelihood-only pass).
+struct PassSeg {
+  int problem;
+  int64_t tile0, tile1;
+  int64_t slot_full, slot_ll;
+};
+
+// A generic grouped work item: (problem, index within the problem).
+struct GroupItem {
+  int problem;
+  int idx;
+};
+
+// Grouped Hessian pieces (one CTA per item; items of inactive problems exit).
+cudaError_t launch_grouped_build(OpType t, const GroupProblem *probs, const GroupItem *items, int nitems,
+                                 const int *active, size_t smem, cudaStream_t st);
+cudaError_t launch_grouped_zblocks(bool fp64, const GroupProblem *probs, const GroupItem *items, int nitems,
+                                   const int *active, size_t smem, void *zpart, cudaStream_t st);
+cudaError_t launch_grouped_assemble(bool fp64, const GroupProblem *probs, const GroupItem *items, int nitems,
+                                    const int *active, const void *mainp, const void *bandp, const void *zpart,
+                                    cudaStream_t st);
+size_t build_smem_bytes(const Shape &s, OpType t, int ob, int kc);
+void build_blocking(const Shape &s, OpType t, int *ob, int *kc);
+int zblocks_rows(const Shape &s, bool fp64);
+size_t zblocks_smem(const Shape &s, int rows, bool fp64);
+constexpr int kAssembleCols = 8;  // columns per grouped-assembly item
+
+// Grouped float64 contraction (FP64 mode): one CTA per unit, map 0 = At, 1 = Ad,
+// K range in chunks of f64_chunk_rows() observations.
+cudaError_t launch_grouped_syrk_f64(const GroupProblem *probs, const SyrkUnit *units, int nunits, const int *active,
+                                    double *out, cudaStream_t st);
+int f64_chunk_rows();
+
+// One CTA per active problem: delta = (-H)^{-1} g (mixed or float64), see cholesky.cu.
+size_t grouped_chol_smem(int64_t nmax);
+cudaError_t launch_grouped_chol_solve(bool mixed, const GroupProblem *probs, int nprob, const int *active,
+                                      int iters, int *status, size_t smem, cudaStream_t st);
+
+struct GroupedPassPlan {
+  int grid, block, rows, npt;
+  size_t smem;
+  bool ok;
+};
+GroupedPassPlan plan_grouped_pass(const std::vector<Shape> &shapes, bool fp64, int rows, int num_sms);
+cudaError_t launch_grouped_pass(const GroupedPassPlan &pl, bool fp64, bool full, const GroupProblem *probs,
+                                const PassSeg *segs, const int *seg_start, const int *active, double *partials,
+                                cudaStream_t st);
+// Per problem (one CTA each): l, sum|l| -> scal[base..]; full: g -> grad, max|g| -> scal[kGsGinf].
+cudaError_t launch_grouped_reduce(int nprob, bool full, const GroupProblem *probs, const int *slot_start,
+                                  const PassSeg *segs, const int *slot_segs, const int *active,
+                                  const double *partials, int base, cudaStream_t st);
+
 // Fixed-order FP64 reduction of the pass partials.
 //   out: [0] l, [1] sum |l_i|, [2] max|g|; grad (θ order) when full.
 cudaError_t launch_pass_reduce(const Shape &s, int grid, bool full, const double *partials, double *scal,
@@ -90,7 +188,6 @@ cudaError_t launch_validate(const Shape &s, const float *X, const float *Y, cons
 //   At  [c][i] = P_ik m_ik[l]                   (c = (k-1)q + l)
 //   Ad  [c][i] = sqrt(P_ik (1 - P_ik)) m_ik[l]
 // T = double (FP64), float rounded to TF32 (TF32), or bf16 (BF16).
-enum class OpType { F64 = 0, TF32 = 1, BF16 = 2 };
 cudaError_t launch_build_operands(const Shape &s, OpType t, const float *X, const float *Y, const void *P,
                                   void *At, void *Ad, int64_t ldn, cudaStream_t st);
 
@@ -106,16 +203,16 @@ struct TileLists {
 cudaError_t launch_syrk_f64(const double *At, int64_t ldn, int64_t N, const int2 *tiles, int ntiles, int nsplit,
                             double *out, cudaStream_t st);
 
-// tcgen05 tensor-core SYRK (BF16 or TF32 operands, FP32 accumulation in TMEM).
-struct TcPlan {
-  CUtensorMap map;
-  int nsplit, kblocks, grid;
-  size_t smem;
-};
-cudaError_t make_tc_plan(OpType t, const void *At, int64_t rows_pad, int64_t ldn, int64_t N, int ntiles,
-                         int num_sms, TcPlan *out);
-cudaError_t launch_syrk_tc(OpType t, const TcPlan &pl, const int2 *tiles, int ntiles, float *out, int *err,
-                           cudaStream_t st);
+// tcgen05 tensor-core SYRK (BF16 or TF32 operands, FP32 accumulation in TMEM)
+// over a list of work units: unit = (tensor map, problem, output tile (ti, tj),
+// K-block range [kb0, kb1)), writing out[out_off .. + 128*128) transposed.
+// Units of problems with active[problem] == 0 are skipped (active may be null).
+cudaError_t encode_operand_map(OpType t, const void *At, int64_t rows_pad, int64_t ldn, CUtensorMap *out);
+int tc_kblocks(OpType t, int64_t ldn);
+int tc_pick_split(int ntiles, int kblocks, int num_sms);
+size_t tc_smem_bytes();
+cudaError_t launch_syrk_tc(OpType t, const CUtensorMap *maps, const SyrkUnit *units, int nunits, const int *active,
+                           int grid, float *out, int *err, cudaStream_t st);
 
 // Z blocks (FP32 or FP64 accumulation) per observation split s:
 // out[s][zblocks_outputs()] = [C_X: p*K*f | C_Y: K*d*f | A: f*f] (see hessian.cu).

@@ -96,8 +96,11 @@ struct PassDims {
 //   tile  f32 [rows * (p + K d + K f)]   Xs | Ys | Zs
 //   res   T   [rows * K]          residuals (FULL only)
 //   red   f64 [32 * 4]            per-warp log-likelihood partials
+// One CTA processes tiles tile0, tile0 + tstride, ... < tile1 of one problem
+// and writes its partial row `out` = [l, sum |l_i|, g (FULL only)].
 template <typename T, bool FULL, int NPT>
-__global__ void __launch_bounds__(512) pass_kernel(PassDims D, PassIO io) {
+__device__ __forceinline__ void pass_segment(const PassDims &D, const PassIO &io, int64_t tile0, int64_t tile1,
+                                             int64_t tstride, double *out) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int K = D.K, p = D.p, d = D.d, f = D.f, R = D.rows;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -142,7 +145,7 @@ __global__ void __launch_bounds__(512) pass_kernel(PassDims D, PassIO io) {
   Acc<T> lsum, labs;  // lane 0 of each warp
   Acc<T> acc[FULL ? NPT : 1];
 
-  for (int64_t tile = blockIdx.x; tile < D.ntiles; tile += gridDim.x) {
+  for (int64_t tile = tile0; tile < tile1; tile += tstride) {
     const int64_t row0 = tile * R;
     const int nrows = (int)min((int64_t)R, D.N - row0);
     __syncthreads();  // previous tile fully consumed (and coefficients written)
@@ -252,7 +255,6 @@ __global__ void __launch_bounds__(512) pass_kernel(PassDims D, PassIO io) {
   }
   __syncthreads();
   // Partials row: [l, sum |l_i|, g (theta order: class coefficients, then alpha)].
-  double *out = io.partials + (int64_t)blockIdx.x * (FULL ? 2 + D.mc + f : 2);
   if (tid == 0) {
     double a = 0.0, b = 0.0;
     for (int w = 0; w < nwarps; ++w) { a += red[w * 2]; b += red[w * 2 + 1]; }
@@ -274,6 +276,83 @@ __global__ void __launch_bounds__(512) pass_kernel(PassDims D, PassIO io) {
       double sa = 0.0;
       for (int k = 0; k < K; ++k) sa += az[k * f + j];
       out[2 + D.mc + j] = sa;
+    }
+  }
+  __syncthreads();  // the shared memory is reused by the caller's next segment
+}
+
+template <typename T, bool FULL, int NPT>
+__global__ void __launch_bounds__(512) pass_kernel(PassDims D, PassIO io) {
+  double *out = io.partials + (int64_t)blockIdx.x * (FULL ? 2 + D.mc + D.f : 2);
+  pass_segment<T, FULL, NPT>(D, io, blockIdx.x, D.ntiles, gridDim.x, out);
+}
+
+// Grouped pass over many problems: CTA c walks its segments
+// segs[seg_start[c] .. seg_start[c+1]), skipping problems with active == 0.
+template <typename T, bool FULL, int NPT>
+__global__ void __launch_bounds__(512) grouped_pass_kernel(const GroupProblem *__restrict__ probs,
+                                                           const PassSeg *__restrict__ segs,
+                                                           const int *__restrict__ seg_start,
+                                                           const int *__restrict__ active, int rows,
+                                                           double *__restrict__ partials) {
+  for (int si = seg_start[blockIdx.x]; si < seg_start[blockIdx.x + 1]; ++si) {
+    const PassSeg sg = segs[si];
+    const GroupProblem &gp = probs[sg.problem];
+    if (active[sg.problem] == 0) continue;
+    PassDims D;
+    D.N = gp.N; D.K = gp.K; D.p = gp.p; D.d = gp.d; D.f = gp.f;
+    D.nb = (int64_t)(gp.K - 1) * gp.p; D.ng = (int64_t)(gp.K - 1) * gp.d; D.mc = D.nb + D.ng;
+    D.nout = D.mc + (int64_t)gp.K * gp.f;
+    D.rows = rows;
+    D.ntiles = (gp.N + rows - 1) / rows;
+    PassIO io;
+    io.X = gp.X; io.Y = gp.Y; io.Z = gp.Z; io.choice = gp.choice;
+    io.theta = gp.theta;
+    io.delta = FULL ? nullptr : gp.delta;
+    io.tscale = gp.scal + kGsT;
+    io.P = gp.P; io.zbar = gp.zbar;
+    io.partials = nullptr;
+    pass_segment<T, FULL, NPT>(D, io, sg.tile0, sg.tile1, 1, partials + (FULL ? sg.slot_full : sg.slot_ll));
+  }
+}
+
+// Per-problem fixed-order reduction of the grouped pass partials:
+// l -> scal[base], sum |l_i| -> scal[base+1]; FULL: g -> grad, max|g| -> scal[kGsGinf].
+template <bool FULL>
+__global__ void __launch_bounds__(128) grouped_reduce_kernel(const GroupProblem *__restrict__ probs,
+                                                             const int *__restrict__ slot_start,
+                                                             const PassSeg *__restrict__ segs,
+                                                             const int *__restrict__ slot_segs,
+                                                             const int *__restrict__ active,
+                                                             const double *__restrict__ partials, int base) {
+  const int b = blockIdx.x;
+  if (active[b] == 0) return;
+  const GroupProblem &gp = probs[b];
+  const int64_t n = (int64_t)(gp.K - 1) * (gp.p + gp.d) + gp.f;
+  const int64_t len = FULL ? 2 + n : 2;
+  const int s0 = slot_start[b], s1 = slot_start[b + 1];
+  __shared__ double red[4];
+  double gmax = 0.0;
+  for (int64_t o = threadIdx.x; o < len; o += blockDim.x) {
+    double acc = 0.0;
+    for (int s = s0; s < s1; ++s) {
+      const PassSeg &sg = segs[slot_segs[s]];
+      acc += partials[(FULL ? sg.slot_full : sg.slot_ll) + o];
+    }
+    if (o < 2) gp.scal[base + o] = acc;
+    else {
+      gp.grad[o - 2] = acc;
+      gmax = fmax(gmax, isfinite(acc) ? fabs(acc) : INFINITY);
+    }
+  }
+  if (FULL) {
+    for (int off = 16; off > 0; off >>= 1) gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = gmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+      gp.scal[kGsGinf] = m;
     }
   }
 }
@@ -412,10 +491,86 @@ cudaError_t launch_pass_reduce(const Shape &s, int grid, bool full, const double
   return cudaGetLastError();
 }
 
+template <typename T, bool FULL, int NPT>
+cudaError_t launch_grouped_t(const GroupedPassPlan &pl, const GroupProblem *probs, const PassSeg *segs,
+                             const int *seg_start, const int *active, double *partials, cudaStream_t st) {
+  auto kern = grouped_pass_kernel<T, FULL, NPT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+  if (e != cudaSuccess) return e;
+  kern<<<pl.grid, pl.block, pl.smem, st>>>(probs, segs, seg_start, active, pl.rows, partials);
+  return cudaGetLastError();
+}
+
+template <typename T, bool FULL>
+cudaError_t launch_grouped_npt(const GroupedPassPlan &pl, const GroupProblem *probs, const PassSeg *segs,
+                               const int *seg_start, const int *active, double *partials, cudaStream_t st) {
+  if (!FULL) return launch_grouped_t<T, false, 1>(pl, probs, segs, seg_start, active, partials, st);
+  switch (pl.npt) {
+    case 1: return launch_grouped_t<T, FULL, 1>(pl, probs, segs, seg_start, active, partials, st);
+    case 2: return launch_grouped_t<T, FULL, 2>(pl, probs, segs, seg_start, active, partials, st);
+    case 4: return launch_grouped_t<T, FULL, 4>(pl, probs, segs, seg_start, active, partials, st);
+    case 8: return launch_grouped_t<T, FULL, 8>(pl, probs, segs, seg_start, active, partials, st);
+    case 16: return launch_grouped_t<T, FULL, 16>(pl, probs, segs, seg_start, active, partials, st);
+    case 24: return launch_grouped_t<T, FULL, 24>(pl, probs, segs, seg_start, active, partials, st);
+    case 32: return launch_grouped_t<T, FULL, 32>(pl, probs, segs, seg_start, active, partials, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_validate(const Shape &s, const float *X, const float *Y, const float *Z, const int32_t *choice,
                             int *status, cudaStream_t st) {
   validate_kernel<<<1024, 256, 0, st>>>(s.N, s.K, s.p, s.d, s.f, X, s.d ? Y : nullptr, s.f ? Z : nullptr, choice,
                                         status);
+  return cudaGetLastError();
+}
+
+}  // namespace mnl
+
+namespace mnl {
+
+GroupedPassPlan plan_grouped_pass(const std::vector<Shape> &shapes, bool fp64, int rows, int num_sms) {
+  GroupedPassPlan pl{};
+  pl.ok = false;
+  int64_t max_nout = 0;
+  size_t smem = 0;
+  const size_t tsz = fp64 ? 8 : 4;
+  for (const Shape &s : shapes) {
+    if (s.K > 32 * kMaxClassSlots) return pl;
+    max_nout = std::max<int64_t>(max_nout, s.nout);
+    smem = std::max(smem, pass_smem(s, rows, tsz, true));
+  }
+  pl.block = 256;
+  int need = (int)((max_nout + pl.block - 1) / pl.block);
+  if (need > 16) { pl.block = 512; need = (int)((max_nout + pl.block - 1) / pl.block); }
+  static const int opts[] = {1, 2, 4, 8, 16, 24, 32};
+  pl.npt = 0;
+  for (int o : opts) if (o >= need) { pl.npt = o; break; }
+  if (!pl.npt || smem > 220 * 1024) return pl;
+  pl.rows = rows;
+  pl.smem = smem;
+  const int per_sm = (smem <= 100 * 1024 && pl.block == 256) ? 2 : 1;
+  pl.grid = num_sms * per_sm;
+  pl.ok = true;
+  return pl;
+}
+
+cudaError_t launch_grouped_pass(const GroupedPassPlan &pl, bool fp64, bool full, const GroupProblem *probs,
+                                const PassSeg *segs, const int *seg_start, const int *active, double *partials,
+                                cudaStream_t st) {
+  if (fp64)
+    return full ? launch_grouped_npt<double, true>(pl, probs, segs, seg_start, active, partials, st)
+                : launch_grouped_npt<double, false>(pl, probs, segs, seg_start, active, partials, st);
+  return full ? launch_grouped_npt<float, true>(pl, probs, segs, seg_start, active, partials, st)
+              : launch_grouped_npt<float, false>(pl, probs, segs, seg_start, active, partials, st);
+}
+
+cudaError_t launch_grouped_reduce(int nprob, bool full, const GroupProblem *probs, const int *slot_start,
+                                  const PassSeg *segs, const int *slot_segs, const int *active,
+                                  const double *partials, int base, cudaStream_t st) {
+  if (full)
+    grouped_reduce_kernel<true><<<nprob, 128, 0, st>>>(probs, slot_start, segs, slot_segs, active, partials, base);
+  else
+    grouped_reduce_kernel<false><<<nprob, 128, 0, st>>>(probs, slot_start, segs, slot_segs, active, partials, base);
   return cudaGetLastError();
 }
 

@@ -152,9 +152,10 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&v)
 constexpr int kErrProducer = 1, kErrMma = 2, kErrEpilogue = 4, kErrDrain = 8;
 
 template <bool TF32>
-__global__ void __launch_bounds__(192, 1) syrk_tc_kernel(const __grid_constant__ CUtensorMap map,
-                                                         const int2 *__restrict__ tiles, int ntiles, int nsplit,
-                                                         int kblocks, float *__restrict__ out, int *__restrict__ err) {
+__global__ void __launch_bounds__(192, 1) syrk_tc_kernel(const CUtensorMap *__restrict__ maps,
+                                                         const SyrkUnit *__restrict__ units, int nunits,
+                                                         const int *__restrict__ active, float *__restrict__ out,
+                                                         int *__restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
@@ -166,8 +167,9 @@ __global__ void __launch_bounds__(192, 1) syrk_tc_kernel(const __grid_constant__
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int total = ntiles * nsplit;
   constexpr int kBk = TF32 ? kBkTf32 : kBkBf16;
+  // A unit is skipped by every role alike when its problem is inactive.
+  auto skip = [&](const SyrkUnit &w) { return active != nullptr && active[w.problem] == 0; };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -175,7 +177,6 @@ __global__ void __launch_bounds__(192, 1) syrk_tc_kernel(const __grid_constant__
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map)) : "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tmem_slot)),
@@ -196,17 +197,17 @@ __global__ void __launch_bounds__(192, 1) syrk_tc_kernel(const __grid_constant__
       int last_par[kStages];
       for (int s = 0; s < kStages; ++s) last_par[s] = -1;
       bool ok = true;
-      for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
-        const int sp = u / ntiles, t = u % ntiles;
-        const int2 tl = tiles[t];
-        const int kb0 = (int)((int64_t)kblocks * sp / nsplit), kb1 = (int)((int64_t)kblocks * (sp + 1) / nsplit);
-        const bool diag = tl.x == tl.y;
-        for (int kb = kb0; kb < kb1; ++kb) {
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        const SyrkUnit w = units[u];
+        if (skip(w)) continue;
+        const CUtensorMap *map = maps + w.map;
+        const bool diag = w.ti == w.tj;
+        for (int kb = w.kb0; kb < w.kb1; ++kb) {
           if (!wait_bounded(&empty[stage], phase ^ 1u, abort_flag, err, kErrProducer)) { ok = false; break; }
           uint8_t *dst = smem + stage * kStageBytes;
           mbar_arrive_expect_tx(&full[stage], diag ? kOpBytes : 2 * kOpBytes);
-          tma_load_2d(&map, &full[stage], dst, kb * kBk, tl.x * kTile);
-          if (!diag) tma_load_2d(&map, &full[stage], dst + kOpBytes, kb * kBk, tl.y * kTile);
+          tma_load_2d(map, &full[stage], dst, kb * kBk, w.ti * kTile);
+          if (!diag) tma_load_2d(map, &full[stage], dst + kOpBytes, kb * kBk, w.tj * kTile);
           last_par[stage] = (int)phase;
           if (++stage == kStages) { stage = 0; phase ^= 1u; }
         }
@@ -223,12 +224,13 @@ __global__ void __launch_bounds__(192, 1) syrk_tc_kernel(const __grid_constant__
       uint32_t acc_ph[2] = {0u, 0u};
       int local = 0;
       bool ok = true;
-      for (int u = blockIdx.x; u < total && ok; u += gridDim.x, ++local) {
-        const int sp = u / ntiles, t = u % ntiles;
-        const int2 tl = tiles[t];
-        const int kb0 = (int)((int64_t)kblocks * sp / nsplit), kb1 = (int)((int64_t)kblocks * (sp + 1) / nsplit);
-        const bool diag = tl.x == tl.y;
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        const SyrkUnit w = units[u];
+        if (skip(w)) continue;
+        const int kb0 = w.kb0, kb1 = w.kb1;
+        const bool diag = w.ti == w.tj;
         const int b = local & 1;
+        ++local;
         if (!wait_bounded(&tempty[b], acc_ph[b] ^ 1u, abort_flag, err, kErrMma)) break;
         acc_ph[b] ^= 1u;
         tc_fence_after();
@@ -257,9 +259,11 @@ __global__ void __launch_bounds__(192, 1) syrk_tc_kernel(const __grid_constant__
     const int quarter = warp & 3;  // this warp may access TMEM lanes 32*quarter .. +31
     uint32_t acc_ph[2] = {0u, 0u};
     int local = 0;
-    for (int u = blockIdx.x; u < total; u += gridDim.x, ++local) {
-      const int sp = u / ntiles, t = u % ntiles;
+    for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+      const SyrkUnit w = units[u];
+      if (skip(w)) continue;
       const int b = local & 1;
+      ++local;
       int ok = 0;
       if (lane == 0) ok = wait_bounded(&tfull[b], acc_ph[b], abort_flag, err, kErrEpilogue) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -267,7 +271,7 @@ __global__ void __launch_bounds__(192, 1) syrk_tc_kernel(const __grid_constant__
       acc_ph[b] ^= 1u;
       tc_fence_after();
       // Tile stored transposed: out[col][row], row = MMA M index (operand tile ti).
-      float *dst = out + ((int64_t)sp * ntiles + t) * kTile * kTile + quarter * 32 + lane;
+      float *dst = out + w.out_off + quarter * 32 + lane;
 #pragma unroll 1
       for (int c0 = 0; c0 < kTile; c0 += 32) {
         uint32_t v[32];
@@ -308,9 +312,7 @@ EncodeTiled get_encoder() {
 
 }  // namespace
 
-cudaError_t make_tc_plan(OpType t, const void *At, int64_t rows_pad, int64_t ldn, int64_t N, int ntiles,
-                         int num_sms, TcPlan *out) {
-  (void)N;
+cudaError_t encode_operand_map(OpType t, const void *At, int64_t rows_pad, int64_t ldn, CUtensorMap *out) {
   if (t == OpType::F64) return cudaErrorInvalidValue;
   EncodeTiled enc = get_encoder();
   if (!enc) return cudaErrorNotSupported;
@@ -324,15 +326,19 @@ cudaError_t make_tc_plan(OpType t, const void *At, int64_t rows_pad, int64_t ldn
   cuuint64_t strides[1] = {(cuuint64_t)(ldn * esz)};
   cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)kTile};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(&out->map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+  CUresult r = enc(out, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                    const_cast<void *>(At), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  out->kblocks = (int)(ldn / bk);
-  // Splits of the observation range: balance units over the SMs, keep >= 8 K-blocks per split.
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+int tc_kblocks(OpType t, int64_t ldn) { return (int)(ldn / (t == OpType::TF32 ? kBkTf32 : kBkBf16)); }
+
+int tc_pick_split(int ntiles, int kblocks, int num_sms) {
+  // balance the units over the SMs, keep >= 8 K-blocks per split
   int best = 1;
   double best_eff = -1.0;
-  const int max_split = std::max(1, std::min(16, out->kblocks / 8));
+  const int max_split = std::max(1, std::min(16, kblocks / 8));
   for (int s = 1; s <= max_split; ++s) {
     const int units = ntiles * s;
     const int g = std::min(units, num_sms);
@@ -340,23 +346,23 @@ cudaError_t make_tc_plan(OpType t, const void *At, int64_t rows_pad, int64_t ldn
     const double eff = (double)units / ((double)g * waves) * (g / (double)num_sms);
     if (eff > best_eff + 0.02) { best_eff = eff; best = s; }
   }
-  out->nsplit = best;
-  out->grid = std::min(ntiles * best, num_sms);
-  out->smem = kSmemBytes;
-  return cudaSuccess;
+  return best;
 }
 
-cudaError_t launch_syrk_tc(OpType t, const TcPlan &pl, const int2 *tiles, int ntiles, float *out, int *err,
-                           cudaStream_t st) {
+size_t tc_smem_bytes() { return kSmemBytes; }
+
+cudaError_t launch_syrk_tc(OpType t, const CUtensorMap *maps, const SyrkUnit *units, int nunits, const int *active,
+                           int grid, float *out, int *err, cudaStream_t st) {
+  if (nunits <= 0) return cudaSuccess;
   cudaError_t e;
   if (t == OpType::TF32) {
     if ((e = cudaFuncSetAttribute(syrk_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)))
       return e;
-    syrk_tc_kernel<true><<<pl.grid, 192, kSmemBytes, st>>>(pl.map, tiles, ntiles, pl.nsplit, pl.kblocks, out, err);
+    syrk_tc_kernel<true><<<grid, 192, kSmemBytes, st>>>(maps, units, nunits, active, out, err);
   } else {
     if ((e = cudaFuncSetAttribute(syrk_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)))
       return e;
-    syrk_tc_kernel<false><<<pl.grid, 192, kSmemBytes, st>>>(pl.map, tiles, ntiles, pl.nsplit, pl.kblocks, out, err);
+    syrk_tc_kernel<false><<<grid, 192, kSmemBytes, st>>>(maps, units, nunits, active, out, err);
   }
   return cudaGetLastError();
 }
