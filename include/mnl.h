@@ -62,7 +62,8 @@ enum {
   MNL_ERR_LINESEARCH = 6,  /* no step size 2^-j, j <= max_halvings, kept l from decreasing    */
   MNL_MAXITER = 7,         /* mnl_fit: maxiter reached without meeting a tolerance (non-fatal) */
   MNL_ERR_TIMEOUT = 8,     /* a bounded device-side wait gave up; the result is invalid      */
-  MNL_ERR_UNSUPPORTED = 9  /* valid request this build does not implement                    */
+  MNL_ERR_UNSUPPORTED = 9, /* valid request this build does not implement                    */
+  MNL_PENDING = 10         /* mnl_server_poll: the request has not finished yet (non-fatal)  */
 };
 
 /* Arithmetic of the Hessian contraction.  In every mode the Cholesky solve,
@@ -278,6 +279,55 @@ MNL_API int64_t mnl_batch_num_params(const mnl_batch *b, int64_t *offsets);
 MNL_API int mnl_batch_fit(mnl_batch *b, const mnl_fit_opts *opts, double *theta, mnl_batch_info *info);
 
 MNL_API int mnl_batch_destroy(mnl_batch *b);
+
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of fit requests.  Requests are admitted while
+ * their device state fits in a fixed memory budget; every mnl_server_step
+ * ("tick") runs one Newton iteration for all admitted requests together (the
+ * same grouped launches as mnl_batch_fit), retires the ones that finished and
+ * frees their memory for the next admissions.  Each request's data,
+ * coefficients, P, gradient and Hessian stay on the device from admission to
+ * retirement.  Submit and poll may be called from other threads.
+ * ------------------------------------------------------------------------ */
+typedef struct mnl_server mnl_server;
+
+typedef struct mnl_server_opts {
+  size_t mem_budget;   /* device bytes for admitted requests (one pool, allocated at create) */
+  int32_t precision;   /* an mnl_precision value                                        */
+  int32_t max_active;  /* admitted requests at most                                     */
+  int32_t max_skips;   /* times a queued request may be passed over by later, smaller
+                          ones before admission waits for it (FIFO fairness)            */
+  int32_t pad;
+  mnl_fit_opts fit;    /* stopping rules of every request                               */
+} mnl_server_opts;
+
+typedef struct mnl_request_result {
+  int32_t status;      /* MNL_OK, MNL_MAXITER or an MNL_ERR_*          */
+  int32_t stop_reason; /* MNL_STOP_*                                   */
+  int32_t iters;       /* Newton iterations (= ticks while admitted)   */
+  int32_t ls_evals;
+  double loglik, grad_inf;
+  double latency_ms;   /* submit -> retirement (host clock)            */
+  double queue_ms;     /* submit -> admission                          */
+} mnl_request_result;
+
+/* Defaults: 80 GiB budget, MNL_BF16, 4096 active, 8 skips, mnl_fit_opts_default. */
+MNL_API void mnl_server_opts_default(mnl_server_opts *opts);
+MNL_API int mnl_server_create(const mnl_server_opts *opts, void *stream, mnl_server **out);
+/* Queue a request.  host: HOST arrays (copied before the call returns);
+ * theta0: HOST [n_theta] start values or NULL (zeros).  MNL_ERR_OOM when the
+ * request could never fit the budget; MNL_ERR_INVALID_ARG for a choice out of
+ * range; MNL_ERR_UNSUPPORTED beyond n_theta 1400 or K 256. */
+MNL_API int mnl_server_submit(mnl_server *s, const mnl_dims *dims, const mnl_data *host, const double *theta0,
+                              uint64_t *ticket);
+/* One tick: admit, iterate, retire.  Returns the numbers still admitted and queued. */
+MNL_API int mnl_server_step(mnl_server *s, int32_t *n_active, int32_t *n_queued);
+/* MNL_OK and the result (theta: HOST [n_theta] or NULL) once the request has
+ * finished - the ticket is then released; MNL_PENDING before that. */
+MNL_API int mnl_server_poll(mnl_server *s, uint64_t ticket, double *theta, mnl_request_result *result);
+/* Device bytes held by admitted requests. */
+MNL_API size_t mnl_server_memory_in_use(const mnl_server *s);
+MNL_API int mnl_server_destroy(mnl_server *s);
 
 /* Log-likelihood and gradient, as mnl_loglik_grad, without allocating any
  * device memory.  The paper has no counterpart: this is for callers that

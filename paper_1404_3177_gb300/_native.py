@@ -22,6 +22,7 @@ MNL_ERR_LINESEARCH = 6
 MNL_MAXITER = 7
 MNL_ERR_TIMEOUT = 8
 MNL_ERR_UNSUPPORTED = 9
+MNL_PENDING = 10
 
 MNL_FP64, MNL_TF32, MNL_BF16 = 0, 1, 2
 PRECISIONS = {"fp64": MNL_FP64, "tf32": MNL_TF32, "bf16": MNL_BF16}
@@ -33,7 +34,8 @@ EXPORTS = (
     "mnl_num_params", "mnl_status_string", "mnl_workspace_bytes", "mnl_fit_opts_default", "mnl_create",
     "mnl_upload", "mnl_loglik_grad", "mnl_hessian", "mnl_newton_step", "mnl_fit", "mnl_destroy",
     "mnl_loglik_grad_noalloc", "mnl_set_solve", "mnl_batch_create", "mnl_batch_num_params", "mnl_batch_fit",
-    "mnl_batch_destroy",
+    "mnl_batch_destroy", "mnl_server_opts_default", "mnl_server_create", "mnl_server_submit", "mnl_server_step",
+    "mnl_server_poll", "mnl_server_memory_in_use", "mnl_server_destroy",
 )
 
 MNL_SOLVE_AUTO, MNL_SOLVE_FP64, MNL_SOLVE_MIXED = 0, 1, 2
@@ -82,6 +84,17 @@ class mnl_batch_info(C.Structure):
     _fields_ = [("problems", C.POINTER(mnl_batch_problem_info)), ("iterations", C.c_int32),
                 ("converged", C.c_int32), ("failed", C.c_int32), ("pass_rows", C.c_int32),
                 ("t_total_ms", C.c_double), ("t_graph_ms", C.c_double)]
+
+
+class mnl_server_opts(C.Structure):
+    _fields_ = [("mem_budget", C.c_size_t), ("precision", C.c_int32), ("max_active", C.c_int32),
+                ("max_skips", C.c_int32), ("pad", C.c_int32), ("fit", mnl_fit_opts)]
+
+
+class mnl_request_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("stop_reason", C.c_int32), ("iters", C.c_int32), ("ls_evals", C.c_int32),
+                ("loglik", C.c_double), ("grad_inf", C.c_double), ("latency_ms", C.c_double),
+                ("queue_ms", C.c_double)]
 
 
 def struct_dict(s: C.Structure) -> dict:
@@ -138,6 +151,20 @@ def load() -> C.CDLL:
         lib.mnl_batch_fit.argtypes = [vp, C.POINTER(mnl_fit_opts), vp, C.POINTER(mnl_batch_info)]
         lib.mnl_batch_destroy.restype = i32
         lib.mnl_batch_destroy.argtypes = [vp]
+        lib.mnl_server_opts_default.restype = None
+        lib.mnl_server_opts_default.argtypes = [C.POINTER(mnl_server_opts)]
+        lib.mnl_server_create.restype = i32
+        lib.mnl_server_create.argtypes = [C.POINTER(mnl_server_opts), vp, C.POINTER(vp)]
+        lib.mnl_server_submit.restype = i32
+        lib.mnl_server_submit.argtypes = [vp, C.POINTER(mnl_dims), C.POINTER(mnl_data), vp, C.POINTER(C.c_uint64)]
+        lib.mnl_server_step.restype = i32
+        lib.mnl_server_step.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        lib.mnl_server_poll.restype = i32
+        lib.mnl_server_poll.argtypes = [vp, C.c_uint64, vp, C.POINTER(mnl_request_result)]
+        lib.mnl_server_memory_in_use.restype = C.c_size_t
+        lib.mnl_server_memory_in_use.argtypes = [vp]
+        lib.mnl_server_destroy.restype = i32
+        lib.mnl_server_destroy.argtypes = [vp]
         lib.mnl_set_solve.restype = i32
         lib.mnl_set_solve.argtypes = [vp, i32]
         lib.mnl_loglik_grad_noalloc.restype = i32
@@ -262,3 +289,47 @@ def mnl_batch_fit(handle: int, opts: mnl_fit_opts | None, theta_ptr: int, count:
 
 def mnl_batch_destroy(handle: int) -> None:
     _check(load().mnl_batch_destroy(C.c_void_p(handle)), "mnl_batch_destroy")
+
+
+def mnl_server_opts_default() -> mnl_server_opts:
+    o = mnl_server_opts()
+    load().mnl_server_opts_default(C.byref(o))
+    return o
+
+
+def mnl_server_create(opts: mnl_server_opts, stream: int | None) -> int:
+    h = C.c_void_p()
+    _check(load().mnl_server_create(C.byref(opts), C.c_void_p(stream or 0), C.byref(h)), "mnl_server_create")
+    return h.value
+
+
+def mnl_server_submit(handle: int, dims: mnl_dims, host_data: mnl_data, theta0_ptr: int | None) -> int:
+    t = C.c_uint64()
+    _check(load().mnl_server_submit(C.c_void_p(handle), C.byref(dims), C.byref(host_data),
+                                    C.c_void_p(theta0_ptr) if theta0_ptr else None, C.byref(t)), "mnl_server_submit")
+    return t.value
+
+
+def mnl_server_step(handle: int):
+    a, q = C.c_int32(), C.c_int32()
+    _check(load().mnl_server_step(C.c_void_p(handle), C.byref(a), C.byref(q)), "mnl_server_step")
+    return a.value, q.value
+
+
+def mnl_server_poll(handle: int, ticket: int, theta_ptr: int | None):
+    """(finished, result dict or None)."""
+    res = mnl_request_result()
+    rc = load().mnl_server_poll(C.c_void_p(handle), C.c_uint64(ticket), C.c_void_p(theta_ptr) if theta_ptr else None,
+                                C.byref(res))
+    if rc == MNL_PENDING:
+        return False, None
+    _check(rc, "mnl_server_poll")
+    return True, struct_dict(res)
+
+
+def mnl_server_memory_in_use(handle: int) -> int:
+    return int(load().mnl_server_memory_in_use(C.c_void_p(handle)))
+
+
+def mnl_server_destroy(handle: int) -> None:
+    _check(load().mnl_server_destroy(C.c_void_p(handle)), "mnl_server_destroy")

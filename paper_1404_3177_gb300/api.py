@@ -170,3 +170,72 @@ class MNLBatch:
 
     def __exit__(self, *a):
         self.close()
+
+
+class MNLServer:
+    """Continuous batching of fit requests (one Newton iteration of every admitted request per step)."""
+
+    def __init__(self, *, precision="bf16", mem_budget=80 << 30, max_active=4096, max_skips=8, stream=None, **fit):
+        o = nat.mnl_server_opts_default()
+        o.mem_budget = int(mem_budget)
+        o.precision = nat.PRECISIONS[precision]
+        o.max_active = max_active
+        o.max_skips = max_skips
+        for k, v in fit.items():
+            setattr(o.fit, k, v)
+        self.h = nat.mnl_server_create(o, (stream or torch.cuda.current_stream()).cuda_stream)
+        self._sizes = {}
+
+    def submit(self, X=None, Y=None, Z=None, choice=None, K=None, theta0=None):
+        """X, Y, Z, choice: numpy arrays (float32 / int32) on the host; returns a ticket."""
+        import numpy as np
+        N = choice.shape[0]
+        if Y is not None and Y.size:
+            K = Y.shape[1]
+        elif Z is not None and Z.size:
+            K = Z.shape[1]
+        p = X.shape[1] if X is not None else 0
+        d = Y.shape[2] if Y is not None and Y.size else 0
+        f = Z.shape[2] if Z is not None and Z.size else 0
+        arrs = [np.ascontiguousarray(a) if a is not None else None for a in (X, Y, Z)]
+        c = np.ascontiguousarray(choice, dtype=np.int32)
+        ptr = lambda a: a.ctypes.data if a is not None and a.size else None  # noqa: E731
+        dims = nat.mnl_dims(N, K, p, d, f, 0)
+        data = nat.mnl_data(ptr(arrs[0]), ptr(arrs[1]), ptr(arrs[2]), c.ctypes.data)
+        th = np.ascontiguousarray(theta0, dtype=np.float64) if theta0 is not None else None
+        t = nat.mnl_server_submit(self.h, dims, data, th.ctypes.data if th is not None else None)
+        self._sizes[t] = nat.mnl_num_params(dims)
+        return t
+
+    def step(self):
+        return nat.mnl_server_step(self.h)
+
+    def poll(self, ticket):
+        """(theta numpy array, result dict) once finished, else None."""
+        import numpy as np
+        out = np.empty(self._sizes[ticket])
+        done, res = nat.mnl_server_poll(self.h, ticket, out.ctypes.data)
+        if not done:
+            return None
+        del self._sizes[ticket]
+        return out, res
+
+    def memory_in_use(self):
+        return nat.mnl_server_memory_in_use(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            nat.mnl_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -421,6 +421,7 @@ const char *mnl_status_string(int s) {
     case MNL_MAXITER: return "maximum number of iterations reached";
     case MNL_ERR_TIMEOUT: return "a bounded device wait timed out";
     case MNL_ERR_UNSUPPORTED: return "unsupported configuration";
+    case MNL_PENDING: return "request still pending";
     default: return "unknown status";
   }
 }

@@ -21,6 +21,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <new>
@@ -162,81 +163,201 @@ void tune_store(const std::string &key, int v) {
 
 }  // namespace
 
-struct mnl_batch {
-  int count, prec;
-  OpType op;
-  bool fp64, mixed;
-  cudaStream_t user_st, st;
-  cudaEvent_t ev_user, ev_done, t0, t1;
-  int dev, nsm;
-  std::vector<Shape> shapes;
-  std::vector<GroupProblem> hp;   // host copy of the descriptors
-  std::vector<int64_t> theta_off;
-  int64_t theta_total;
-  GroupProblem *probs;
-  int *active, *pending, *accepted, *status, *stop, *counts, *h_counts;
-  int *err;
-  // grouped pass
-  GroupedPassPlan pfull, pll;
-  PassSeg *segs;
-  int *seg_start, *slot_start, *slot_segs;
-  double *partials;
-  // contractions
-  GroupItem *build_items, *z_items, *asm_items;
-  int n_build, n_z, n_asm;
-  size_t build_smem, z_smem, chol_smem;
-  CUtensorMap *maps;
-  SyrkUnit *units_main, *units_band;
-  int nunits_main, nunits_band;
-  void *main_part, *band_part, *z_part;
-  int64_t nmax;
-  // graph of one iteration (without the extra line-search rounds)
-  cudaGraphExec_t graph;
-  bool have_graph;
-  double graph_gtol;      // options baked into the captured graph
-  int graph_halvings;
-  std::vector<void *> allocs;
-};
 
 namespace {
 
-#define BCK(x)                                           \
-  do {                                                   \
-    cudaError_t e_ = (x);                                \
-    if (e_ != cudaSuccess) { cudaGetLastError(); return e_ == cudaErrorMemoryAllocation ? MNL_ERR_OOM : MNL_ERR_CUDA; } \
+#define BCK(x)                                                                              \
+  do {                                                                                      \
+    cudaError_t e_ = (x);                                                                   \
+    if (e_ != cudaSuccess) {                                                                \
+      cudaGetLastError();                                                                   \
+      return e_ == cudaErrorMemoryAllocation ? MNL_ERR_OOM : MNL_ERR_CUDA;                  \
+    }                                                                                       \
   } while (0)
 
-template <typename T>
-int balloc(mnl_batch *b, T **p, size_t bytes) {
-  *p = nullptr;
-  if (bytes == 0) return MNL_OK;
-  void *q = nullptr;
-  cudaError_t e = cudaMalloc(&q, bytes);
-  if (e != cudaSuccess) { cudaGetLastError(); return e == cudaErrorMemoryAllocation ? MNL_ERR_OOM : MNL_ERR_CUDA; }
-  b->allocs.push_back(q);
-  *p = reinterpret_cast<T *>(q);
-  return MNL_OK;
+// Stream, events and device properties shared by a batch or a server.
+struct Engine {
+  int prec = 0;
+  OpType op = OpType::BF16;
+  bool fp64 = false, mixed = true;
+  cudaStream_t user_st = nullptr, st = nullptr;
+  cudaEvent_t ev_user = nullptr, ev_done = nullptr, t0 = nullptr, t1 = nullptr;
+  int dev = 0, nsm = 148;
+  int *h_counts = nullptr;  // pinned: [0] active, [1] pending, [2] error word
+  int init(int precision, void *stream) {
+    prec = precision;
+    fp64 = precision == MNL_FP64;
+    op = fp64 ? OpType::F64 : precision == MNL_TF32 ? OpType::TF32 : OpType::BF16;
+    mixed = !fp64;
+    user_st = reinterpret_cast<cudaStream_t>(stream);
+    BCK(cudaGetDevice(&dev));
+    BCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    BCK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    BCK(cudaEventCreateWithFlags(&ev_user, cudaEventDisableTiming));
+    BCK(cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming));
+    BCK(cudaEventCreate(&t0));
+    BCK(cudaEventCreate(&t1));
+    BCK(cudaMallocHost(&h_counts, 4 * sizeof(int)));
+    return MNL_OK;
+  }
+  void release() {
+    if (h_counts) cudaFreeHost(h_counts);
+    if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t e : {ev_user, ev_done, t0, t1})
+      if (e) cudaEventDestroy(e);
+    h_counts = nullptr;
+    st = nullptr;
+    ev_user = ev_done = t0 = t1 = nullptr;
+  }
+};
+
+// Persistent device state of one problem, laid out in one chunk.
+struct ProbLayout {
+  Shape s;
+  int64_t ldn = 0, mc_pad = 0;
+  int nt1d = 0, build_ob = 64, build_kc = 1, zrows = 1, zsplit = 1;
+  std::vector<int2> bands;
+  std::vector<int> band_map;
+  size_t P = 0, zbar = 0, At = 0, Ad = 0, F = 0, F32 = 0, grad = 0, delta = 0, scal = 0, rwork = 0, band_of = 0;
+  size_t theta = 0, X = 0, Y = 0, Z = 0, choice = 0;  // owned copies (server requests)
+  size_t bytes = 0;
+};
+
+ProbLayout layout_problem(const mnl_dims &d, OpType op, bool fp64, bool mixed, bool own) {
+  ProbLayout L;
+  const Shape s = make_shape(d);
+  L.s = s;
+  const size_t tsz = fp64 ? 8 : 4;
+  const size_t esz = fp64 ? 8 : op == OpType::TF32 ? 4 : 2;
+  L.ldn = round_up(s.N, 64);
+  L.mc_pad = round_up(s.mc, kTile);
+  L.nt1d = (int)(L.mc_pad / kTile);
+  build_blocking(s, op, &L.build_ob, &L.build_kc);
+  L.zrows = zblocks_rows(s, fp64);
+  L.zsplit = (int)std::max<int64_t>(1, s.N / 4096);
+  L.band_map.assign((size_t)L.nt1d * L.nt1d, -1);
+  if (s.q > 0)
+    for (int k = 1; k < s.K; ++k) {
+      const int lo = (int)((int64_t)(k - 1) * s.q / kTile), hi = (int)(((int64_t)k * s.q - 1) / kTile);
+      for (int ti = lo; ti <= hi; ++ti)
+        for (int tj = lo; tj <= ti; ++tj)
+          if (L.band_map[(size_t)ti * L.nt1d + tj] < 0) {
+            L.band_map[(size_t)ti * L.nt1d + tj] = (int)L.bands.size();
+            L.bands.push_back(make_int2(ti, tj));
+          }
+    }
+  size_t b = 0;
+  auto take = [&](size_t nbytes) { const size_t at = b; b += (nbytes + 255) & ~(size_t)255; return at; };
+  L.P = take((size_t)s.N * s.K * tsz);
+  L.zbar = take((size_t)s.N * s.f * tsz);
+  L.At = take((size_t)L.mc_pad * L.ldn * esz);
+  L.Ad = take((size_t)L.mc_pad * L.ldn * esz);
+  L.F = take((size_t)s.n * s.n * 8);
+  L.F32 = mixed ? take((size_t)s.n * s.n * 4) : 0;
+  L.grad = take((size_t)s.n * 8);
+  L.delta = take((size_t)s.n * 8);
+  L.scal = take(kGsCount * 8);
+  L.rwork = take((size_t)2 * s.n * 8);
+  L.band_of = take(L.band_map.size() * sizeof(int));
+  if (own) {
+    L.theta = take((size_t)s.n * 8);
+    L.X = take((size_t)s.N * s.p * 4);
+    L.Y = take((size_t)s.N * s.K * s.d * 4);
+    L.Z = take((size_t)s.N * s.K * s.f * 4);
+    L.choice = take((size_t)s.N * 4);
+  }
+  L.bytes = b;
+  return L;
 }
 
-void bfree(mnl_batch *b) {
-  if (b->have_graph) cudaGraphExecDestroy(b->graph);
-  for (void *p : b->allocs) cudaFree(p);
-  b->allocs.clear();
-  if (b->h_counts) cudaFreeHost(b->h_counts);
-  if (b->st) cudaStreamDestroy(b->st);
-  for (cudaEvent_t e : {b->ev_user, b->ev_done, b->t0, b->t1})
-    if (e) cudaEventDestroy(e);
+// Descriptor of a problem whose chunk starts at `base`; data and theta either
+// given (batch) or inside the chunk (server).
+void bind_problem(const ProbLayout &L, unsigned char *base, const mnl_data *data, double *theta, GroupProblem &g) {
+  std::memset(&g, 0, sizeof(g));
+  const Shape &s = L.s;
+  g.N = s.N; g.K = s.K; g.p = s.p; g.d = s.d; g.f = s.f; g.n = s.n; g.mc = s.mc;
+  if (data) {
+    g.X = data->X; g.Y = data->Y; g.Z = data->Z; g.choice = data->choice;
+  } else {
+    g.X = reinterpret_cast<const float *>(base + L.X);
+    g.Y = reinterpret_cast<const float *>(base + L.Y);
+    g.Z = reinterpret_cast<const float *>(base + L.Z);
+    g.choice = reinterpret_cast<const int32_t *>(base + L.choice);
+  }
+  g.theta = theta ? theta : reinterpret_cast<double *>(base + L.theta);
+  g.grad = reinterpret_cast<double *>(base + L.grad);
+  g.delta = reinterpret_cast<double *>(base + L.delta);
+  g.P = base + L.P;
+  g.zbar = base + L.zbar;
+  g.At = base + L.At;
+  g.Ad = base + L.Ad;
+  g.ldn = L.ldn;
+  g.mc_pad = L.mc_pad;
+  g.nt1d = L.nt1d;
+  g.zsplit = L.zsplit;
+  g.zrows = L.zrows;
+  g.build_ob = L.build_ob;
+  g.build_kc = L.build_kc;
+  g.band_of = reinterpret_cast<int *>(base + L.band_of);
+  g.F = reinterpret_cast<double *>(base + L.F);
+  g.F32 = L.F32 ? reinterpret_cast<float *>(base + L.F32) : nullptr;
+  g.rwork = reinterpret_cast<double *>(base + L.rwork);
+  g.scal = reinterpret_cast<double *>(base + L.scal);
 }
+
+// Grow-only device buffer.
+struct DBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+  int ensure(size_t bytes) {
+    if (bytes <= cap) return MNL_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    const size_t want = std::max(bytes, cap + cap / 2);
+    if (cudaMalloc(&p, want) != cudaSuccess) { cudaGetLastError(); return MNL_ERR_OOM; }
+    cap = want;
+    return MNL_OK;
+  }
+  void release() { if (p) cudaFree(p); p = nullptr; cap = 0; }
+  template <typename T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// Descriptors, flags and work lists of the problems being iterated together.
+struct WorkSet {
+  int count = 0;
+  int rows = 16;
+  std::vector<GroupProblem> hp;     // host copy of the descriptors
+  std::vector<Shape> shapes;
+  DBuf probs, flags, counts, err, segs, seg_start, slot_start, slot_segs, partials;
+  DBuf build_items, z_items, asm_items, maps, units_main, units_band, main_part, band_part, z_part;
+  GroupedPassPlan pfull{}, pll{};
+  int n_build = 0, n_z = 0, n_asm = 0, nunits_main = 0, nunits_band = 0;
+  size_t build_smem = 0, z_smem = 0, chol_smem = 0;
+  int64_t nmax = 0;
+  int *active() const { return flags.as<int>(); }
+  int *pending() const { return flags.as<int>() + count; }
+  int *accepted() const { return flags.as<int>() + 2 * count; }
+  int *status() const { return flags.as<int>() + 3 * count; }
+  int *stop() const { return flags.as<int>() + 4 * count; }
+  void release() {
+    for (DBuf *d : {&probs, &flags, &counts, &err, &segs, &seg_start, &slot_start, &slot_segs, &partials, &build_items,
+                    &z_items, &asm_items, &maps, &units_main, &units_band, &main_part, &band_part, &z_part})
+      d->release();
+  }
+};
 
 // Pass segments: the tiles of all problems in order, cut into one contiguous
 // range per CTA of about equal cost, then at problem boundaries.
-int build_pass_lists(mnl_batch *b, int rows, int grid, std::vector<PassSeg> &segs, std::vector<int> &seg_start,
-                     std::vector<int> &slot_start, std::vector<int> &slot_segs, int64_t *partial_len) {
+void build_pass_lists(const std::vector<Shape> &shapes, int rows, int grid, std::vector<PassSeg> &segs,
+                      std::vector<int> &seg_start, std::vector<int> &slot_start, std::vector<int> &slot_segs,
+                      int64_t *partial_len) {
   struct TileRun { int problem; int64_t ntiles; double cost; };
   std::vector<TileRun> runs;
   double total = 0.0;
-  for (int i = 0; i < b->count; ++i) {
-    const Shape &s = b->shapes[i];
+  const int count = (int)shapes.size();
+  for (int i = 0; i < count; ++i) {
+    const Shape &s = shapes[i];
     const int64_t nt = (s.N + rows - 1) / rows;
     const double c = (double)rows * s.K * (s.p + s.d + s.f + 1) + (double)s.nout;
     runs.push_back({i, nt, c});
@@ -244,7 +365,7 @@ int build_pass_lists(mnl_batch *b, int rows, int grid, std::vector<PassSeg> &seg
   }
   segs.clear();
   seg_start.assign(grid + 1, 0);
-  std::vector<std::vector<int>> per_prob(b->count);
+  std::vector<std::vector<int>> per_prob(count);
   int64_t off_full = 0, off_ll = 0;
   double acc = 0.0;
   size_t ri = 0;
@@ -254,7 +375,6 @@ int build_pass_lists(mnl_batch *b, int rows, int grid, std::vector<PassSeg> &seg
     const double target = total * (c + 1) / grid;
     while (ri < runs.size() && (acc < target - 1e-9 || c == grid - 1)) {
       const TileRun &r = runs[ri];
-      // tiles of this run that fit below the target
       int64_t take = r.ntiles - ti;
       if (c < grid - 1) {
         const int64_t fit = (int64_t)std::ceil((target - acc) / r.cost - 1e-9);
@@ -266,7 +386,7 @@ int build_pass_lists(mnl_batch *b, int rows, int grid, std::vector<PassSeg> &seg
       sg.tile1 = ti + take;
       sg.slot_full = off_full;
       sg.slot_ll = off_ll;
-      off_full += 2 + b->shapes[r.problem].n;
+      off_full += 2 + shapes[r.problem].n;
       off_ll += 2;
       per_prob[r.problem].push_back((int)segs.size());
       segs.push_back(sg);
@@ -277,43 +397,207 @@ int build_pass_lists(mnl_batch *b, int rows, int grid, std::vector<PassSeg> &seg
     }
   }
   seg_start[grid] = (int)segs.size();
-  slot_start.assign(b->count + 1, 0);
+  slot_start.assign(count + 1, 0);
   slot_segs.clear();
-  for (int i = 0; i < b->count; ++i) {
+  for (int i = 0; i < count; ++i) {
     slot_start[i] = (int)slot_segs.size();
     for (int s : per_prob[i]) slot_segs.push_back(s);
   }
-  slot_start[b->count] = (int)slot_segs.size();
+  slot_start[count] = (int)slot_segs.size();
   *partial_len = std::max(off_full, off_ll);
+}
+
+template <typename T>
+int upload(DBuf &d, const std::vector<T> &v, cudaStream_t st) {
+  int rc = d.ensure(std::max<size_t>(1, v.size()) * sizeof(T));
+  if (rc) return rc;
+  if (!v.empty()) BCK(cudaMemcpyAsync(d.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
   return MNL_OK;
 }
 
-int upload_pass_lists(mnl_batch *b, const std::vector<PassSeg> &segs, const std::vector<int> &seg_start,
-                      const std::vector<int> &slot_start, const std::vector<int> &slot_segs, int64_t plen) {
+// (Re)build a work set over the descriptors W.hp (persistent pointers already
+// bound) with layouts L; fills the per-set partial offsets and work lists.
+int ws_build(Engine &E, WorkSet &W, const std::vector<const ProbLayout *> &L, int rows) {
+  const int count = W.count = (int)W.hp.size();
+  W.rows = rows;
+  W.shapes.clear();
+  for (const ProbLayout *l : L) W.shapes.push_back(l->s);
   int rc;
-  if ((rc = balloc(b, &b->segs, segs.size() * sizeof(PassSeg))) ||
-      (rc = balloc(b, &b->seg_start, seg_start.size() * sizeof(int))) ||
-      (rc = balloc(b, &b->slot_start, slot_start.size() * sizeof(int))) ||
-      (rc = balloc(b, &b->slot_segs, slot_segs.size() * sizeof(int))) ||
-      (rc = balloc(b, &b->partials, (size_t)plen * sizeof(double))))
+  // contraction partials: per-set offsets
+  const size_t csz = E.fp64 ? 8 : 4, tsz = E.fp64 ? 8 : 4;
+  int64_t main_elems = 0, band_elems = 0, z_elems = 0;
+  W.nmax = 0;
+  for (int i = 0; i < count; ++i) {
+    GroupProblem &g = W.hp[i];
+    const ProbLayout &l = *L[i];
+    g.main_off = main_elems;
+    main_elems += (int64_t)l.nt1d * (l.nt1d + 1) / 2 * kTile * kTile;
+    g.band_off = band_elems;
+    band_elems += (int64_t)l.bands.size() * kTile * kTile;
+    g.z_off = z_elems;
+    if (l.s.f > 0) z_elems += (int64_t)l.zsplit * zblocks_outputs(l.s);
+    W.nmax = std::max(W.nmax, l.s.n);
+  }
+  if ((rc = W.main_part.ensure(std::max<int64_t>(1, main_elems) * csz)) ||
+      (rc = W.band_part.ensure(std::max<int64_t>(1, band_elems) * csz)) ||
+      (rc = W.z_part.ensure(std::max<int64_t>(1, z_elems) * tsz)))
     return rc;
-  BCK(cudaMemcpy(b->segs, segs.data(), segs.size() * sizeof(PassSeg), cudaMemcpyHostToDevice));
-  BCK(cudaMemcpy(b->seg_start, seg_start.data(), seg_start.size() * sizeof(int), cudaMemcpyHostToDevice));
-  BCK(cudaMemcpy(b->slot_start, slot_start.data(), slot_start.size() * sizeof(int), cudaMemcpyHostToDevice));
-  if (!slot_segs.empty())
-    BCK(cudaMemcpy(b->slot_segs, slot_segs.data(), slot_segs.size() * sizeof(int), cudaMemcpyHostToDevice));
+  // items
+  std::vector<GroupItem> bi, zi, ai;
+  size_t bsm = 0, zsm = 0;
+  for (int i = 0; i < count; ++i) {
+    const ProbLayout &l = *L[i];
+    const Shape &s = l.s;
+    if (s.mc > 0) {
+      const int nblk = (int)((s.N + l.build_ob - 1) / l.build_ob);
+      for (int k = 0; k < nblk; ++k) bi.push_back({i, k});
+      bsm = std::max(bsm, build_smem_bytes(s, E.op, l.build_ob, l.build_kc));
+    }
+    if (s.f > 0) {
+      const int64_t nzt = zblocks_outputs(s);
+      const int chunks = (int)((nzt + 8191) / 8192);
+      for (int k = 0; k < l.zsplit * chunks; ++k) zi.push_back({i, k});
+      zsm = std::max(zsm, zblocks_smem(s, l.zrows, E.fp64));
+    }
+    const int ncb = (int)((s.n + kAssembleCols - 1) / kAssembleCols);
+    for (int k = 0; k < ncb; ++k) ai.push_back({i, k});
+  }
+  W.n_build = (int)bi.size();
+  W.n_z = (int)zi.size();
+  W.n_asm = (int)ai.size();
+  W.build_smem = bsm;
+  W.z_smem = zsm;
+  W.chol_smem = grouped_chol_smem(W.nmax);
+  if (bsm > 200 * 1024 || zsm > 200 * 1024 || W.chol_smem > 220 * 1024) return MNL_ERR_UNSUPPORTED;
+  if ((rc = upload(W.build_items, bi, E.st)) || (rc = upload(W.z_items, zi, E.st)) ||
+      (rc = upload(W.asm_items, ai, E.st)))
+    return rc;
+  // contraction units (longest K range first, dealt round-robin over the CTAs)
+  std::vector<CUtensorMap> maps(E.fp64 ? 1 : 2 * (size_t)count);
+  std::vector<SyrkUnit> um, ub;
+  for (int i = 0; i < count; ++i) {
+    const GroupProblem &g = W.hp[i];
+    const ProbLayout &l = *L[i];
+    if (l.s.mc == 0) continue;
+    if (!E.fp64 && (encode_operand_map(E.op, g.At, g.mc_pad, g.ldn, &maps[2 * i]) != cudaSuccess ||
+                    encode_operand_map(E.op, g.Ad, g.mc_pad, g.ldn, &maps[2 * i + 1]) != cudaSuccess))
+      return MNL_ERR_CUDA;
+    const int kb = E.fp64 ? (int)(g.ldn / f64_chunk_rows()) : tc_kblocks(E.op, g.ldn);
+    const int mA = E.fp64 ? 0 : 2 * i, mD = E.fp64 ? 1 : 2 * i + 1;
+    int t = 0;
+    for (int ti = 0; ti < l.nt1d; ++ti)
+      for (int tj = 0; tj <= ti; ++tj, ++t)
+        um.push_back({mA, i, ti, tj, 0, kb, g.main_off + (int64_t)t * kTile * kTile});
+    for (size_t k = 0; k < l.bands.size(); ++k)
+      ub.push_back({mD, i, l.bands[k].x, l.bands[k].y, 0, kb, g.band_off + (int64_t)k * kTile * kTile});
+  }
+  auto by_len = [](const SyrkUnit &a, const SyrkUnit &c) { return (a.kb1 - a.kb0) > (c.kb1 - c.kb0); };
+  std::stable_sort(um.begin(), um.end(), by_len);
+  std::stable_sort(ub.begin(), ub.end(), by_len);
+  W.nunits_main = (int)um.size();
+  W.nunits_band = (int)ub.size();
+  if ((rc = upload(W.maps, maps, E.st)) || (rc = upload(W.units_main, um, E.st)) || (rc = upload(W.units_band, ub, E.st)))
+    return rc;
+  // grouped pass
+  W.pfull = plan_grouped_pass(W.shapes, E.fp64, rows, E.nsm);
+  if (!W.pfull.ok) return MNL_ERR_UNSUPPORTED;
+  W.pll = W.pfull;
+  std::vector<PassSeg> segs;
+  std::vector<int> ss, sl, sls;
+  int64_t plen = 0;
+  build_pass_lists(W.shapes, rows, W.pfull.grid, segs, ss, sl, sls, &plen);
+  if ((rc = upload(W.segs, segs, E.st)) || (rc = upload(W.seg_start, ss, E.st)) || (rc = upload(W.slot_start, sl, E.st)) ||
+      (rc = upload(W.slot_segs, sls, E.st)) || (rc = W.partials.ensure(std::max<int64_t>(1, plen) * sizeof(double))))
+    return rc;
+  // descriptors and flags
+  if ((rc = upload(W.probs, W.hp, E.st)) || (rc = W.flags.ensure(5 * (size_t)count * sizeof(int))) ||
+      (rc = W.counts.ensure(4 * sizeof(int))) || (rc = W.err.ensure(sizeof(int))))
+    return rc;
+  BCK(cudaMemsetAsync(W.flags.p, 0, 5 * (size_t)count * sizeof(int), E.st));
   return MNL_OK;
 }
 
-// Grouped log-likelihood pass over all problems at theta (delta ignored: t = 0
-// is not used; the pass reads theta + t delta, so set t = 0 first) - used to
-// time tile heights.
-int autotune_rows(mnl_batch *b, int *rows_out) {
-  std::string key = std::string(b->fp64 ? "f64" : "f32") + ":";
+const GroupProblem *dprobs(const WorkSet &W) { return W.probs.as<GroupProblem>(); }
+
+int enqueue_iteration(Engine &E, WorkSet &W, const mnl_fit_opts &o) {
+  const int np = W.count;
+  const int tb = 256, nb = (np + tb - 1) / tb;
+  const GroupProblem *P = dprobs(W);
+  BCK(launch_grouped_pass(W.pfull, E.fp64, true, P, W.segs.as<PassSeg>(), W.seg_start.as<int>(), W.active(),
+                          W.partials.as<double>(), E.st));
+  BCK(launch_grouped_reduce(np, true, P, W.slot_start.as<int>(), W.segs.as<PassSeg>(), W.slot_segs.as<int>(),
+                            W.active(), W.partials.as<double>(), kGsL, E.st));
+  gtol_check_kernel<<<nb, tb, 0, E.st>>>(np, P, W.active(), W.status(), W.stop(), o.gtol);
+  BCK(cudaGetLastError());
+  BCK(launch_grouped_build(E.op, P, W.build_items.as<GroupItem>(), W.n_build, W.active(), W.build_smem, E.st));
+  if (E.fp64) {
+    BCK(launch_grouped_syrk_f64(P, W.units_main.as<SyrkUnit>(), W.nunits_main, W.active(), W.main_part.as<double>(),
+                                E.st));
+    BCK(launch_grouped_syrk_f64(P, W.units_band.as<SyrkUnit>(), W.nunits_band, W.active(), W.band_part.as<double>(),
+                                E.st));
+  } else {
+    BCK(launch_syrk_tc(E.op, W.maps.as<CUtensorMap>(), W.units_main.as<SyrkUnit>(), W.nunits_main, W.active(), E.nsm,
+                       W.main_part.as<float>(), W.err.as<int>(), E.st));
+    BCK(launch_syrk_tc(E.op, W.maps.as<CUtensorMap>(), W.units_band.as<SyrkUnit>(), W.nunits_band, W.active(), E.nsm,
+                       W.band_part.as<float>(), W.err.as<int>(), E.st));
+  }
+  BCK(launch_grouped_zblocks(E.fp64, P, W.z_items.as<GroupItem>(), W.n_z, W.active(), W.z_smem, W.z_part.p, E.st));
+  BCK(launch_grouped_assemble(E.fp64, P, W.asm_items.as<GroupItem>(), W.n_asm, W.active(), W.main_part.p,
+                              W.band_part.p, W.z_part.p, E.st));
+  BCK(launch_grouped_chol_solve(E.mixed, P, np, W.active(), 5, W.status(), W.chol_smem, E.st));
+  ls_init_kernel<<<nb, tb, 0, E.st>>>(np, P, W.active(), W.pending(), W.status());
+  BCK(cudaGetLastError());
+  return MNL_OK;
+}
+
+int enqueue_ls_round(Engine &E, WorkSet &W, const mnl_fit_opts &o) {
+  const int np = W.count;
+  const int tb = 256, nb = (np + tb - 1) / tb;
+  const GroupProblem *P = dprobs(W);
+  BCK(launch_grouped_pass(W.pll, E.fp64, false, P, W.segs.as<PassSeg>(), W.seg_start.as<int>(), W.pending(),
+                          W.partials.as<double>(), E.st));
+  BCK(launch_grouped_reduce(np, false, P, W.slot_start.as<int>(), W.segs.as<PassSeg>(), W.slot_segs.as<int>(),
+                            W.pending(), W.partials.as<double>(), kGsLt, E.st));
+  const double u = E.fp64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
+  ls_update_kernel<<<nb, tb, 0, E.st>>>(np, P, W.pending(), W.accepted(), W.active(), W.status(), u, o.max_halvings);
+  BCK(cudaGetLastError());
+  count_kernel<<<1, 256, 0, E.st>>>(np, W.active(), W.pending(), W.counts.as<int>());
+  BCK(cudaGetLastError());
+  return MNL_OK;
+}
+
+// After enqueue_iteration + one enqueue_ls_round: the remaining line-search
+// rounds (host loop), the coefficient update and the count of problems still
+// iterating (E.h_counts[0]).
+int finish_iteration(Engine &E, WorkSet &W, const mnl_fit_opts &o, double steptol) {
+  BCK(cudaMemcpyAsync(E.h_counts, W.counts.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, E.st));
+  BCK(cudaStreamSynchronize(E.st));
+  int rounds = 1;
+  while (E.h_counts[1] > 0 && rounds <= o.max_halvings) {
+    int rc = enqueue_ls_round(E, W, o);
+    if (rc) return rc;
+    BCK(cudaMemcpyAsync(E.h_counts, W.counts.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, E.st));
+    BCK(cudaStreamSynchronize(E.st));
+    ++rounds;
+  }
+  const int np = W.count;
+  theta_update_kernel<<<np, 256, 0, E.st>>>(dprobs(W), W.accepted(), W.active(), W.stop(), steptol, o.ftol);
+  count_kernel<<<1, 256, 0, E.st>>>(np, W.active(), W.pending(), W.counts.as<int>());
+  BCK(cudaGetLastError());
+  BCK(cudaMemcpyAsync(E.h_counts, W.counts.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, E.st));
+  BCK(cudaMemcpyAsync(E.h_counts + 2, W.err.p, sizeof(int), cudaMemcpyDeviceToHost, E.st));
+  BCK(cudaStreamSynchronize(E.st));
+  if (E.h_counts[2]) return MNL_ERR_TIMEOUT;
+  return MNL_OK;
+}
+
+// Time the grouped log-likelihood pass for a few tile heights (theta = 0).
+int autotune_rows(Engine &E, WorkSet &W, const std::vector<const ProbLayout *> &L, double *theta0, int *rows_out) {
+  std::string key = std::string(E.fp64 ? "f64" : "f32") + ":";
   {
     int64_t sN = 0, sK = 0, sq = 0;
-    for (const Shape &s : b->shapes) { sN += s.N; sK += s.K; sq += s.p + s.d + s.f; }
-    key += std::to_string(b->count) + "," + std::to_string(sN) + "," + std::to_string(sK) + "," + std::to_string(sq);
+    for (const ProbLayout *l : L) { sN += l->s.N; sK += l->s.K; sq += l->s.p + l->s.d + l->s.f; }
+    key += std::to_string(L.size()) + "," + std::to_string(sN) + "," + std::to_string(sK) + "," + std::to_string(sq);
   }
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -321,42 +605,32 @@ int autotune_rows(mnl_batch *b, int *rows_out) {
     auto it = g_tune.find(key);
     if (it != g_tune.end()) { *rows_out = it->second; return MNL_OK; }
   }
+  // a scratch copy of the descriptors with theta = delta = 0 and every problem pending
+  std::vector<GroupProblem> saved = W.hp;
+  for (size_t i = 0; i < W.hp.size(); ++i) { W.hp[i].theta = theta0; W.hp[i].delta = theta0; }
   static const int cands[] = {8, 16, 32};
   float best = 1e30f;
   int best_rows = 16;
   for (int rows : cands) {
-    GroupedPassPlan pl = plan_grouped_pass(b->shapes, b->fp64, rows, b->nsm);
-    if (!pl.ok) continue;
-    std::vector<PassSeg> segs;
-    std::vector<int> ss, sl, sls;
-    int64_t plen = 0;
-    build_pass_lists(b, rows, pl.grid, segs, ss, sl, sls, &plen);
-    PassSeg *d_segs = nullptr;
-    int *d_ss = nullptr;
-    double *d_part = nullptr;
-    if (cudaMalloc(&d_segs, segs.size() * sizeof(PassSeg)) != cudaSuccess ||
-        cudaMalloc(&d_ss, ss.size() * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&d_part, (size_t)plen * sizeof(double)) != cudaSuccess) {
-      cudaGetLastError();
-      cudaFree(d_segs); cudaFree(d_ss); cudaFree(d_part);
-      continue;
-    }
-    cudaMemcpy(d_segs, segs.data(), segs.size() * sizeof(PassSeg), cudaMemcpyHostToDevice);
-    cudaMemcpy(d_ss, ss.data(), ss.size() * sizeof(int), cudaMemcpyHostToDevice);
+    int rc = ws_build(E, W, L, rows);
+    if (rc) continue;
+    std::vector<int> ones(W.count, 1);
+    BCK(cudaMemcpyAsync(W.pending(), ones.data(), ones.size() * sizeof(int), cudaMemcpyHostToDevice, E.st));
+    for (const GroupProblem &g : W.hp) BCK(cudaMemsetAsync(g.scal, 0, kGsCount * sizeof(double), E.st));
     float ms = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
-      cudaEventRecord(b->t0, b->st);
-      launch_grouped_pass(pl, b->fp64, false, b->probs, d_segs, d_ss, b->active, d_part, b->st);
-      cudaEventRecord(b->t1, b->st);
-      cudaEventSynchronize(b->t1);
+      BCK(cudaEventRecord(E.t0, E.st));
+      BCK(launch_grouped_pass(W.pll, E.fp64, false, dprobs(W), W.segs.as<PassSeg>(), W.seg_start.as<int>(),
+                              W.pending(), W.partials.as<double>(), E.st));
+      BCK(cudaEventRecord(E.t1, E.st));
+      BCK(cudaEventSynchronize(E.t1));
       float m = 0.f;
-      cudaEventElapsedTime(&m, b->t0, b->t1);
+      cudaEventElapsedTime(&m, E.t0, E.t1);
       if (rep > 0) ms = std::min(ms, m);
     }
-    cudaFree(d_segs); cudaFree(d_ss); cudaFree(d_part);
-    if (cudaGetLastError() != cudaSuccess) continue;
     if (ms < best) { best = ms; best_rows = rows; }
   }
+  W.hp = saved;
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     tune_store(key, best_rows);
@@ -365,51 +639,33 @@ int autotune_rows(mnl_batch *b, int *rows_out) {
   return MNL_OK;
 }
 
-int enqueue_iteration(mnl_batch *b, const mnl_fit_opts &o) {
-  const int np = b->count;
-  const int tb = 256, nb = (np + tb - 1) / tb;
-  BCK(launch_grouped_pass(b->pfull, b->fp64, true, b->probs, b->segs, b->seg_start, b->active, b->partials, b->st));
-  BCK(launch_grouped_reduce(np, true, b->probs, b->slot_start, b->segs, b->slot_segs, b->active, b->partials, kGsL,
-                            b->st));
-  gtol_check_kernel<<<nb, tb, 0, b->st>>>(np, b->probs, b->active, b->status, b->stop, o.gtol);
-  BCK(cudaGetLastError());
-  BCK(launch_grouped_build(b->op, b->probs, b->build_items, b->n_build, b->active, b->build_smem, b->st));
-  if (b->fp64) {
-    BCK(launch_grouped_syrk_f64(b->probs, b->units_main, b->nunits_main, b->active,
-                                reinterpret_cast<double *>(b->main_part), b->st));
-    BCK(launch_grouped_syrk_f64(b->probs, b->units_band, b->nunits_band, b->active,
-                                reinterpret_cast<double *>(b->band_part), b->st));
-  } else {
-    BCK(launch_syrk_tc(b->op, b->maps, b->units_main, b->nunits_main, b->active, b->nsm,
-                       reinterpret_cast<float *>(b->main_part), b->err, b->st));
-    BCK(launch_syrk_tc(b->op, b->maps, b->units_band, b->nunits_band, b->active, b->nsm,
-                       reinterpret_cast<float *>(b->band_part), b->err, b->st));
-  }
-  BCK(launch_grouped_zblocks(b->fp64, b->probs, b->z_items, b->n_z, b->active, b->z_smem, b->z_part, b->st));
-  BCK(launch_grouped_assemble(b->fp64, b->probs, b->asm_items, b->n_asm, b->active, b->main_part, b->band_part,
-                              b->z_part, b->st));
-  BCK(launch_grouped_chol_solve(b->mixed, b->probs, np, b->active, 5, b->status, b->chol_smem, b->st));
-  ls_init_kernel<<<nb, tb, 0, b->st>>>(np, b->probs, b->active, b->pending, b->status);
-  BCK(cudaGetLastError());
-  return MNL_OK;
-}
-
-int enqueue_ls_round(mnl_batch *b, const mnl_fit_opts &o) {
-  const int np = b->count;
-  const int tb = 256, nb = (np + tb - 1) / tb;
-  BCK(launch_grouped_pass(b->pll, b->fp64, false, b->probs, b->segs, b->seg_start, b->pending, b->partials, b->st));
-  BCK(launch_grouped_reduce(np, false, b->probs, b->slot_start, b->segs, b->slot_segs, b->pending, b->partials, kGsLt,
-                            b->st));
-  const double u = b->fp64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
-  ls_update_kernel<<<nb, tb, 0, b->st>>>(np, b->probs, b->pending, b->accepted, b->active, b->status, u,
-                                         o.max_halvings);
-  BCK(cudaGetLastError());
-  count_kernel<<<1, 256, 0, b->st>>>(np, b->active, b->pending, b->counts);
-  BCK(cudaGetLastError());
-  return MNL_OK;
-}
-
 }  // namespace
+
+// ===========================================================================
+// Batched fits over a fixed set of problems (one CUDA graph per iteration).
+// ===========================================================================
+
+struct mnl_batch {
+  Engine E;
+  WorkSet W;
+  std::vector<ProbLayout> layouts;
+  std::vector<const ProbLayout *> lp;
+  std::vector<int64_t> theta_off;
+  int64_t theta_total = 0;
+  unsigned char *arena = nullptr;
+  double *theta0 = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  bool have_graph = false;
+  double graph_gtol = 0.0;
+  int graph_halvings = 0;
+  void release() {
+    if (have_graph) cudaGraphExecDestroy(graph);
+    W.release();
+    if (arena) cudaFree(arena);
+    if (theta0) cudaFree(theta0);
+    E.release();
+  }
+};
 
 extern "C" {
 
@@ -427,225 +683,43 @@ int mnl_batch_create(int count, const mnl_dims *dims, const mnl_data *data, int 
   }
   mnl_batch *b = new (std::nothrow) mnl_batch();
   if (!b) return MNL_ERR_OOM;
-  auto fail = [&](int rc) { bfree(b); delete b; return rc; };
-  b->count = count;
-  b->prec = precision;
-  b->fp64 = precision == MNL_FP64;
-  b->op = precision == MNL_FP64 ? OpType::F64 : precision == MNL_TF32 ? OpType::TF32 : OpType::BF16;
-  b->mixed = !b->fp64;
-  b->user_st = reinterpret_cast<cudaStream_t>(stream);
-  if (cudaGetDevice(&b->dev) != cudaSuccess) { cudaGetLastError(); return fail(MNL_ERR_CUDA); }
-  cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, b->dev);
-  if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->ev_user, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreate(&b->t0) != cudaSuccess || cudaEventCreate(&b->t1) != cudaSuccess ||
-      cudaMallocHost(&b->h_counts, 4 * sizeof(int)) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(MNL_ERR_CUDA);
-  }
+  auto fail = [&](int rc) { b->release(); delete b; return rc; };
   int rc;
-  const size_t tsz = b->fp64 ? 8 : 4;
-  const size_t esz = b->fp64 ? 8 : b->op == OpType::TF32 ? 4 : 2;
-  // shapes, offsets and the per-problem arena
-  b->theta_total = 0;
-  b->nmax = 0;
+  if ((rc = b->E.init(precision, stream))) return fail(rc);
+  Engine &E = b->E;
   size_t bytes = 0;
-  struct Off { size_t P, zbar, At, Ad, F, F32, grad, delta, scal, rwork, band_of; };
-  std::vector<Off> offs(count);
-  std::vector<std::vector<int2>> bands(count);
-  std::vector<std::vector<int>> band_maps(count);
-  int64_t main_elems = 0, band_elems = 0, z_elems = 0;
-  b->hp.resize(count);
+  std::vector<size_t> base(count);
   for (int i = 0; i < count; ++i) {
-    const Shape s = make_shape(dims[i]);
-    b->shapes.push_back(s);
+    b->layouts.push_back(layout_problem(dims[i], E.op, E.fp64, E.mixed, false));
+    if (b->layouts.back().s.n > 1400) return fail(MNL_ERR_UNSUPPORTED);
+    base[i] = bytes;
+    bytes += b->layouts.back().bytes;
     b->theta_off.push_back(b->theta_total);
-    b->theta_total += s.n;
-    b->nmax = std::max(b->nmax, s.n);
-    GroupProblem &g = b->hp[i];
-    std::memset(&g, 0, sizeof(g));
-    g.N = s.N; g.K = s.K; g.p = s.p; g.d = s.d; g.f = s.f; g.n = s.n; g.mc = s.mc;
-    g.X = data[i].X; g.Y = data[i].Y; g.Z = data[i].Z; g.choice = data[i].choice;
-    g.ldn = round_up(s.N, 64);
-    g.mc_pad = round_up(s.mc, kTile);
-    g.nt1d = (int)(g.mc_pad / kTile);
-    build_blocking(s, b->op, &g.build_ob, &g.build_kc);
-    g.zrows = zblocks_rows(s, b->fp64);
-    g.zsplit = (int)std::max<int64_t>(1, s.N / 4096);
-    // band tiles of this problem
-    band_maps[i].assign((size_t)g.nt1d * g.nt1d, -1);
-    if (s.q > 0)
-      for (int k = 1; k < s.K; ++k) {
-        const int lo = (int)((int64_t)(k - 1) * s.q / kTile), hi = (int)(((int64_t)k * s.q - 1) / kTile);
-        for (int ti = lo; ti <= hi; ++ti)
-          for (int tj = lo; tj <= ti; ++tj)
-            if (band_maps[i][(size_t)ti * g.nt1d + tj] < 0) {
-              band_maps[i][(size_t)ti * g.nt1d + tj] = (int)bands[i].size();
-              bands[i].push_back(make_int2(ti, tj));
-            }
-      }
-    g.main_off = main_elems;
-    main_elems += (int64_t)g.nt1d * (g.nt1d + 1) / 2 * kTile * kTile;
-    g.band_off = band_elems;
-    band_elems += (int64_t)bands[i].size() * kTile * kTile;
-    g.z_off = z_elems;
-    if (s.f > 0) z_elems += (int64_t)g.zsplit * zblocks_outputs(s);
-    Off &o = offs[i];
-    auto take = [&](size_t nbytes) { size_t at = bytes; bytes += (nbytes + 255) & ~(size_t)255; return at; };
-    o.P = take((size_t)s.N * s.K * tsz);
-    o.zbar = take((size_t)s.N * s.f * tsz);
-    o.At = take((size_t)g.mc_pad * g.ldn * esz);
-    o.Ad = take((size_t)g.mc_pad * g.ldn * esz);
-    o.F = take((size_t)s.n * s.n * 8);
-    o.F32 = b->mixed ? take((size_t)s.n * s.n * 4) : 0;
-    o.grad = take((size_t)s.n * 8);
-    o.delta = take((size_t)s.n * 8);
-    o.scal = take(kGsCount * 8);
-    o.rwork = take((size_t)2 * s.n * 8);
-    o.band_of = take(band_maps[i].size() * sizeof(int));
+    b->theta_total += b->layouts.back().s.n;
   }
-  if (b->nmax > 1400) return fail(MNL_ERR_UNSUPPORTED);  // per-problem solve keeps 128 n bytes in shared memory
-  unsigned char *arena = nullptr;
-  if ((rc = balloc(b, &arena, bytes))) return fail(rc);
-  if (cudaMemsetAsync(arena, 0, bytes, b->st) != cudaSuccess) { cudaGetLastError(); return fail(MNL_ERR_CUDA); }
+  for (const ProbLayout &l : b->layouts) b->lp.push_back(&l);
+  if (cudaMalloc(&b->arena, bytes) != cudaSuccess || cudaMalloc(&b->theta0, b->theta_total * sizeof(double))) {
+    cudaGetLastError();
+    return fail(MNL_ERR_OOM);
+  }
+  if (cudaMemsetAsync(b->arena, 0, bytes, E.st) || cudaMemsetAsync(b->theta0, 0, b->theta_total * 8, E.st)) {
+    cudaGetLastError();
+    return fail(MNL_ERR_CUDA);
+  }
+  b->W.hp.resize(count);
   for (int i = 0; i < count; ++i) {
-    GroupProblem &g = b->hp[i];
-    const Off &o = offs[i];
-    g.P = arena + o.P;
-    g.zbar = arena + o.zbar;
-    g.At = arena + o.At;
-    g.Ad = arena + o.Ad;
-    g.F = reinterpret_cast<double *>(arena + o.F);
-    g.F32 = b->mixed ? reinterpret_cast<float *>(arena + o.F32) : nullptr;
-    g.grad = reinterpret_cast<double *>(arena + o.grad);
-    g.delta = reinterpret_cast<double *>(arena + o.delta);
-    g.scal = reinterpret_cast<double *>(arena + o.scal);
-    g.rwork = reinterpret_cast<double *>(arena + o.rwork);
-    g.band_of = reinterpret_cast<int *>(arena + o.band_of);
-    if (!band_maps[i].empty() && cudaMemcpy(g.band_of, band_maps[i].data(), band_maps[i].size() * sizeof(int),
-                                            cudaMemcpyHostToDevice) != cudaSuccess) {
+    const ProbLayout &l = b->layouts[i];
+    bind_problem(l, b->arena + base[i], &data[i], b->theta0 + b->theta_off[i], b->W.hp[i]);
+    if (!l.band_map.empty() && cudaMemcpyAsync(b->W.hp[i].band_of, l.band_map.data(), l.band_map.size() * sizeof(int),
+                                               cudaMemcpyHostToDevice, E.st)) {
       cudaGetLastError();
       return fail(MNL_ERR_CUDA);
     }
   }
-  const size_t csz = b->fp64 ? 8 : 4;
-  if ((rc = balloc(b, &b->main_part, (size_t)main_elems * csz)) ||
-      (rc = balloc(b, &b->band_part, (size_t)band_elems * csz)) || (rc = balloc(b, &b->z_part, (size_t)z_elems * tsz)) ||
-      (rc = balloc(b, &b->probs, (size_t)count * sizeof(GroupProblem))) ||
-      (rc = balloc(b, &b->active, (size_t)count * sizeof(int))) ||
-      (rc = balloc(b, &b->pending, (size_t)count * sizeof(int))) ||
-      (rc = balloc(b, &b->accepted, (size_t)count * sizeof(int))) ||
-      (rc = balloc(b, &b->status, (size_t)count * sizeof(int))) ||
-      (rc = balloc(b, &b->stop, (size_t)count * sizeof(int))) || (rc = balloc(b, &b->counts, 4 * sizeof(int))) ||
-      (rc = balloc(b, &b->err, sizeof(int))))
-    return fail(rc);
-  // work items
-  std::vector<GroupItem> bi, zi, ai;
-  size_t bsm = 0, zsm = 0;
-  for (int i = 0; i < count; ++i) {
-    const Shape &s = b->shapes[i];
-    const GroupProblem &g = b->hp[i];
-    if (s.mc > 0) {
-      const int nblk = (int)((s.N + g.build_ob - 1) / g.build_ob);
-      for (int k = 0; k < nblk; ++k) bi.push_back({i, k});
-      bsm = std::max(bsm, build_smem_bytes(s, b->op, g.build_ob, g.build_kc));
-    }
-    if (s.f > 0) {
-      const int64_t nzt = zblocks_outputs(s);
-      const int chunks = (int)((nzt + 8191) / 8192);
-      for (int k = 0; k < g.zsplit * chunks; ++k) zi.push_back({i, k});
-      zsm = std::max(zsm, zblocks_smem(s, g.zrows, b->fp64));
-    }
-    const int ncb = (int)((s.n + kAssembleCols - 1) / kAssembleCols);
-    for (int k = 0; k < ncb; ++k) ai.push_back({i, k});
-  }
-  b->n_build = (int)bi.size();
-  b->n_z = (int)zi.size();
-  b->n_asm = (int)ai.size();
-  b->build_smem = bsm;
-  b->z_smem = zsm;
-  b->chol_smem = grouped_chol_smem(b->nmax);
-  if (bsm > 200 * 1024 || zsm > 200 * 1024 || b->chol_smem > 220 * 1024) return fail(MNL_ERR_UNSUPPORTED);
-  if ((rc = balloc(b, &b->build_items, bi.size() * sizeof(GroupItem))) ||
-      (rc = balloc(b, &b->z_items, zi.size() * sizeof(GroupItem))) ||
-      (rc = balloc(b, &b->asm_items, ai.size() * sizeof(GroupItem))))
-    return fail(rc);
-  if ((!bi.empty() && cudaMemcpy(b->build_items, bi.data(), bi.size() * sizeof(GroupItem), cudaMemcpyHostToDevice)) ||
-      (!zi.empty() && cudaMemcpy(b->z_items, zi.data(), zi.size() * sizeof(GroupItem), cudaMemcpyHostToDevice)) ||
-      (!ai.empty() && cudaMemcpy(b->asm_items, ai.data(), ai.size() * sizeof(GroupItem), cudaMemcpyHostToDevice))) {
-    cudaGetLastError();
-    return fail(MNL_ERR_CUDA);
-  }
-  // contraction units: per-problem maps (tensor-core modes), tiles in
-  // decreasing K-length (longest first, round-robin over the CTAs)
-  {
-    std::vector<CUtensorMap> maps(b->fp64 ? 1 : 2 * (size_t)count);
-    std::vector<SyrkUnit> um, ub;
-    for (int i = 0; i < count; ++i) {
-      const GroupProblem &g = b->hp[i];
-      if (b->shapes[i].mc == 0) continue;
-      if (!b->fp64 && (encode_operand_map(b->op, g.At, g.mc_pad, g.ldn, &maps[2 * i]) != cudaSuccess ||
-                       encode_operand_map(b->op, g.Ad, g.mc_pad, g.ldn, &maps[2 * i + 1]) != cudaSuccess))
-        return fail(MNL_ERR_CUDA);
-      const int kb = b->fp64 ? (int)(g.ldn / f64_chunk_rows()) : tc_kblocks(b->op, g.ldn);
-      const int mA = b->fp64 ? 0 : 2 * i, mD = b->fp64 ? 1 : 2 * i + 1;
-      int t = 0;
-      for (int ti = 0; ti < g.nt1d; ++ti)
-        for (int tj = 0; tj <= ti; ++tj, ++t)
-          um.push_back({mA, i, ti, tj, 0, kb, g.main_off + (int64_t)t * kTile * kTile});
-      for (size_t k = 0; k < bands[i].size(); ++k)
-        ub.push_back({mD, i, bands[i][k].x, bands[i][k].y, 0, kb, g.band_off + (int64_t)k * kTile * kTile});
-    }
-    auto by_len = [](const SyrkUnit &a, const SyrkUnit &c) { return (a.kb1 - a.kb0) > (c.kb1 - c.kb0); };
-    std::stable_sort(um.begin(), um.end(), by_len);
-    std::stable_sort(ub.begin(), ub.end(), by_len);
-    b->nunits_main = (int)um.size();
-    b->nunits_band = (int)ub.size();
-    if ((rc = balloc(b, &b->maps, maps.size() * sizeof(CUtensorMap))) ||
-        (rc = balloc(b, &b->units_main, um.size() * sizeof(SyrkUnit))) ||
-        (rc = balloc(b, &b->units_band, ub.size() * sizeof(SyrkUnit))))
-      return fail(rc);
-    if (cudaMemcpy(b->maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice) ||
-        (!um.empty() && cudaMemcpy(b->units_main, um.data(), um.size() * sizeof(SyrkUnit), cudaMemcpyHostToDevice)) ||
-        (!ub.empty() && cudaMemcpy(b->units_band, ub.data(), ub.size() * sizeof(SyrkUnit), cudaMemcpyHostToDevice))) {
-      cudaGetLastError();
-      return fail(MNL_ERR_CUDA);
-    }
-  }
-  // descriptors (theta pointers are set by each fit), then autotune the pass tile height
-  if (cudaMemcpy(b->probs, b->hp.data(), (size_t)count * sizeof(GroupProblem), cudaMemcpyHostToDevice) ||
-      cudaMemsetAsync(b->active, 0, (size_t)count * sizeof(int), b->st)) {
-    cudaGetLastError();
-    return fail(MNL_ERR_CUDA);
-  }
-  cudaStreamSynchronize(b->st);
   int rows = 16;
-  if (b->fp64) {
-    rows = 16;
-  } else {
-    // timing needs the probabilities' inputs only: theta = 0 everywhere (the arena is zeroed)
-    std::vector<int> ones(count, 1);
-    double *th0 = nullptr;
-    if ((rc = balloc(b, &th0, (size_t)b->theta_total * 8))) return fail(rc);
-    cudaMemset(th0, 0, (size_t)b->theta_total * 8);
-    std::vector<GroupProblem> tmp = b->hp;
-    for (int i = 0; i < count; ++i) { tmp[i].theta = th0 + b->theta_off[i]; tmp[i].delta = th0 + b->theta_off[i]; }
-    cudaMemcpy(b->probs, tmp.data(), (size_t)count * sizeof(GroupProblem), cudaMemcpyHostToDevice);
-    cudaMemcpy(b->active, ones.data(), (size_t)count * sizeof(int), cudaMemcpyHostToDevice);
-    autotune_rows(b, &rows);
-    cudaMemset(b->active, 0, (size_t)count * sizeof(int));
-  }
-  b->pfull = plan_grouped_pass(b->shapes, b->fp64, rows, b->nsm);
-  b->pll = plan_grouped_pass(b->shapes, b->fp64, rows, b->nsm);
-  if (!b->pfull.ok) return fail(MNL_ERR_UNSUPPORTED);
-  b->pll.grid = b->pfull.grid;
-  std::vector<PassSeg> segs;
-  std::vector<int> ss, sl, sls;
-  int64_t plen = 0;
-  build_pass_lists(b, rows, b->pfull.grid, segs, ss, sl, sls, &plen);
-  if ((rc = upload_pass_lists(b, segs, ss, sl, sls, plen))) return fail(rc);
-  if (cudaStreamSynchronize(b->st) != cudaSuccess) { cudaGetLastError(); return fail(MNL_ERR_CUDA); }
+  if ((rc = autotune_rows(E, b->W, b->lp, b->theta0, &rows))) return fail(rc);
+  if ((rc = ws_build(E, b->W, b->lp, rows))) return fail(rc);
+  if (cudaStreamSynchronize(E.st) != cudaSuccess) { cudaGetLastError(); return fail(MNL_ERR_CUDA); }
   *out = b;
   return MNL_OK;
 }
@@ -653,7 +727,7 @@ int mnl_batch_create(int count, const mnl_dims *dims, const mnl_data *data, int 
 int64_t mnl_batch_num_params(const mnl_batch *b, int64_t *offsets) {
   if (!b) return -1;
   if (offsets)
-    for (int i = 0; i < b->count; ++i) offsets[i] = b->theta_off[i];
+    for (size_t i = 0; i < b->theta_off.size(); ++i) offsets[i] = b->theta_off[i];
   return b->theta_total;
 }
 
@@ -663,35 +737,31 @@ int mnl_batch_fit(mnl_batch *b, const mnl_fit_opts *opts, double *theta, mnl_bat
   mnl_fit_opts_default(&o);
   if (opts) o = *opts;
   if (o.maxiter < 0 || o.max_halvings < 0) return MNL_ERR_INVALID_ARG;
-  const double steptol = o.steptol >= 0 ? o.steptol : (b->fp64 ? 1e-10 : 1e-7);
-  const int np = b->count;
+  Engine &E = b->E;
+  WorkSet &W = b->W;
+  const double steptol = o.steptol >= 0 ? o.steptol : (E.fp64 ? 1e-10 : 1e-7);
+  const int np = W.count;
   const auto wall0 = std::chrono::steady_clock::now();
-  // order after the caller's prior work on its stream
-  BCK(cudaEventRecord(b->ev_user, b->user_st));
-  BCK(cudaStreamWaitEvent(b->st, b->ev_user, 0));
-  for (int i = 0; i < np; ++i) b->hp[i].theta = theta + b->theta_off[i];
-  BCK(cudaMemcpyAsync(b->probs, b->hp.data(), (size_t)np * sizeof(GroupProblem), cudaMemcpyHostToDevice, b->st));
-  {
-    std::vector<int> ones(np, 1);
-    BCK(cudaMemcpyAsync(b->active, ones.data(), (size_t)np * sizeof(int), cudaMemcpyHostToDevice, b->st));
-    BCK(cudaMemsetAsync(b->status, 0, (size_t)np * sizeof(int), b->st));
-    BCK(cudaMemsetAsync(b->stop, 0, (size_t)np * sizeof(int), b->st));
-    BCK(cudaMemsetAsync(b->accepted, 0, (size_t)np * sizeof(int), b->st));
-    BCK(cudaMemsetAsync(b->err, 0, sizeof(int), b->st));
-    for (int i = 0; i < np; ++i) BCK(cudaMemsetAsync(b->hp[i].scal, 0, kGsCount * sizeof(double), b->st));
-    BCK(cudaStreamSynchronize(b->st));
-  }
-  // one iteration + first line-search round, captured once per set of options
+  BCK(cudaEventRecord(E.ev_user, E.user_st));
+  BCK(cudaStreamWaitEvent(E.st, E.ev_user, 0));
+  for (int i = 0; i < np; ++i) W.hp[i].theta = theta + b->theta_off[i];
+  BCK(cudaMemcpyAsync(W.probs.p, W.hp.data(), (size_t)np * sizeof(GroupProblem), cudaMemcpyHostToDevice, E.st));
+  std::vector<int> ones(np, 1);
+  BCK(cudaMemcpyAsync(W.active(), ones.data(), (size_t)np * sizeof(int), cudaMemcpyHostToDevice, E.st));
+  BCK(cudaMemsetAsync(W.pending(), 0, 4 * (size_t)np * sizeof(int), E.st));  // pending, accepted, status, stop
+  BCK(cudaMemsetAsync(W.err.p, 0, sizeof(int), E.st));
+  for (int i = 0; i < np; ++i) BCK(cudaMemsetAsync(W.hp[i].scal, 0, kGsCount * sizeof(double), E.st));
+  BCK(cudaStreamSynchronize(E.st));
   if (b->have_graph && (b->graph_gtol != o.gtol || b->graph_halvings != o.max_halvings)) {
     cudaGraphExecDestroy(b->graph);
     b->have_graph = false;
   }
   if (!b->have_graph) {
     cudaGraph_t g;
-    BCK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
-    int rc1 = enqueue_iteration(b, o);
-    int rc2 = rc1 == MNL_OK ? enqueue_ls_round(b, o) : rc1;
-    cudaError_t ec = cudaStreamEndCapture(b->st, &g);
+    BCK(cudaStreamBeginCapture(E.st, cudaStreamCaptureModeThreadLocal));
+    int rc1 = enqueue_iteration(E, W, o);
+    int rc2 = rc1 == MNL_OK ? enqueue_ls_round(E, W, o) : rc1;
+    cudaError_t ec = cudaStreamEndCapture(E.st, &g);
     if (rc2 != MNL_OK) return rc2;
     BCK(ec);
     BCK(cudaGraphInstantiate(&b->graph, g, 0));
@@ -700,48 +770,30 @@ int mnl_batch_fit(mnl_batch *b, const mnl_fit_opts *opts, double *theta, mnl_bat
     b->graph_gtol = o.gtol;
     b->graph_halvings = o.max_halvings;
   }
-  const int tb = 256, nb = (np + tb - 1) / tb;
   int iters = 0;
   float t_graph = 0.f;
   for (int it = 0; it < o.maxiter; ++it) {
-    BCK(cudaEventRecord(b->t0, b->st));
-    BCK(cudaGraphLaunch(b->graph, b->st));
-    BCK(cudaEventRecord(b->t1, b->st));
-    BCK(cudaMemcpyAsync(b->h_counts, b->counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, b->st));
-    BCK(cudaStreamSynchronize(b->st));
+    BCK(cudaEventRecord(E.t0, E.st));
+    BCK(cudaGraphLaunch(b->graph, E.st));
+    BCK(cudaEventRecord(E.t1, E.st));
+    int rc = finish_iteration(E, W, o, steptol);
+    if (rc) return rc;
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, b->t0, b->t1);
+    cudaEventElapsedTime(&ms, E.t0, E.t1);
     t_graph += ms;
-    int rounds = 1;
-    while (b->h_counts[1] > 0 && rounds <= o.max_halvings) {
-      int rc = enqueue_ls_round(b, o);
-      if (rc) return rc;
-      BCK(cudaMemcpyAsync(b->h_counts, b->counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, b->st));
-      BCK(cudaStreamSynchronize(b->st));
-      ++rounds;
-    }
-    theta_update_kernel<<<np, 256, 0, b->st>>>(b->probs, b->accepted, b->active, b->stop, steptol, o.ftol);
-    count_kernel<<<1, 256, 0, b->st>>>(np, b->active, b->pending, b->counts);
-    BCK(cudaGetLastError());
-    BCK(cudaMemcpyAsync(b->h_counts, b->counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, b->st));
-    BCK(cudaMemcpyAsync(b->h_counts + 2, b->err, sizeof(int), cudaMemcpyDeviceToHost, b->st));
-    BCK(cudaStreamSynchronize(b->st));
     ++iters;
-    if (b->h_counts[2]) return MNL_ERR_TIMEOUT;
-    if (b->h_counts[0] == 0) break;
+    if (E.h_counts[0] == 0) break;
   }
-  (void)nb;
-  // results
   std::vector<int> st(np), sp(np);
   std::vector<double> sc((size_t)np * kGsCount);
-  BCK(cudaMemcpyAsync(st.data(), b->status, np * sizeof(int), cudaMemcpyDeviceToHost, b->st));
-  BCK(cudaMemcpyAsync(sp.data(), b->stop, np * sizeof(int), cudaMemcpyDeviceToHost, b->st));
+  BCK(cudaMemcpyAsync(st.data(), W.status(), np * sizeof(int), cudaMemcpyDeviceToHost, E.st));
+  BCK(cudaMemcpyAsync(sp.data(), W.stop(), np * sizeof(int), cudaMemcpyDeviceToHost, E.st));
   for (int i = 0; i < np; ++i)
-    BCK(cudaMemcpyAsync(sc.data() + (size_t)i * kGsCount, b->hp[i].scal, kGsCount * sizeof(double),
-                        cudaMemcpyDeviceToHost, b->st));
-  BCK(cudaStreamSynchronize(b->st));
-  BCK(cudaEventRecord(b->ev_done, b->st));
-  BCK(cudaStreamWaitEvent(b->user_st, b->ev_done, 0));
+    BCK(cudaMemcpyAsync(sc.data() + (size_t)i * kGsCount, W.hp[i].scal, kGsCount * sizeof(double),
+                        cudaMemcpyDeviceToHost, E.st));
+  BCK(cudaStreamSynchronize(E.st));
+  BCK(cudaEventRecord(E.ev_done, E.st));
+  BCK(cudaStreamWaitEvent(E.user_st, E.ev_done, 0));
   int nconv = 0, nerr = 0;
   for (int i = 0; i < np; ++i) {
     if (st[i] != MNL_OK) ++nerr;
@@ -762,7 +814,7 @@ int mnl_batch_fit(mnl_batch *b, const mnl_fit_opts *opts, double *theta, mnl_bat
     info->failed = nerr;
     info->t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
     info->t_graph_ms = t_graph;
-    info->pass_rows = b->pfull.rows;
+    info->pass_rows = W.rows;
   }
   if (nconv == np) return MNL_OK;
   for (int i = 0; i < np; ++i)
@@ -772,10 +824,287 @@ int mnl_batch_fit(mnl_batch *b, const mnl_fit_opts *opts, double *theta, mnl_bat
 
 int mnl_batch_destroy(mnl_batch *b) {
   if (!b) return MNL_OK;
-  cudaStreamSynchronize(b->st);
+  cudaStreamSynchronize(b->E.st);
   cudaGetLastError();
-  bfree(b);
+  b->release();
   delete b;
+  return MNL_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Serving: continuous batching of fit requests under a device-memory budget.
+// Each tick admits queued requests whose state fits in the remaining budget
+// (FIFO; a request skipped too often blocks later ones so large requests are
+// not starved), runs one Newton iteration for every admitted request in the
+// same grouped launches, and retires the requests that finished.  A request's
+// data, coefficients, P, gradient and Hessian stay resident in its chunk of
+// the pool from admission to retirement.
+// ===========================================================================
+
+namespace {
+
+struct Pool {
+  unsigned char *base = nullptr;
+  size_t size = 0, used = 0;
+  std::map<size_t, size_t> free_;  // offset -> bytes
+  int init(size_t bytes) {
+    size = (bytes + 255) & ~(size_t)255;
+    if (cudaMalloc(&base, size) != cudaSuccess) { cudaGetLastError(); base = nullptr; return MNL_ERR_OOM; }
+    free_[0] = size;
+    return MNL_OK;
+  }
+  bool alloc(size_t bytes, size_t *off) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < bytes) continue;
+      *off = it->first;
+      const size_t rem = it->second - bytes, o2 = it->first + bytes;
+      free_.erase(it);
+      if (rem) free_[o2] = rem;
+      used += bytes;
+      return true;
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    used -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  void destroy() { if (base) cudaFree(base); base = nullptr; }
+};
+
+struct Request {
+  mnl_dims dims{};
+  ProbLayout L;
+  std::vector<float> X, Y, Z;
+  std::vector<int32_t> choice;
+  std::vector<double> theta0, theta_out;
+  size_t off = 0;
+  bool admitted = false, done = false;
+  int skipped = 0;
+  GroupProblem g{};
+  mnl_request_result res{};
+  std::chrono::steady_clock::time_point t_submit, t_admit;
+};
+
+}  // namespace
+
+struct mnl_server {
+  Engine E;
+  WorkSet W;
+  Pool pool;
+  mnl_server_opts opts{};
+  double steptol = 1e-7;
+  uint64_t next_ticket = 1;
+  std::deque<uint64_t> queue;
+  std::vector<uint64_t> members;
+  std::map<uint64_t, Request> reqs;
+  bool dirty = true;
+  std::mutex mu;
+  int ticks = 0;
+  void release() {
+    W.release();
+    pool.destroy();
+    E.release();
+  }
+};
+
+extern "C" {
+
+void mnl_server_opts_default(mnl_server_opts *o) {
+  if (!o) return;
+  o->mem_budget = (size_t)80 << 30;
+  o->precision = MNL_BF16;
+  o->max_active = 4096;
+  o->max_skips = 8;
+  mnl_fit_opts_default(&o->fit);
+}
+
+int mnl_server_create(const mnl_server_opts *opts, void *stream, mnl_server **out) {
+  if (!out) return MNL_ERR_INVALID_ARG;
+  *out = nullptr;
+  mnl_server_opts o;
+  mnl_server_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.precision < MNL_FP64 || o.precision > MNL_BF16 || o.mem_budget < ((size_t)1 << 20) || o.max_active < 1)
+    return MNL_ERR_INVALID_ARG;
+  mnl_server *s = new (std::nothrow) mnl_server();
+  if (!s) return MNL_ERR_OOM;
+  int rc;
+  if ((rc = s->E.init(o.precision, stream)) || (rc = s->pool.init(o.mem_budget))) {
+    s->release();
+    delete s;
+    return rc;
+  }
+  s->opts = o;
+  s->steptol = o.fit.steptol >= 0 ? o.fit.steptol : (s->E.fp64 ? 1e-10 : 1e-7);
+  *out = s;
+  return MNL_OK;
+}
+
+int mnl_server_submit(mnl_server *s, const mnl_dims *dims, const mnl_data *host, const double *theta0,
+                      uint64_t *ticket) {
+  if (!s || !dims || !host || !ticket) return MNL_ERR_INVALID_ARG;
+  const mnl_dims &d = *dims;
+  if (d.N < 1 || d.K < 2 || d.p < 0 || d.d < 0 || d.f < 0 || d.p + d.d + d.f < 1) return MNL_ERR_INVALID_ARG;
+  if (d.gamma_base != 0) return MNL_ERR_UNSUPPORTED;
+  if (!host->choice || (d.p > 0 && !host->X) || (d.d > 0 && !host->Y) || (d.f > 0 && !host->Z))
+    return MNL_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < d.N; ++i)
+    if (host->choice[i] < 0 || host->choice[i] >= d.K) return MNL_ERR_INVALID_ARG;
+  Request r;
+  r.dims = d;
+  r.L = layout_problem(d, s->E.op, s->E.fp64, s->E.mixed, true);
+  if (r.L.s.n > 1400 || r.L.s.K > 256) return MNL_ERR_UNSUPPORTED;
+  if (r.L.bytes > s->pool.size) return MNL_ERR_OOM;
+  r.X.assign(host->X, host->X + (size_t)d.N * d.p);
+  if (d.d) r.Y.assign(host->Y, host->Y + (size_t)d.N * d.K * d.d);
+  if (d.f) r.Z.assign(host->Z, host->Z + (size_t)d.N * d.K * d.f);
+  r.choice.assign(host->choice, host->choice + d.N);
+  r.theta0.assign((size_t)r.L.s.n, 0.0);
+  if (theta0) std::copy(theta0, theta0 + r.L.s.n, r.theta0.begin());
+  r.t_submit = std::chrono::steady_clock::now();
+  std::lock_guard<std::mutex> lock(s->mu);
+  const uint64_t t = s->next_ticket++;
+  s->reqs.emplace(t, std::move(r));
+  s->queue.push_back(t);
+  *ticket = t;
+  return MNL_OK;
+}
+
+int mnl_server_step(mnl_server *s, int32_t *n_active, int32_t *n_queued) {
+  if (!s) return MNL_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(s->mu);
+  Engine &E = s->E;
+  WorkSet &W = s->W;
+  // admission
+  for (auto it = s->queue.begin(); it != s->queue.end();) {
+    if ((int)s->members.size() >= s->opts.max_active) break;
+    Request &r = s->reqs.at(*it);
+    size_t off = 0;
+    if (!s->pool.alloc(r.L.bytes, &off)) {
+      if (++r.skipped > s->opts.max_skips) break;  // keep its place: later requests wait
+      ++it;
+      continue;
+    }
+    r.off = off;
+    r.admitted = true;
+    r.t_admit = std::chrono::steady_clock::now();
+    unsigned char *base = s->pool.base + off;
+    bind_problem(r.L, base, nullptr, nullptr, r.g);
+    const Shape &sh = r.L.s;
+    BCK(cudaMemsetAsync(base, 0, r.L.bytes, E.st));
+    if (sh.p) BCK(cudaMemcpyAsync(base + r.L.X, r.X.data(), r.X.size() * 4, cudaMemcpyHostToDevice, E.st));
+    if (sh.d) BCK(cudaMemcpyAsync(base + r.L.Y, r.Y.data(), r.Y.size() * 4, cudaMemcpyHostToDevice, E.st));
+    if (sh.f) BCK(cudaMemcpyAsync(base + r.L.Z, r.Z.data(), r.Z.size() * 4, cudaMemcpyHostToDevice, E.st));
+    BCK(cudaMemcpyAsync(base + r.L.choice, r.choice.data(), r.choice.size() * 4, cudaMemcpyHostToDevice, E.st));
+    BCK(cudaMemcpyAsync(base + r.L.theta, r.theta0.data(), r.theta0.size() * 8, cudaMemcpyHostToDevice, E.st));
+    if (!r.L.band_map.empty())
+      BCK(cudaMemcpyAsync(r.g.band_of, r.L.band_map.data(), r.L.band_map.size() * sizeof(int),
+                          cudaMemcpyHostToDevice, E.st));
+    s->members.push_back(*it);
+    s->dirty = true;
+    it = s->queue.erase(it);
+  }
+  if (!s->members.empty()) {
+    const int np = (int)s->members.size();
+    if (s->dirty) {
+      std::vector<const ProbLayout *> lp;
+      W.hp.clear();
+      for (uint64_t t : s->members) {
+        Request &r = s->reqs.at(t);
+        W.hp.push_back(r.g);
+        lp.push_back(&r.L);
+      }
+      int rc = ws_build(E, W, lp, 16);
+      if (rc) return rc;
+      s->dirty = false;
+    }
+    std::vector<int> ones(np, 1);
+    BCK(cudaMemcpyAsync(W.active(), ones.data(), (size_t)np * sizeof(int), cudaMemcpyHostToDevice, E.st));
+    BCK(cudaMemsetAsync(W.pending(), 0, 4 * (size_t)np * sizeof(int), E.st));
+    BCK(cudaMemsetAsync(W.err.p, 0, sizeof(int), E.st));
+    int rc = enqueue_iteration(E, W, s->opts.fit);
+    if (!rc) rc = enqueue_ls_round(E, W, s->opts.fit);
+    if (!rc) rc = finish_iteration(E, W, s->opts.fit, s->steptol);
+    if (rc) return rc;
+    ++s->ticks;
+    // retire
+    std::vector<int> st(np), sp(np);
+    BCK(cudaMemcpyAsync(st.data(), W.status(), np * sizeof(int), cudaMemcpyDeviceToHost, E.st));
+    BCK(cudaMemcpyAsync(sp.data(), W.stop(), np * sizeof(int), cudaMemcpyDeviceToHost, E.st));
+    std::vector<double> sc((size_t)np * kGsCount);
+    for (int i = 0; i < np; ++i)
+      BCK(cudaMemcpyAsync(sc.data() + (size_t)i * kGsCount, W.hp[i].scal, kGsCount * 8, cudaMemcpyDeviceToHost, E.st));
+    BCK(cudaStreamSynchronize(E.st));
+    std::vector<uint64_t> keep;
+    for (int i = 0; i < np; ++i) {
+      Request &r = s->reqs.at(s->members[i]);
+      const double *c = sc.data() + (size_t)i * kGsCount;
+      const int iters = (int)c[kGsIters];
+      const bool fin = st[i] != MNL_OK || sp[i] != 0 || iters >= s->opts.fit.maxiter;
+      if (!fin) { keep.push_back(s->members[i]); continue; }
+      r.theta_out.resize((size_t)r.L.s.n);
+      BCK(cudaMemcpy(r.theta_out.data(), r.g.theta, r.theta_out.size() * 8, cudaMemcpyDeviceToHost));
+      r.res.status = st[i] != MNL_OK ? st[i] : (sp[i] != 0 ? MNL_OK : MNL_MAXITER);
+      r.res.stop_reason = sp[i] != 0 ? sp[i] : (st[i] == MNL_OK ? MNL_STOP_MAXITER : 0);
+      r.res.iters = iters;
+      r.res.ls_evals = (int)c[kGsLsEvals];
+      r.res.loglik = c[kGsL];
+      r.res.grad_inf = c[kGsGinf];
+      const auto now = std::chrono::steady_clock::now();
+      r.res.latency_ms = std::chrono::duration<double, std::milli>(now - r.t_submit).count();
+      r.res.queue_ms = std::chrono::duration<double, std::milli>(r.t_admit - r.t_submit).count();
+      r.done = true;
+      s->pool.release(r.off, r.L.bytes);
+      r.X.clear(); r.X.shrink_to_fit();
+      r.Y.clear(); r.Y.shrink_to_fit();
+      r.Z.clear(); r.Z.shrink_to_fit();
+      r.choice.clear(); r.choice.shrink_to_fit();
+      s->dirty = true;
+    }
+    s->members.swap(keep);
+  }
+  if (n_active) *n_active = (int32_t)s->members.size();
+  if (n_queued) *n_queued = (int32_t)s->queue.size();
+  return MNL_OK;
+}
+
+int mnl_server_poll(mnl_server *s, uint64_t ticket, double *theta, mnl_request_result *res) {
+  if (!s) return MNL_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return MNL_ERR_INVALID_ARG;
+  if (!it->second.done) return MNL_PENDING;
+  if (theta) std::copy(it->second.theta_out.begin(), it->second.theta_out.end(), theta);
+  if (res) *res = it->second.res;
+  s->reqs.erase(it);
+  return MNL_OK;
+}
+
+size_t mnl_server_memory_in_use(const mnl_server *s) { return s ? s->pool.used : 0; }
+
+int mnl_server_destroy(mnl_server *s) {
+  if (!s) return MNL_OK;
+  cudaStreamSynchronize(s->E.st);
+  cudaGetLastError();
+  s->release();
+  delete s;
   return MNL_OK;
 }
 
