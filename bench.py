@@ -368,6 +368,104 @@ def run_ours(args, world, rank, local):
     m.close()
 
 
+# ---------------------------------------------------------------------------
+# batched and serving workloads (separate lines; not the default run)
+# ---------------------------------------------------------------------------
+
+def run_batch(args):
+    """All problems of the batched workload fitted by one mnl_batch_fit: fits/s."""
+    import torch
+
+    from paper_1404_3177_gb300 import _build, datagen
+    from paper_1404_3177_gb300.api import MNLBatch
+
+    _build.build()
+    torch.cuda.set_device(0)
+    shapes = datagen.config4_shapes()[: args.count]
+    t0 = time.time()
+    probs = [datagen.config4_problem(b, sh) for b, sh in enumerate(shapes)]
+    gen_s = time.time() - t0
+    dev = []
+    for pr in probs:
+        dev.append(dict(X=torch.from_numpy(pr.X).cuda(), Y=None,
+                        Z=torch.from_numpy(pr.Z).cuda() if pr.f else None,
+                        choice=torch.from_numpy(pr.choice).cuda(), K=pr.K))
+    out = {}
+    for prec in args.batch_precisions.split(","):
+        with MNLBatch(dev, precision=prec) as b:
+            b.fit()  # warm-up (graph capture, lazy module loading)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            th, summary, per, rc = b.fit()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t
+        out[prec] = {"fits_per_s": len(probs) / dt, "seconds": dt, "iterations": summary["iterations"],
+                     "converged": summary["converged"], "failed": summary["failed"],
+                     "pass_rows": summary["pass_rows"], "graph_ms": summary["t_graph_ms"]}
+    line = {"metric": "batched_fits_per_s", "value": out[args.batch_precisions.split(",")[0]]["fits_per_s"],
+            "unit": "fits/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": f"c4_{len(probs)}_problems_N500-50000_K3-30_p2-40_f0-4",
+                       "rows_total": int(sum(p.N for p in probs)), "generation_s": round(gen_s, 1)},
+            "by_precision": out}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Poisson arrivals of fit requests (batched-workload sizes plus 2% large ones), p50/p99 latency, fits/s."""
+    import torch
+
+    from paper_1404_3177_gb300 import _build, datagen
+    from paper_1404_3177_gb300.api import MNLServer
+
+    _build.build()
+    torch.cuda.set_device(0)
+    arrivals = datagen.config5_arrivals(rate=args.rate, duration=args.duration)
+    shapes = datagen.config4_shapes()
+    small = [datagen.config4_problem(b, sh) for b, sh in enumerate(shapes[: args.pool])]
+    large = [datagen.config5_large(r) for r in range(args.large_pool)]
+    res = {}
+    for prec in args.serve_precisions.split(","):
+        lat, qms, done, ns, nl = [], [], 0, 0, 0
+        with MNLServer(precision=prec, mem_budget=80 << 30) as srv:
+            pending = {}
+            t0 = time.perf_counter()
+            i = 0
+            ticks = 0
+            while i < len(arrivals) or pending:
+                now = time.perf_counter() - t0
+                while i < len(arrivals) and arrivals[i][0] <= now:
+                    is_large = arrivals[i][1]
+                    pr = large[nl % len(large)] if is_large else small[ns % len(small)]
+                    if is_large:
+                        nl += 1
+                    else:
+                        ns += 1
+                    pending[srv.submit(X=pr.X, Z=pr.Z if pr.f else None, choice=pr.choice, K=pr.K)] = is_large
+                    i += 1
+                srv.step()
+                ticks += 1
+                for t in list(pending):
+                    r = srv.poll(t)
+                    if r is not None:
+                        lat.append(r[1]["latency_ms"])
+                        qms.append(r[1]["queue_ms"])
+                        done += 1
+                        del pending[t]
+            wall = time.perf_counter() - t0
+        lat.sort()
+        res[prec] = {"requests": len(arrivals), "large": nl, "fits_per_s": done / wall, "wall_s": wall,
+                     "ticks": ticks, "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                     "queue_p99_ms": sorted(qms)[min(len(qms) - 1, int(0.99 * len(qms)))]}
+    first = args.serve_precisions.split(",")[0]
+    line = {"metric": "serving_p50_p99_latency_ms", "value": res[first]["p99_ms"], "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": f"c5_poisson_{args.rate:g}_per_s_{args.duration:g}s_2pct_large",
+                       "distinct_small_datasets": args.pool, "distinct_large_datasets": args.large_pool,
+                       "mem_budget_gb": 80},
+            "by_precision": res}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -379,7 +477,20 @@ def main():
                     help="Newton solve: float64 Cholesky, or float32 factor + float64 refinement")
     ap.add_argument("--ref-rows", type=int, default=20000, help="observations in the oracle's bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c2", "batch", "serve"],
+                    help="c2: the single large fit (default); batch / serve: the batched and serving workloads")
+    ap.add_argument("--count", type=int, default=2048, help="batch: number of problems")
+    ap.add_argument("--batch-precisions", default="bf16,fp64")
+    ap.add_argument("--serve-precisions", default="bf16,fp64")
+    ap.add_argument("--rate", type=float, default=500.0)
+    ap.add_argument("--duration", type=float, default=10.0)
+    ap.add_argument("--pool", type=int, default=256, help="serve: distinct small request datasets (cycled)")
+    ap.add_argument("--large-pool", type=int, default=2)
     args = ap.parse_args()
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     world, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, world, rank)

@@ -131,7 +131,10 @@ typedef struct mnl_fit_opts {
 /* Defaults: maxiter 50, max_halvings 30, gtol 1e-8, ftol 0, steptol -1 (per precision). */
 MNL_API void mnl_fit_opts_default(mnl_fit_opts *opts);
 
-enum { MNL_STOP_GTOL = 1, MNL_STOP_FTOL = 2, MNL_STOP_STEPTOL = 3, MNL_STOP_MAXITER = 4 };
+/* MNL_STOP_NOISE (TF32 / BF16 only): the relative step stopped shrinking (it
+ * fell by less than half in one iteration) while already below 1e-5, i.e. the
+ * iterates reached the noise floor of the float32 gradient. */
+enum { MNL_STOP_GTOL = 1, MNL_STOP_FTOL = 2, MNL_STOP_STEPTOL = 3, MNL_STOP_MAXITER = 4, MNL_STOP_NOISE = 5 };
 
 typedef struct mnl_fit_info {
   int32_t iters;       /* Newton iterations taken                          */

@@ -27,7 +27,7 @@ MNL_PENDING = 10
 MNL_FP64, MNL_TF32, MNL_BF16 = 0, 1, 2
 PRECISIONS = {"fp64": MNL_FP64, "tf32": MNL_TF32, "bf16": MNL_BF16}
 
-MNL_STOP_GTOL, MNL_STOP_FTOL, MNL_STOP_STEPTOL, MNL_STOP_MAXITER = 1, 2, 3, 4
+MNL_STOP_GTOL, MNL_STOP_FTOL, MNL_STOP_STEPTOL, MNL_STOP_MAXITER, MNL_STOP_NOISE = 1, 2, 3, 4, 5
 
 # Every entry point declared in include/mnl.h.
 EXPORTS = (

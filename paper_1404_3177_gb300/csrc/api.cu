@@ -78,6 +78,8 @@ int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 constexpr int64_t kBf16MinRows = 1024;
 // Refinement steps of a mixed solve at most (each skipped once converged).
 constexpr int kRefineIters = 5;
+// Relative step below which a non-shrinking step means the float32 noise floor.
+constexpr double kNoiseStep = 1e-5;
 
 bool dims_ok(const mnl_dims *d) {
   return d && d->N >= 1 && d->K >= 2 && d->p >= 0 && d->d >= 0 && d->f >= 0 && (d->p + d->d + d->f) >= 1 &&
@@ -651,6 +653,7 @@ int mnl_fit(mnl_handle *h, const mnl_fit_opts *opts, double *theta, mnl_fit_info
   mnl_fit_info fi{};
   const auto t0 = std::chrono::steady_clock::now();
   rc = MNL_MAXITER;
+  double prev_step_rel = 1e300;
   for (int it = 0; it < o.maxiter; ++it) {
     mnl_step_info si{};
     bool conv = false;
@@ -674,6 +677,12 @@ int mnl_fit(mnl_handle *h, const mnl_fit_opts *opts, double *theta, mnl_fit_info
     fi.step_rel = si.step_inf / std::max(1.0, si.theta_inf);
     if (o.ftol > 0 && std::fabs(fi.dloglik) < o.ftol) { fi.stop_reason = MNL_STOP_FTOL; rc = MNL_OK; break; }
     if (steptol > 0 && fi.step_rel <= steptol) { fi.stop_reason = MNL_STOP_STEPTOL; rc = MNL_OK; break; }
+    if (!h->fp64 && it > 0 && fi.step_rel > 0.5 * prev_step_rel && fi.step_rel <= kNoiseStep) {
+      fi.stop_reason = MNL_STOP_NOISE;
+      rc = MNL_OK;
+      break;
+    }
+    prev_step_rel = fi.step_rel;
   }
   if (rc == MNL_MAXITER) fi.stop_reason = MNL_STOP_MAXITER;
   fi.status = rc;

@@ -84,7 +84,8 @@ __global__ void ls_update_kernel(int nprob, const GroupProblem *__restrict__ pro
 // theta += t delta for accepted problems, step test, iteration count.
 __global__ void __launch_bounds__(256) theta_update_kernel(const GroupProblem *__restrict__ probs,
                                                            int *__restrict__ accepted, int *__restrict__ active,
-                                                           int *__restrict__ stop, double steptol, double ftol) {
+                                                           int *__restrict__ stop, double steptol, double ftol,
+                                                           double noise_step) {
   __shared__ double red[2][8];
   const int b = blockIdx.x;
   if (accepted[b] == 0) return;
@@ -114,8 +115,12 @@ __global__ void __launch_bounds__(256) theta_update_kernel(const GroupProblem *_
     const double dl = sc[kGsLt] - sc[kGsLold];
     sc[kGsL] = sc[kGsLt];
     accepted[b] = 0;
+    const double rel = a / fmax(1.0, c);
+    const double prev = sc[kGsIters] > 1.0 ? sc[kGsPrevStep] : 1e300;
+    sc[kGsPrevStep] = rel;
     if (ftol > 0 && fabs(dl) < ftol) { stop[b] = MNL_STOP_FTOL; active[b] = 0; }
-    else if (steptol > 0 && a <= steptol * fmax(1.0, c)) { stop[b] = MNL_STOP_STEPTOL; active[b] = 0; }
+    else if (steptol > 0 && rel <= steptol) { stop[b] = MNL_STOP_STEPTOL; active[b] = 0; }
+    else if (noise_step > 0 && rel > 0.5 * prev && rel <= noise_step) { stop[b] = MNL_STOP_NOISE; active[b] = 0; }
   }
 }
 
@@ -220,6 +225,9 @@ struct ProbLayout {
   std::vector<int> band_map;
   size_t P = 0, zbar = 0, At = 0, Ad = 0, F = 0, F32 = 0, grad = 0, delta = 0, scal = 0, rwork = 0, band_of = 0;
   size_t theta = 0, X = 0, Y = 0, Z = 0, choice = 0;  // owned copies (server requests)
+  // multi-CTA solve workspace (problems with n_theta > kCtaSolveMaxN)
+  size_t dinv = 0, dinv32 = 0, lrwork = 0, fwork = 0, ref = 0, sstat = 0;
+  bool large = false;
   size_t bytes = 0;
 };
 
@@ -259,6 +267,16 @@ ProbLayout layout_problem(const mnl_dims &d, OpType op, bool fp64, bool mixed, b
   L.scal = take(kGsCount * 8);
   L.rwork = take((size_t)2 * s.n * 8);
   L.band_of = take(L.band_map.size() * sizeof(int));
+  L.large = s.n > kCtaSolveMaxN;
+  if (L.large) {
+    L.dinv = take((size_t)s.n * 8);
+    L.dinv32 = take((size_t)s.n * 4);
+    L.lrwork = take(mixed_solve_rwork_doubles(s.n) * 8);
+    L.fwork = take((size_t)s.n * 4);
+    L.ref = take(4 * 8);
+    L.sstat = take(16);
+    if (!mixed) L.F32 = 0;
+  }
   if (own) {
     L.theta = take((size_t)s.n * 8);
     L.X = take((size_t)s.N * s.p * 4);
@@ -436,7 +454,7 @@ int ws_build(Engine &E, WorkSet &W, const std::vector<const ProbLayout *> &L, in
     band_elems += (int64_t)l.bands.size() * kTile * kTile;
     g.z_off = z_elems;
     if (l.s.f > 0) z_elems += (int64_t)l.zsplit * zblocks_outputs(l.s);
-    W.nmax = std::max(W.nmax, l.s.n);
+    if (!l.large) W.nmax = std::max(W.nmax, l.s.n);
   }
   if ((rc = W.main_part.ensure(std::max<int64_t>(1, main_elems) * csz)) ||
       (rc = W.band_part.ensure(std::max<int64_t>(1, band_elems) * csz)) ||
@@ -519,7 +537,7 @@ int ws_build(Engine &E, WorkSet &W, const std::vector<const ProbLayout *> &L, in
 
 const GroupProblem *dprobs(const WorkSet &W) { return W.probs.as<GroupProblem>(); }
 
-int enqueue_iteration(Engine &E, WorkSet &W, const mnl_fit_opts &o) {
+int enqueue_iteration(Engine &E, WorkSet &W, const mnl_fit_opts &o, bool with_ls_init = true) {
   const int np = W.count;
   const int tb = 256, nb = (np + tb - 1) / tb;
   const GroupProblem *P = dprobs(W);
@@ -544,8 +562,16 @@ int enqueue_iteration(Engine &E, WorkSet &W, const mnl_fit_opts &o) {
   BCK(launch_grouped_zblocks(E.fp64, P, W.z_items.as<GroupItem>(), W.n_z, W.active(), W.z_smem, W.z_part.p, E.st));
   BCK(launch_grouped_assemble(E.fp64, P, W.asm_items.as<GroupItem>(), W.n_asm, W.active(), W.main_part.p,
                               W.band_part.p, W.z_part.p, E.st));
-  BCK(launch_grouped_chol_solve(E.mixed, P, np, W.active(), 5, W.status(), W.chol_smem, E.st));
+  BCK(launch_grouped_chol_solve(E.mixed, P, np, W.active(), 5, W.status(), W.chol_smem, kCtaSolveMaxN, E.st));
+  if (!with_ls_init) return MNL_OK;
   ls_init_kernel<<<nb, tb, 0, E.st>>>(np, P, W.active(), W.pending(), W.status());
+  BCK(cudaGetLastError());
+  return MNL_OK;
+}
+
+int enqueue_ls_init(Engine &E, WorkSet &W) {
+  const int np = W.count;
+  ls_init_kernel<<<(np + 255) / 256, 256, 0, E.st>>>(np, dprobs(W), W.active(), W.pending(), W.status());
   BCK(cudaGetLastError());
   return MNL_OK;
 }
@@ -581,7 +607,8 @@ int finish_iteration(Engine &E, WorkSet &W, const mnl_fit_opts &o, double stepto
     ++rounds;
   }
   const int np = W.count;
-  theta_update_kernel<<<np, 256, 0, E.st>>>(dprobs(W), W.accepted(), W.active(), W.stop(), steptol, o.ftol);
+  theta_update_kernel<<<np, 256, 0, E.st>>>(dprobs(W), W.accepted(), W.active(), W.stop(), steptol, o.ftol,
+                                            E.fp64 ? 0.0 : 1e-5);
   count_kernel<<<1, 256, 0, E.st>>>(np, W.active(), W.pending(), W.counts.as<int>());
   BCK(cudaGetLastError());
   BCK(cudaMemcpyAsync(E.h_counts, W.counts.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, E.st));
@@ -691,7 +718,7 @@ int mnl_batch_create(int count, const mnl_dims *dims, const mnl_data *data, int 
   std::vector<size_t> base(count);
   for (int i = 0; i < count; ++i) {
     b->layouts.push_back(layout_problem(dims[i], E.op, E.fp64, E.mixed, false));
-    if (b->layouts.back().s.n > 1400) return fail(MNL_ERR_UNSUPPORTED);
+    if (b->layouts.back().large) return fail(MNL_ERR_UNSUPPORTED);
     base[i] = bytes;
     bytes += b->layouts.back().bytes;
     b->theta_off.push_back(b->theta_total);
@@ -924,6 +951,61 @@ struct mnl_server {
   }
 };
 
+// Members too large for the one-CTA solve: the multi-CTA mixed solve (float64
+// Cholesky for MNL_FP64, or as the fallback), then their status code.
+int solve_large_members(mnl_server *s, int np) {
+  Engine &E = s->E;
+  WorkSet &W = s->W;
+  std::vector<int> large;
+  for (int i = 0; i < np; ++i)
+    if (s->reqs.at(s->members[i]).L.large) large.push_back(i);
+  if (large.empty()) return MNL_OK;
+  std::vector<int> act(np);
+  BCK(cudaMemcpyAsync(act.data(), W.active(), np * sizeof(int), cudaMemcpyDeviceToHost, E.st));
+  BCK(cudaStreamSynchronize(E.st));
+  std::vector<int> flags(large.size(), 0);
+  for (size_t j = 0; j < large.size(); ++j) {
+    const int i = large[j];
+    if (!act[i]) continue;
+    Request &r = s->reqs.at(s->members[i]);
+    unsigned char *base = s->pool.base + r.off;
+    const int64_t n = r.L.s.n;
+    int *sst = reinterpret_cast<int *>(base + r.L.sstat);
+    int nl = 0;
+    BCK(cudaMemsetAsync(sst, 0, sizeof(int), E.st));
+    BCK(cudaMemsetAsync(base + r.L.ref, 0, 4 * 8, E.st));
+    if (E.mixed)
+      BCK(launch_mixed_solve(n, r.g.F, r.g.F32, reinterpret_cast<float *>(base + r.L.dinv32), r.g.grad, r.g.delta,
+                             reinterpret_cast<double *>(base + r.L.lrwork), reinterpret_cast<float *>(base + r.L.fwork),
+                             reinterpret_cast<double *>(base + r.L.ref), sst, 5, E.st, &nl));
+    else
+      BCK(cudaMemsetAsync(sst, 0xff, sizeof(int), E.st));  // straight to the float64 path
+    BCK(cudaMemcpyAsync(&flags[j], sst, sizeof(int), cudaMemcpyDeviceToHost, E.st));
+  }
+  BCK(cudaStreamSynchronize(E.st));
+  for (size_t j = 0; j < large.size(); ++j) {
+    const int i = large[j];
+    if (!act[i]) continue;
+    Request &r = s->reqs.at(s->members[i]);
+    if (E.mixed && (flags[j] & (8 | 16 | 4)) == 0) continue;
+    unsigned char *base = s->pool.base + r.off;
+    int *sst = reinterpret_cast<int *>(base + r.L.sstat);
+    double *dinv = reinterpret_cast<double *>(base + r.L.dinv);
+    int nl = 0;
+    BCK(cudaMemsetAsync(sst, 0, sizeof(int), E.st));
+    BCK(launch_cholesky(r.L.s.n, r.g.F, dinv, sst, E.st));
+    BCK(launch_cholesky_solve(r.L.s.n, r.g.F, dinv, r.g.grad, r.g.delta, sst, E.st, &nl));
+    int st = 0;
+    BCK(cudaMemcpyAsync(&st, sst, sizeof(int), cudaMemcpyDeviceToHost, E.st));
+    BCK(cudaStreamSynchronize(E.st));
+    if (st & 4) {
+      const int code = MNL_ERR_NOT_PD;
+      BCK(cudaMemcpy(W.status() + i, &code, sizeof(int), cudaMemcpyHostToDevice));
+    }
+  }
+  return MNL_OK;
+}
+
 extern "C" {
 
 void mnl_server_opts_default(mnl_server_opts *o) {
@@ -970,7 +1052,7 @@ int mnl_server_submit(mnl_server *s, const mnl_dims *dims, const mnl_data *host,
   Request r;
   r.dims = d;
   r.L = layout_problem(d, s->E.op, s->E.fp64, s->E.mixed, true);
-  if (r.L.s.n > 1400 || r.L.s.K > 256) return MNL_ERR_UNSUPPORTED;
+  if (r.L.s.K > 256 || r.L.s.nout > 16384) return MNL_ERR_UNSUPPORTED;
   if (r.L.bytes > s->pool.size) return MNL_ERR_OOM;
   r.X.assign(host->X, host->X + (size_t)d.N * d.p);
   if (d.d) r.Y.assign(host->Y, host->Y + (size_t)d.N * d.K * d.d);
@@ -1039,7 +1121,9 @@ int mnl_server_step(mnl_server *s, int32_t *n_active, int32_t *n_queued) {
     BCK(cudaMemcpyAsync(W.active(), ones.data(), (size_t)np * sizeof(int), cudaMemcpyHostToDevice, E.st));
     BCK(cudaMemsetAsync(W.pending(), 0, 4 * (size_t)np * sizeof(int), E.st));
     BCK(cudaMemsetAsync(W.err.p, 0, sizeof(int), E.st));
-    int rc = enqueue_iteration(E, W, s->opts.fit);
+    int rc = enqueue_iteration(E, W, s->opts.fit, false);
+    if (!rc) rc = solve_large_members(s, np);
+    if (!rc) rc = enqueue_ls_init(E, W);
     if (!rc) rc = enqueue_ls_round(E, W, s->opts.fit);
     if (!rc) rc = finish_iteration(E, W, s->opts.fit, s->steptol);
     if (rc) return rc;

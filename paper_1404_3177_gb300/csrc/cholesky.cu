@@ -627,7 +627,7 @@ __device__ double cta_max_abs(const double *v, int64_t n, double *red) {
 template <bool MIXED>
 __global__ void __launch_bounds__(kCtaThreads) grouped_chol_solve_kernel(const GroupProblem *__restrict__ probs,
                                                                          const int *__restrict__ active, int iters,
-                                                                         int *__restrict__ status) {
+                                                                         int *__restrict__ status, int64_t max_n) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
   __shared__ float dinv32[32];
@@ -636,6 +636,7 @@ __global__ void __launch_bounds__(kCtaThreads) grouped_chol_solve_kernel(const G
   if (active[b] == 0) return;
   const GroupProblem &g = probs[b];
   const int64_t n = g.n;
+  if (n > max_n) return;  // solved by the multi-CTA path
   double *xs = reinterpret_cast<double *>(smem);  // [n] solution work vector
   double *ds = xs + n;                            // [n] correction
   unsigned char *panel = smem + (((size_t)2 * n * sizeof(double) + 15) & ~(size_t)15);
@@ -773,18 +774,18 @@ size_t grouped_chol_smem(int64_t nmax) {
 }
 
 cudaError_t launch_grouped_chol_solve(bool mixed, const GroupProblem *probs, int nprob, const int *active,
-                                      int iters, int *status, size_t smem, cudaStream_t st) {
+                                      int iters, int *status, size_t smem, int64_t max_n, cudaStream_t st) {
   cudaError_t e;
   if (mixed) {
     if ((e = cudaFuncSetAttribute(grouped_chol_solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)))
       return e;
-    grouped_chol_solve_kernel<true><<<nprob, kCtaThreads, smem, st>>>(probs, active, iters, status);
+    grouped_chol_solve_kernel<true><<<nprob, kCtaThreads, smem, st>>>(probs, active, iters, status, max_n);
   } else {
     if ((e = cudaFuncSetAttribute(grouped_chol_solve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)))
       return e;
-    grouped_chol_solve_kernel<false><<<nprob, kCtaThreads, smem, st>>>(probs, active, iters, status);
+    grouped_chol_solve_kernel<false><<<nprob, kCtaThreads, smem, st>>>(probs, active, iters, status, max_n);
   }
   return cudaGetLastError();
 }

@@ -98,7 +98,7 @@ cudaError_t launch_pass(const Shape &s, const PassPlan &pl, bool fp64, bool full
 // Per-problem float64 scalars of a batched fit (GroupProblem::scal).
 enum GroupScal {
   kGsL = 0, kGsLabs = 1, kGsGinf = 2, kGsLt = 3, kGsLtabs = 4, kGsT = 5, kGsStepInf = 6, kGsThetaInf = 7,
-  kGsLold = 8, kGsLsEvals = 9, kGsIters = 10, kGsRefine = 11, kGsCount = 16
+  kGsLold = 8, kGsLsEvals = 9, kGsIters = 10, kGsRefine = 11, kGsPrevStep = 12, kGsCount = 16
 };
 
 // Everything a grouped kernel needs to know about one problem (device memory).
@@ -157,9 +157,11 @@ cudaError_t launch_grouped_syrk_f64(const GroupProblem *probs, const SyrkUnit *u
 int f64_chunk_rows();
 
 // One CTA per active problem: delta = (-H)^{-1} g (mixed or float64), see cholesky.cu.
+// Problems with n_theta above max_n are skipped (solved by the multi-CTA path).
+constexpr int64_t kCtaSolveMaxN = 1400;
 size_t grouped_chol_smem(int64_t nmax);
 cudaError_t launch_grouped_chol_solve(bool mixed, const GroupProblem *probs, int nprob, const int *active,
-                                      int iters, int *status, size_t smem, cudaStream_t st);
+                                      int iters, int *status, size_t smem, int64_t max_n, cudaStream_t st);
 
 struct GroupedPassPlan {
   int grid, block, rows, npt;

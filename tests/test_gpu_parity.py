@@ -6,6 +6,7 @@ Tolerances (the stated bars):
   negative Hessian, rel. Frobenius:   1e-10 (FP64)   2e-3 (tensor-core contraction)
   converged coefficients, max|dtheta| / max|theta|: 1e-6 in every mode.
 """
+import math
 import os
 
 import numpy as np
@@ -314,3 +315,15 @@ def test_mixed_solve_falls_back_to_fp64_on_ill_conditioned_design(MNL):
             out[solve] = (th.cpu().numpy(), info)
     assert out["mixed"][1]["fallback"] == 1
     assert np.array_equal(out["fp64"][0], out["mixed"][0])
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_float32_gradient_modes_stop_at_the_noise_floor(MNL, prec):
+    """Few observations per coefficient: the step stops shrinking near the float32
+    gradient's noise floor; the fit stops there, within the coefficient bar."""
+    prob = datagen.make_problem(6000, 30, 50, 0, 0, 4242, intercept=True, theta_sd=0.3 / math.sqrt(50))
+    ref, _ = oracle.fit(prob)
+    with MNL(**dev(prob), precision=prec) as m:
+        th, info = m.fit()
+    assert info["status"] == 0 and info["stop_reason"] in (3, 5), info
+    assert np.abs(th.cpu().numpy() - ref).max() / np.abs(ref).max() <= THETA_TOL

@@ -112,3 +112,19 @@ def test_request_larger_than_the_budget_is_rejected(Server):
         with pytest.raises(MnlError) as e:
             submit(srv, pr)
         assert e.value.status == MNL_ERR_OOM
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp64"])
+def test_large_request_in_the_mix(Server, reqs_and_ref, prec):
+    """n_theta = 1450: solved by the multi-SM path while small requests use one CTA each."""
+    reqs, refs = reqs_and_ref
+    big = datagen.make_problem(6000, 30, 50, 0, 0, 4242, intercept=True, theta_sd=0.3 / math.sqrt(50))
+    assert big.n_theta > 1400
+    ref_big = oracle.fit(big)[0]
+    with Server(precision=prec, mem_budget=8 << 30) as srv:
+        tickets = {submit(srv, r): r for r in reqs[:3] + [big]}
+        res = run_until_done(srv, tickets)
+    for _, (pr, (theta, info)) in res.items():
+        ref = ref_big if pr is big else refs[reqs.index(pr)]
+        assert info["status"] == 0, info
+        assert np.abs(theta - ref).max() / np.abs(ref).max() <= THETA_TOL
