@@ -46,8 +46,9 @@ struct mnl_handle {
   double *F;
   // solve
   int solve_mode;  // MNL_SOLVE_FP64 or MNL_SOLVE_MIXED (resolved)
-  double *dinv, *rwork, *ref;
-  float *F32, *dinv32, *fwork;
+  double *dinv, *ref;  // ref points into mwork
+  float *F32;
+  void *mwork, *cwork;  // mixed-solve and float64-factor workspaces
   // host mirrors (pinned)
   double *h_scal;
   int *h_flags;
@@ -150,12 +151,16 @@ Sizes plan_sizes(const mnl_dims &d, int prec_in, bool owned, int nsm, int *main_
   z.main_part = (size_t)(*main_split) * nmain * kTile * kTile * csz;
   z.band_part = (size_t)(*band_split) * (*nband) * kTile * kTile * csz;
   const int64_t nzt = zblocks_outputs(S);
-  const int64_t zchunks = (nzt + 8191) / 8192;
-  *z_split = (int)std::max<int64_t>(1, std::min<int64_t>((2 * nsm + zchunks - 1) / zchunks, S.N / 256));
+  // observation splits of the Z blocks: about 1024 observations each, at least four CTAs per SM,
+  // at least 256 observations each, and at most 64 MB of partial sums
+  const int64_t zparts = S.f ? zblocks_parts(S, fp64) : 1;
+  int64_t zs = std::max<int64_t>((4 * nsm + zparts - 1) / zparts, S.N / 1024);
+  zs = std::min<int64_t>(zs, std::max<int64_t>(1, ((int64_t)64 << 20) / std::max<int64_t>(1, nzt * (int64_t)tsz)));
+  *z_split = (int)std::max<int64_t>(1, std::min<int64_t>(zs, S.N / 256));
   z.z_part = S.f ? (size_t)(*z_split) * nzt * tsz : 0;
   z.F = (size_t)S.n * S.n * 8;
-  // dinv, rwork, ref (float64); F32, dinv32, fwork (float32)
-  z.solve = ((size_t)S.n + mixed_solve_rwork_doubles(S.n) + 4) * 8 + ((size_t)S.n * S.n + 2 * (size_t)S.n) * 4;
+  // dinv (float64), F32 (float32), the mixed-solve and float64-factor workspaces
+  z.solve = (size_t)S.n * 8 + (size_t)S.n * S.n * 4 + mixed_solve_bytes(S.n) + chol_work_bytes(S.n);
   z.owned = owned ? ((size_t)S.N * S.p + (size_t)S.N * S.K * (S.d + S.f)) * 4 + (size_t)S.N * 4 : 0;
   return z;
 }
@@ -304,12 +309,12 @@ int step_impl(mnl_handle *h, double *theta, mnl_step_info *info, double gtol, bo
   int nl = 0;
   const bool mixed = h->solve_mode == MNL_SOLVE_MIXED;
   if (mixed) {
-    CK(launch_mixed_solve(n, h->F, h->F32, h->dinv32, h->grad, h->delta, h->rwork, h->fwork, h->ref, h->status,
-                          kRefineIters, h->st, &nl));
+    CK(launch_mixed_solve(n, h->F, h->F32, h->grad, h->delta, h->mwork, h->status, h->err, kRefineIters, h->st,
+                          &nl));
     h->launches += nl;
     CK(cudaEventRecord(h->ev[9], h->st));
   } else {
-    CK(launch_cholesky(n, h->F, h->dinv, h->status, h->st));
+    CK(launch_cholesky(n, h->F, h->dinv, h->cwork, h->status, h->err, h->st));
     h->launches += cholesky_launches(n);
     CK(cudaEventRecord(h->ev[9], h->st));
     CK(launch_cholesky_solve(n, h->F, h->dinv, h->grad, h->delta, h->status, h->st, &nl));
@@ -331,12 +336,14 @@ int step_impl(mnl_handle *h, double *theta, mnl_step_info *info, double gtol, bo
     // float32 factor or refinement failed: float64 Cholesky of the intact F
     loc.fallback = 1;
     CK(cudaEventRecord(h->ev[10], h->st));
-    CK(launch_cholesky(n, h->F, h->dinv, h->status, h->st));
+    CK(launch_cholesky(n, h->F, h->dinv, h->cwork, h->status, h->err, h->st));
     CK(launch_cholesky_solve(n, h->F, h->dinv, h->grad, h->delta, h->status, h->st, &nl));
     h->launches += cholesky_launches(n) + nl;
     CK(cudaEventRecord(h->ev[11], h->st));
     CK(cudaMemcpyAsync(h->h_flags, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(h->h_flags + 1, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
+    if (h->h_flags[1]) return MNL_ERR_TIMEOUT;
     t_fallback = elapsed(h->ev[10], h->ev[11]);
   }
   if (h->h_flags[0] & 4) return MNL_ERR_NOT_PD;
@@ -498,10 +505,10 @@ int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *
       (rc = dalloc(h, &h->Ad, z.ops)) || (rc = dalloc(h, &h->main_part, z.main_part)) ||
       (rc = dalloc(h, &h->band_part, z.band_part)) || (rc = dalloc(h, &h->z_part, z.z_part)) ||
       (rc = dalloc(h, &h->F, z.F)) || (rc = dalloc(h, &h->dinv, S.n * 8)) ||
-      (rc = dalloc(h, &h->rwork, mixed_solve_rwork_doubles(S.n) * 8)) || (rc = dalloc(h, &h->ref, 4 * 8)) ||
-      (rc = dalloc(h, &h->F32, (size_t)S.n * S.n * 4)) || (rc = dalloc(h, &h->dinv32, S.n * 4)) ||
-      (rc = dalloc(h, &h->fwork, S.n * 4)))
+      (rc = dalloc(h, &h->F32, (size_t)S.n * S.n * 4)) || (rc = dalloc(h, &h->mwork, mixed_solve_bytes(S.n))) ||
+      (rc = dalloc(h, &h->cwork, chol_work_bytes(S.n))))
     return fail(rc);
+  h->ref = mixed_solve_ref(h->mwork, S.n);
   h->solve_mode = h->fp64 ? MNL_SOLVE_FP64 : MNL_SOLVE_MIXED;
   (void)tsz;
   h->op_bytes = z.ops;

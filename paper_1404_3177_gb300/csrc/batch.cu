@@ -220,13 +220,13 @@ struct Engine {
 struct ProbLayout {
   Shape s;
   int64_t ldn = 0, mc_pad = 0;
-  int nt1d = 0, build_ob = 64, build_kc = 1, zrows = 1, zsplit = 1;
+  int nt1d = 0, build_ob = 64, build_kc = 1, zsplit = 1;
   std::vector<int2> bands;
   std::vector<int> band_map;
   size_t P = 0, zbar = 0, At = 0, Ad = 0, F = 0, F32 = 0, grad = 0, delta = 0, scal = 0, rwork = 0, band_of = 0;
   size_t theta = 0, X = 0, Y = 0, Z = 0, choice = 0;  // owned copies (server requests)
   // multi-CTA solve workspace (problems with n_theta > kCtaSolveMaxN)
-  size_t dinv = 0, dinv32 = 0, lrwork = 0, fwork = 0, ref = 0, sstat = 0;
+  size_t dinv = 0, mwork = 0, cwork = 0, sstat = 0;
   bool large = false;
   size_t bytes = 0;
 };
@@ -241,7 +241,6 @@ ProbLayout layout_problem(const mnl_dims &d, OpType op, bool fp64, bool mixed, b
   L.mc_pad = round_up(s.mc, kTile);
   L.nt1d = (int)(L.mc_pad / kTile);
   build_blocking(s, op, &L.build_ob, &L.build_kc);
-  L.zrows = zblocks_rows(s, fp64);
   L.zsplit = (int)std::max<int64_t>(1, s.N / 4096);
   L.band_map.assign((size_t)L.nt1d * L.nt1d, -1);
   if (s.q > 0)
@@ -270,10 +269,8 @@ ProbLayout layout_problem(const mnl_dims &d, OpType op, bool fp64, bool mixed, b
   L.large = s.n > kCtaSolveMaxN;
   if (L.large) {
     L.dinv = take((size_t)s.n * 8);
-    L.dinv32 = take((size_t)s.n * 4);
-    L.lrwork = take(mixed_solve_rwork_doubles(s.n) * 8);
-    L.fwork = take((size_t)s.n * 4);
-    L.ref = take(4 * 8);
+    L.mwork = mixed ? take(mixed_solve_bytes(s.n)) : 0;
+    L.cwork = take(chol_work_bytes(s.n));
     L.sstat = take(16);
     if (!mixed) L.F32 = 0;
   }
@@ -313,7 +310,6 @@ void bind_problem(const ProbLayout &L, unsigned char *base, const mnl_data *data
   g.mc_pad = L.mc_pad;
   g.nt1d = L.nt1d;
   g.zsplit = L.zsplit;
-  g.zrows = L.zrows;
   g.build_ob = L.build_ob;
   g.build_kc = L.build_kc;
   g.band_of = reinterpret_cast<int *>(base + L.band_of);
@@ -472,10 +468,9 @@ int ws_build(Engine &E, WorkSet &W, const std::vector<const ProbLayout *> &L, in
       bsm = std::max(bsm, build_smem_bytes(s, E.op, l.build_ob, l.build_kc));
     }
     if (s.f > 0) {
-      const int64_t nzt = zblocks_outputs(s);
-      const int chunks = (int)((nzt + 8191) / 8192);
-      for (int k = 0; k < l.zsplit * chunks; ++k) zi.push_back({i, k});
-      zsm = std::max(zsm, zblocks_smem(s, l.zrows, E.fp64));
+      const int parts = zblocks_parts(s, E.fp64);
+      for (int k = 0; k < l.zsplit * parts; ++k) zi.push_back({i, k});
+      zsm = std::max(zsm, zblocks_smem(s, E.fp64));
     }
     const int ncb = (int)((s.n + kAssembleCols - 1) / kAssembleCols);
     for (int k = 0; k < ncb; ++k) ai.push_back({i, k});
@@ -973,12 +968,11 @@ int solve_large_members(mnl_server *s, int np) {
     int *sst = reinterpret_cast<int *>(base + r.L.sstat);
     int nl = 0;
     BCK(cudaMemsetAsync(sst, 0, sizeof(int), E.st));
-    BCK(cudaMemsetAsync(base + r.L.ref, 0, 4 * 8, E.st));
-    if (E.mixed)
-      BCK(launch_mixed_solve(n, r.g.F, r.g.F32, reinterpret_cast<float *>(base + r.L.dinv32), r.g.grad, r.g.delta,
-                             reinterpret_cast<double *>(base + r.L.lrwork), reinterpret_cast<float *>(base + r.L.fwork),
-                             reinterpret_cast<double *>(base + r.L.ref), sst, 5, E.st, &nl));
-    else
+    if (E.mixed) {
+      void *mw = base + r.L.mwork;
+      BCK(cudaMemsetAsync(mixed_solve_ref(mw, n), 0, 4 * 8, E.st));
+      BCK(launch_mixed_solve(n, r.g.F, r.g.F32, r.g.grad, r.g.delta, mw, sst, W.err.as<int>(), 5, E.st, &nl));
+    } else
       BCK(cudaMemsetAsync(sst, 0xff, sizeof(int), E.st));  // straight to the float64 path
     BCK(cudaMemcpyAsync(&flags[j], sst, sizeof(int), cudaMemcpyDeviceToHost, E.st));
   }
@@ -993,7 +987,7 @@ int solve_large_members(mnl_server *s, int np) {
     double *dinv = reinterpret_cast<double *>(base + r.L.dinv);
     int nl = 0;
     BCK(cudaMemsetAsync(sst, 0, sizeof(int), E.st));
-    BCK(launch_cholesky(r.L.s.n, r.g.F, dinv, sst, E.st));
+    BCK(launch_cholesky(r.L.s.n, r.g.F, dinv, base + r.L.cwork, sst, W.err.as<int>(), E.st));
     BCK(launch_cholesky_solve(r.L.s.n, r.g.F, dinv, r.g.grad, r.g.delta, sst, E.st, &nl));
     int st = 0;
     BCK(cudaMemcpyAsync(&st, sst, sizeof(int), cudaMemcpyDeviceToHost, E.st));

@@ -22,20 +22,25 @@ namespace {
 // ---------------------------------------------------------------------------
 
 // Rounding of the operands.  TF32 rounds to nearest (cvt.rna).  BF16 rounds
-// stochastically: the 16 discarded bits of the float32 value are replaced by
-// a uniform random draw before truncation, so the rounded value is unbiased.
-// With round-to-nearest, designs in which many observations share the same
-// P_ik (an intercept-only model, indicator columns) would give every product
-// the same rounding error; unbiased rounding turns that into independent
-// errors that average out over the observations.  The random bits are a hash
-// of (operand, column, observation pair), so results are reproducible.
+// stochastically: a random dither is added below the kept bits of the float32
+// value before truncation, so the rounded value is unbiased (to within 2^-8 of
+// a BF16 unit with the 8 dither bits used here).  With round-to-nearest,
+// designs in which many observations share the same P_ik (an intercept-only
+// model, indicator columns) would give every product the same rounding error;
+// unbiased rounding turns that into independent errors that average out over
+// the observations.  The dither is a hash of (column, observation), so results
+// are reproducible.
+//
+// put8 stores 8 consecutive observations of one operand row (16-byte stores).
 template <OpType OT>
 struct OpStore;
 template <>
 struct OpStore<OpType::F64> {
   using CT = double;
-  __device__ static void put(void *base, int64_t idx, double a, double b, uint32_t) {
-    *reinterpret_cast<double2 *>(reinterpret_cast<double *>(base) + idx) = make_double2(a, b);
+  __device__ static void put8(void *row, const double v[8], uint32_t, uint32_t) {
+    double2 *d = reinterpret_cast<double2 *>(row);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) d[u] = make_double2(v[2 * u], v[2 * u + 1]);
   }
 };
 __device__ __forceinline__ float to_tf32(float x) {
@@ -46,18 +51,32 @@ __device__ __forceinline__ float to_tf32(float x) {
 template <>
 struct OpStore<OpType::TF32> {
   using CT = float;
-  __device__ static void put(void *base, int64_t idx, float a, float b, uint32_t) {
-    *reinterpret_cast<float2 *>(reinterpret_cast<float *>(base) + idx) = make_float2(to_tf32(a), to_tf32(b));
+  __device__ static void put8(void *row, const float v[8], uint32_t, uint32_t) {
+    float4 *d = reinterpret_cast<float4 *>(row);
+    d[0] = make_float4(to_tf32(v[0]), to_tf32(v[1]), to_tf32(v[2]), to_tf32(v[3]));
+    d[1] = make_float4(to_tf32(v[4]), to_tf32(v[5]), to_tf32(v[6]), to_tf32(v[7]));
   }
 };
+// Byte b of w placed in bits 8..15 (zero elsewhere): the dither of one value.
+__device__ __forceinline__ uint32_t dither(uint32_t w, int b) {
+  uint32_t r;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(w), "r"(0u), "r"(0x4404u | ((uint32_t)b << 4)));
+  return r;
+}
 template <>
 struct OpStore<OpType::BF16> {
   using CT = float;
-  // r: 32 random bits, 16 for each of the two values.
-  __device__ static void put(void *base, int64_t idx, float a, float b, uint32_t r) {
-    const uint32_t ua = __float_as_uint(a) + (r & 0xFFFFu);
-    const uint32_t ub = __float_as_uint(b) + (r >> 16);
-    *reinterpret_cast<uint32_t *>(reinterpret_cast<__nv_bfloat16 *>(base) + idx) = (ua >> 16) | (ub & 0xFFFF0000u);
+  // w0, w1: 8 random bytes, one per value.
+  __device__ static void put8(void *row, const float v[8], uint32_t w0, uint32_t w1) {
+    uint32_t o[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t w = u < 2 ? w0 : w1;
+      const uint32_t ua = __float_as_uint(v[2 * u]) + dither(w, (2 * u) & 3);
+      const uint32_t ub = __float_as_uint(v[2 * u + 1]) + dither(w, (2 * u + 1) & 3);
+      o[u] = (ua >> 16) | (ub & 0xFFFF0000u);
+    }
+    *reinterpret_cast<uint4 *>(row) = make_uint4(o[0], o[1], o[2], o[3]);
   }
 };
 
@@ -67,70 +86,128 @@ __device__ __forceinline__ uint32_t mix3(uint32_t s, uint32_t c, uint32_t i) {
   h = (h ^ (h >> 16)) * 0x7FEB352Du;
   return h ^ (h >> 15);
 }
+__device__ __forceinline__ uint32_t remix(uint32_t h, uint32_t k) {
+  uint32_t w = (h ^ (k * 0x9E3779B9u)) * 0x85EBCA6Bu;
+  return w ^ (w >> 13);
+}
+
+constexpr int kBob = 64;        // observations per builder block (8 lanes x 8)
+constexpr int kBs = kBob + 4;   // shared row stride (16-byte aligned rows)
 
 struct BuildDims {
   int64_t N, ldn;
   int K, p, d, q;
-  int ob;  // observations per CTA (even)
+  int ob;  // observations per block (kBob)
   int kc;  // classes per Y staging chunk
 };
 
-// Shared memory (row strides made odd so that lanes reading every other row
-// hit distinct banks): Ps[ob][K|1], Ws[ob][K|1] (P and sqrt(P(1-P)), compute
-// type), Xs[ob][p|1], Ys[ob][(kc*d)|1] (float32).
+// Shared memory, transposed so that observations are contiguous:
+//   PsT[K][kBs], WsT[K][kBs] (P and sqrt(P(1-P)), compute type),
+//   XsT[p][kBs], YsT[kc*d][kBs] (float32).
+// A warp writes 4 operand rows at a time: lanes 8c..8c+7 take row c of the
+// group, 8 observations each (one 16-byte store per lane and operand for BF16).
 template <OpType OT, typename PT>
 __device__ __forceinline__ void build_block(const BuildDims &D, const float *__restrict__ X,
                                             const float *__restrict__ Y, const PT *__restrict__ P, void *At,
                                             void *Ad, int64_t blk) {
   using CT = typename OpStore<OT>::CT;
+  constexpr int esz = OT == OpType::F64 ? 8 : OT == OpType::TF32 ? 4 : 2;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int K = D.K, p = D.p, d = D.d, q = D.q, OB = D.ob;
-  const int SP = K | 1, SX = p | 1;
-  CT *Ps = reinterpret_cast<CT *>(smem);
-  CT *Ws = Ps + (size_t)OB * SP;
-  float *Xs = reinterpret_cast<float *>(smem + ((2 * (size_t)OB * SP * sizeof(CT) + 15) & ~(size_t)15));
-  float *Ys = Xs + (((size_t)OB * SX + 3) & ~(size_t)3);
-  const int64_t i0 = blk * OB;
-  const int nobs = (int)min((int64_t)OB, D.N - i0);
+  const int K = D.K, p = D.p, d = D.d, q = D.q;
+  CT *PsT = reinterpret_cast<CT *>(smem);
+  CT *WsT = PsT + (size_t)K * kBs;
+  float *XsT = reinterpret_cast<float *>(WsT + (size_t)K * kBs);
+  float *YsT = XsT + (size_t)p * kBs;
+  const int64_t i0 = blk * kBob;
+  const int nobs = (int)min((int64_t)kBob, D.N - i0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
 
-  for (int e = tid; e < OB * K; e += blockDim.x) {
-    const int r = e / K, k = e % K;
-    const CT pk = r < nobs ? (CT)P[i0 * K + e] : (CT)0;
-    const CT w = pk * ((CT)1 - pk);
-    Ps[r * SP + k] = pk;
-    Ws[r * SP + k] = w > (CT)0 ? sqrt(w) : (CT)0;
+  // staging, 8 loads in flight per thread
+  for (int e0 = 0; e0 < kBob * K; e0 += 8 * 256) {
+    PT v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + tid + u * 256;
+      v[u] = (e < kBob * K && e / K < nobs) ? P[i0 * K + e] : (PT)0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + tid + u * 256;
+      if (e < kBob * K) {
+        const int r = e / K, k = e - r * K;
+        const CT pk = (CT)v[u], w = pk * ((CT)1 - pk);
+        PsT[k * kBs + r] = pk;
+        WsT[k * kBs + r] = w > (CT)0 ? sqrt(w) : (CT)0;
+      }
+    }
   }
-  for (int e = tid; e < OB * p; e += blockDim.x) {
-    const int r = e / p, l = e % p;
-    Xs[r * SX + l] = r < nobs ? X[i0 * p + e] : 0.f;
+  for (int e0 = 0; e0 < kBob * p; e0 += 8 * 256) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + tid + u * 256;
+      v[u] = (e < kBob * p && e / p < nobs) ? __ldg(X + i0 * p + e) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + tid + u * 256;
+      if (e < kBob * p) {
+        const int r = e / p, l = e - r * p;
+        XsT[l * kBs + r] = v[u];
+      }
+    }
   }
 
+  const int cl = lane >> 3, oc = (lane & 7) * 8;
+  const uint32_t iobs = (uint32_t)(i0 + oc);
   for (int k0 = 1; k0 < K; k0 += D.kc) {
     const int k1 = min(K, k0 + D.kc);
-    const int w = (k1 - k0) * d, SY = w | 1;
+    const int w = (k1 - k0) * d;
     __syncthreads();
     if (d) {
-      for (int e = tid; e < OB * w; e += blockDim.x) {
-        const int r = e / w, c = e % w;
-        Ys[r * SY + c] = r < nobs ? Y[((i0 + r) * K + k0) * d + c] : 0.f;
+      for (int e0 = 0; e0 < kBob * w; e0 += 8 * 256) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int e = e0 + tid + u * 256;
+          const int r = e / w;
+          v[u] = (e < kBob * w && r < nobs) ? __ldg(Y + ((i0 + r) * K + k0) * d + (e - r * w)) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int e = e0 + tid + u * 256;
+          if (e < kBob * w) {
+            const int r = e / w;
+            YsT[(e - r * w) * kBs + r] = v[u];
+          }
+        }
       }
     }
     __syncthreads();
     const int ncols = (k1 - k0) * q;
-    for (int cc = warp; cc < ncols; cc += nw) {
-      const int k = k0 + cc / q, l = cc % q;
+    for (int cg = warp * 4; cg < ncols; cg += nw * 4) {
+      const int cc = cg + cl;
+      if (cc >= ncols) continue;
+      const int kk = cc / q, l = cc - kk * q, k = k0 + kk;
       const int64_t c = (int64_t)(k - 1) * q + l;
-      const float *mcol = l < p ? Xs + l : Ys + (k - k0) * d + (l - p);
-      const int mstride = l < p ? SX : SY;
-      for (int r = 2 * lane; r < OB; r += 64) {
-        const CT m0 = (CT)mcol[r * mstride], m1 = (CT)mcol[(r + 1) * mstride];
-        const CT p0 = Ps[r * SP + k], p1 = Ps[(r + 1) * SP + k];
-        const CT w0 = Ws[r * SP + k], w1 = Ws[(r + 1) * SP + k];
-        const uint32_t ii = (uint32_t)(i0 + r), c32 = (uint32_t)c;
-        OpStore<OT>::put(At, c * D.ldn + i0 + r, p0 * m0, p1 * m1, mix3(1u, c32, ii));
-        OpStore<OT>::put(Ad, c * D.ldn + i0 + r, w0 * m0, w1 * m1, mix3(2u, c32, ii));
+      const float *mrow = l < p ? XsT + l * kBs : YsT + (kk * d + (l - p)) * kBs;
+      float m[8];
+      CT pv[8], wv[8];
+      {
+        const float4 a = *reinterpret_cast<const float4 *>(mrow + oc);
+        const float4 b = *reinterpret_cast<const float4 *>(mrow + oc + 4);
+        m[0] = a.x; m[1] = a.y; m[2] = a.z; m[3] = a.w; m[4] = b.x; m[5] = b.y; m[6] = b.z; m[7] = b.w;
       }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        pv[u] = PsT[k * kBs + oc + u] * (CT)m[u];
+        wv[u] = WsT[k * kBs + oc + u] * (CT)m[u];
+      }
+      const uint32_t h = mix3(1u, (uint32_t)c, iobs);
+      unsigned char *rowA = reinterpret_cast<unsigned char *>(At) + (c * D.ldn + i0 + oc) * esz;
+      unsigned char *rowD = reinterpret_cast<unsigned char *>(Ad) + (c * D.ldn + i0 + oc) * esz;
+      OpStore<OT>::put8(rowA, pv, h, remix(h, 1u));
+      OpStore<OT>::put8(rowD, wv, remix(h, 2u), remix(h, 3u));
     }
   }
 }
@@ -236,101 +313,341 @@ __global__ void __launch_bounds__(256, 1) grouped_syrk_f64_kernel(const GroupPro
 //   C_X[l][k f + j] = sum_i x_il W_ikj                 (beta_k x alpha)
 //   C_Y[k][l][j]    = sum_i y_ikl W_ikj                (gamma_k x alpha)
 //   A[j1][j2]       = sum_i sum_k W_ikj1 (z_ikj2 - zbar_ij2)
-// Output vector per split: [C_X: p*K*f | C_Y: K*d*f | A: f*f] (k = 0 entries
-// of C_X and C_Y are computed but not used).  A CTA stages a tile of rows
-// (X, Y, Z, P, zbar contiguous in memory), forms W and z - zbar in shared
-// memory and adds the tile to the outputs it owns; grid.y splits the output
-// vector when one CTA cannot own all of it.
+// Output vector per observation split: [C_X: p*K*f | C_Y: K*d*f | A: f*f]
+// (k = 0 entries of C_X and C_Y are computed but not used).
+//
+// The work of one split is cut into parts, one CTA each:
+//   * C_X tiles of 64 (l) x 64 (c = k f + j): X and W rows are staged in a
+//     double-buffered shared tile (the next tile's loads are in flight while
+//     the current one is used) and every thread accumulates a 4 x 4 block of
+//     Xᵀ W in registers (two 16-byte shared loads per 16 FMAs);
+//   * C_Y chunks of kZyOut outputs, a thread per output;
+//   * the alpha block: the (observation, alternative) pairs of a staged tile
+//     are dealt to thread subsets, each thread accumulating a 4 x 4 block of
+//     the f x f result; the subsets are added in a fixed order at the end.
 // ---------------------------------------------------------------------------
 
-constexpr int kZSlots = 16;   // outputs per thread
-constexpr int kZThreads = 512;
+constexpr int kZThreads = 256;
+constexpr int kZxTile = 64;    // C_X tile edge (l and c)
+constexpr int kZxRows = 32;    // observations per staged C_X tile
+constexpr int kZxStride = 68;  // shared row stride of the C_X tiles (multiple of 4)
+constexpr int kZySlots = 8;
+constexpr int kZyOut = kZThreads * kZySlots;  // C_Y outputs per part
+constexpr size_t kZBudget = 96 * 1024;        // shared bytes of a C_Y or alpha tile
+constexpr int kZBatch = 8;                    // rows staged per batch of loads
+
+struct ZPlan {
+  int nl, nc;  // C_X tiles over l (p) and c (K f)
+  int ny;      // C_Y parts
+  int kspan;   // classes a C_Y part spans at most
+  int ry, ra;  // observations per staged tile of a C_Y / alpha part
+  int fs;      // f rounded up to a multiple of 4
+  __host__ __device__ int parts() const { return nl * nc + ny + 1; }
+};
+
+__host__ __device__ inline size_t zmin(size_t a, size_t b) { return a < b ? a : b; }
+__host__ __device__ inline size_t zmax(size_t a, size_t b) { return a > b ? a : b; }
+
+__host__ __device__ inline ZPlan make_zplan(int K, int p, int d, int f, int tsz) {
+  ZPlan z;
+  const int Kf = K * f;
+  z.nl = (p + kZxTile - 1) / kZxTile;
+  z.nc = (Kf + kZxTile - 1) / kZxTile;
+  const int64_t ny = (int64_t)K * d * f;
+  z.ny = (int)((ny + kZyOut - 1) / kZyOut);
+  z.fs = (f + 3) & ~3;
+  z.kspan = d ? (int)zmin((size_t)K, (size_t)(kZyOut / (d * f) + 2)) : 0;
+  const size_t yrow = (size_t)z.kspan * ((size_t)d * 4 + (size_t)f * tsz);
+  z.ry = yrow ? (int)zmin(32, zmax(1, kZBudget / yrow)) : 1;
+  const size_t arow = (size_t)2 * K * z.fs * tsz, red = (size_t)kZThreads * 16 * tsz;
+  z.ra = (int)zmin(32, zmax(1, (kZBudget - red) / arow));
+  return z;
+}
 
 struct ZDims {
   int64_t N;
   int K, p, d, f;
-  int rows;     // rows per tile
-  int nsplit;   // row splits (grid.x)
+  int nsplit;   // observation splits
   int64_t nzt;  // outputs per split
+  ZPlan zp;
 };
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  __device__ static void load(const float *p, float v[4]) {
+    const float4 a = *reinterpret_cast<const float4 *>(p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  }
+};
+template <>
+struct Vec4<double> {
+  __device__ static void load(const double *p, double v[4]) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+};
+
+// C_X tile (lb, cb) over observations [r0, r1).
+template <typename T>
+__device__ __forceinline__ void zx_part(const ZDims &D, const float *__restrict__ X, const float *__restrict__ Z,
+                                        const T *__restrict__ P, const T *__restrict__ zbar, int64_t r0, int64_t r1,
+                                        int lb, int cb, T *__restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int kBuf = kZxRows * kZxStride;
+  float *Xs = reinterpret_cast<float *>(smem);  // [2][kZxRows][kZxStride]
+  T *Ws = reinterpret_cast<T *>(Xs + 2 * kBuf);  // [2][kZxRows][kZxStride]
+  const int K = D.K, p = D.p, f = D.f, Kf = K * f;
+  const int l0 = lb * kZxTile, c0 = cb * kZxTile;
+  const int nlw = min(kZxTile, p - l0), ncw = min(kZxTile, Kf - c0);
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  // Staging: this thread moves column cc of rows rr, rr + 4, ..., rr + 28.
+  const int cc = tid & 63, rr = tid >> 6;
+  const bool xcol = cc < nlw, zcol = cc < ncw;
+  const int c = c0 + cc, k = zcol ? c / f : 0, j = zcol ? c - k * f : 0;
+  constexpr int kPer = kZxRows / 4;
+  float xv[kPer], zv[kPer];
+  T pv[kPer], bv[kPer];
+  auto fetch = [&](int64_t rb) {
+#pragma unroll
+    for (int s = 0; s < kPer; ++s) {
+      const int64_t i = rb + rr + 4 * s;
+      const bool in = i < r1;
+      xv[s] = (in && xcol) ? __ldg(X + i * p + l0 + cc) : 0.f;
+      if (in && zcol) {
+        zv[s] = __ldg(Z + i * Kf + c);
+        pv[s] = P[i * K + k];
+        bv[s] = zbar[i * f + j];
+      } else {
+        zv[s] = 0.f; pv[s] = (T)0; bv[s] = (T)0;
+      }
+    }
+  };
+  auto put = [&](int buf) {
+#pragma unroll
+    for (int s = 0; s < kPer; ++s) {
+      const int o = buf * kBuf + (rr + 4 * s) * kZxStride + cc;
+      Xs[o] = xv[s];
+      Ws[o] = pv[s] * ((T)zv[s] - bv[s]);
+    }
+  };
+  T acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = (T)0;
+  fetch(r0);
+  put(0);
+  __syncthreads();
+  int buf = 0;
+  for (int64_t rb = r0; rb < r1; rb += kZxRows) {
+    const bool more = rb + kZxRows < r1;
+    if (more) fetch(rb + kZxRows);
+    const float *xs = Xs + buf * kBuf + ty * 4;
+    const T *ws = Ws + buf * kBuf + tx * 4;
+#pragma unroll 8
+    for (int r = 0; r < kZxRows; ++r) {
+      const float4 a4 = *reinterpret_cast<const float4 *>(xs + r * kZxStride);
+      const T a[4] = {(T)a4.x, (T)a4.y, (T)a4.z, (T)a4.w};
+      T b[4];
+      Vec4<T>::load(ws + r * kZxStride, b);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+    if (more) put(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int l = l0 + ty * 4 + u;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int cw = c0 + tx * 4 + v;
+      if (l < p && cw < Kf) out[(int64_t)l * Kf + cw] = acc[u][v];
+    }
+  }
+}
+
+// C_Y outputs [o0, o0 + kZyOut) over observations [r0, r1).
+template <typename T>
+__device__ __forceinline__ void zy_part(const ZDims &D, const float *__restrict__ Y, const float *__restrict__ Z,
+                                        const T *__restrict__ P, const T *__restrict__ zbar, int64_t r0, int64_t r1,
+                                        int yc, T *__restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int K = D.K, d = D.d, f = D.f, Kf = K * f, df = d * f;
+  const int64_t ny = (int64_t)K * df;
+  const int64_t o0 = (int64_t)yc * kZyOut, o1 = o0 + kZyOut < ny ? o0 + kZyOut : ny;
+  const int kb = (int)(o0 / df), ku = (int)((o1 - 1) / df) - kb + 1;
+  const int YW = ku * d, WW = ku * f, R = D.zp.ry;
+  float *Ys = reinterpret_cast<float *>(smem);                                   // [R][YW]
+  T *Wy = reinterpret_cast<T *>(smem + (((size_t)R * YW * 4 + 15) & ~(size_t)15));  // [R][WW]
+  const int tid = threadIdx.x;
+  int yo[kZySlots], wo[kZySlots];
+#pragma unroll
+  for (int s = 0; s < kZySlots; ++s) {
+    const int64_t o = o0 + tid + (int64_t)s * kZThreads;
+    if (o < o1) {
+      const int k = (int)(o / df), l = (int)((o / f) % d), j = (int)(o % f);
+      yo[s] = (k - kb) * d + l;
+      wo[s] = (k - kb) * f + j;
+    } else {
+      yo[s] = -1; wo[s] = 0;
+    }
+  }
+  T acc[kZySlots];
+#pragma unroll
+  for (int s = 0; s < kZySlots; ++s) acc[s] = (T)0;
+  for (int64_t rb = r0; rb < r1; rb += R) {
+    const int nr = (int)(r1 - rb < R ? r1 - rb : R);
+    __syncthreads();
+    // Each thread owns fixed columns and moves kZBatch rows at a time, so that
+    // kZBatch loads per operand are in flight.
+    for (int c = tid; c < YW; c += kZThreads) {
+      const float *src = Y + (rb * K + kb) * d + c;
+      for (int q0 = 0; q0 < nr; q0 += kZBatch) {
+        float v[kZBatch];
+#pragma unroll
+        for (int u = 0; u < kZBatch; ++u) v[u] = q0 + u < nr ? __ldg(src + (int64_t)(q0 + u) * K * d) : 0.f;
+#pragma unroll
+        for (int u = 0; u < kZBatch; ++u)
+          if (q0 + u < nr) Ys[(q0 + u) * YW + c] = v[u];
+      }
+    }
+    for (int c = tid; c < WW; c += kZThreads) {
+      const int kk = c / f, j = c - kk * f;
+      for (int q0 = 0; q0 < nr; q0 += kZBatch) {
+        float zv[kZBatch];
+        T pv[kZBatch], bv[kZBatch];
+#pragma unroll
+        for (int u = 0; u < kZBatch; ++u) {
+          const int64_t i = rb + q0 + u;
+          const bool in = q0 + u < nr;
+          zv[u] = in ? __ldg(Z + i * Kf + (int64_t)kb * f + c) : 0.f;
+          pv[u] = in ? P[i * K + kb + kk] : (T)0;
+          bv[u] = in ? zbar[i * f + j] : (T)0;
+        }
+#pragma unroll
+        for (int u = 0; u < kZBatch; ++u)
+          if (q0 + u < nr) Wy[(q0 + u) * WW + c] = pv[u] * ((T)zv[u] - bv[u]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < kZySlots; ++s) {
+      if (yo[s] < 0) continue;
+      T a0 = (T)0, a1 = (T)0;
+      int r = 0;
+      for (; r + 1 < nr; r += 2) {
+        a0 = fma((T)Ys[r * YW + yo[s]], Wy[r * WW + wo[s]], a0);
+        a1 = fma((T)Ys[(r + 1) * YW + yo[s]], Wy[(r + 1) * WW + wo[s]], a1);
+      }
+      if (r < nr) a0 = fma((T)Ys[r * YW + yo[s]], Wy[r * WW + wo[s]], a0);
+      acc[s] += a0 + a1;
+    }
+  }
+  const int64_t nx = (int64_t)D.p * Kf;
+#pragma unroll
+  for (int s = 0; s < kZySlots; ++s)
+    if (yo[s] >= 0) out[nx + o0 + tid + (int64_t)s * kZThreads] = acc[s];
+}
+
+// Alpha block over observations [r0, r1).
+template <typename T>
+__device__ __forceinline__ void za_part(const ZDims &D, const float *__restrict__ Z, const T *__restrict__ P,
+                                        const T *__restrict__ zbar, int64_t r0, int64_t r1, T *__restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int K = D.K, f = D.f, Kf = K * f, fs = D.zp.fs, R = D.zp.ra;
+  const int nm4 = fs / 4, nm = nm4 * nm4;  // 4 x 4 micro-tiles of the f x f block
+  T *Wa = reinterpret_cast<T *>(smem);      // [R*K][fs]
+  T *Za = Wa + (size_t)R * K * fs;          // [R*K][fs]
+  T *red = Za + (size_t)R * K * fs;         // [kZThreads][16]
+  const int tid = threadIdx.x;
+  const int64_t nx = (int64_t)D.p * Kf, ny = (int64_t)K * D.d * f;
+  for (int m0 = 0; m0 < nm; m0 += kZThreads) {  // more than one pass only when f > 64
+    const int nmp = nm - m0 < kZThreads ? nm - m0 : kZThreads;  // micro-tiles of this pass
+    const int S = kZThreads / nmp;                               // thread subsets
+    const int m = m0 + tid % nmp, s = tid / nmp;
+    const bool act = s < S;
+    const int mi = m / nm4, mj = m - mi * nm4;
+    T acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = (T)0;
+    for (int64_t rb = r0; rb < r1; rb += R) {
+      const int nr = (int)(r1 - rb < R ? r1 - rb : R);
+      __syncthreads();
+      for (int c = tid; c < K * fs; c += kZThreads) {  // fixed columns, kZBatch rows in flight
+        const int kk = c / fs, j = c - kk * fs;
+        const bool jin = j < f;
+        for (int q0 = 0; q0 < nr; q0 += kZBatch) {
+          float zv[kZBatch];
+          T pv[kZBatch], bv[kZBatch];
+#pragma unroll
+          for (int u = 0; u < kZBatch; ++u) {
+            const int64_t i = rb + q0 + u;
+            const bool in = jin && q0 + u < nr;
+            zv[u] = in ? __ldg(Z + i * Kf + kk * f + j) : 0.f;
+            pv[u] = in ? P[i * K + kk] : (T)0;
+            bv[u] = in ? zbar[i * f + j] : (T)0;
+          }
+#pragma unroll
+          for (int u = 0; u < kZBatch; ++u) {
+            if (q0 + u >= nr) continue;
+            const T zc = (T)zv[u] - bv[u];
+            Wa[((size_t)(q0 + u) * K) * fs + c] = pv[u] * zc;
+            Za[((size_t)(q0 + u) * K) * fs + c] = zc;
+          }
+        }
+      }
+      __syncthreads();
+      if (act) {
+        const int ne = nr * K;
+        for (int e = s; e < ne; e += S) {
+          T a[4], b[4];
+          Vec4<T>::load(Wa + (size_t)e * fs + mi * 4, a);
+          Vec4<T>::load(Za + (size_t)e * fs + mj * 4, b);
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        }
+      }
+    }
+    // fixed-order sum over the subsets
+    __syncthreads();
+    if (act)
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) red[(size_t)tid * 16 + u * 4 + v] = acc[u][v];
+    __syncthreads();
+    for (int o = tid; o < f * f; o += kZThreads) {
+      const int j1 = o / f, j2 = o - (o / f) * f;
+      const int mo = (j1 / 4) * nm4 + j2 / 4;
+      if (mo < m0 || mo >= m0 + nmp) continue;
+      const int uv = (j1 & 3) * 4 + (j2 & 3);
+      T v = (T)0;
+      for (int ss = 0; ss < S; ++ss) v += red[(size_t)(ss * nmp + (mo - m0)) * 16 + uv];
+      out[nx + ny + o] = v;
+    }
+  }
+}
 
 template <typename T>
 __device__ __forceinline__ void zblocks_item(const ZDims &D, const float *__restrict__ X,
                                              const float *__restrict__ Y, const float *__restrict__ Z,
                                              const T *__restrict__ P, const T *__restrict__ zbar, int split,
-                                             int chunk, T *__restrict__ out_row) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int K = D.K, p = D.p, d = D.d, f = D.f, R = D.rows;
-  const int Kf = K * f, Kd = K * d;
-  T *Ws = reinterpret_cast<T *>(smem);          // [R][K f]
-  T *Zc = Ws + (size_t)R * Kf;                   // [R][K f]
-  float *Xs = reinterpret_cast<float *>(Zc + (size_t)R * Kf);  // [R][p]
-  float *Ys = Xs + (size_t)R * p;                // [R][K d]
-  const int tid = threadIdx.x;
+                                             int part, T *__restrict__ out_row) {
   const int64_t r0 = D.N * split / D.nsplit, r1 = D.N * (split + 1) / D.nsplit;
-  const int64_t obase = (int64_t)chunk * kZThreads * kZSlots;
-  const int64_t nx = (int64_t)p * Kf, ny = (int64_t)Kd * f;
-  // Slot decoding, once: kind (0 C_X, 1 C_Y, 2 A, 3 none), the two operand
-  // offsets inside a staged row, and their row strides.
-  int kind[kZSlots], ou[kZSlots], ov[kZSlots];
-#pragma unroll
-  for (int sl = 0; sl < kZSlots; ++sl) {
-    const int64_t o = obase + tid + (int64_t)sl * blockDim.x;
-    if (o >= D.nzt) { kind[sl] = 3; ou[sl] = ov[sl] = 0; }
-    else if (o < nx) { kind[sl] = 0; ou[sl] = (int)(o / Kf); ov[sl] = (int)(o % Kf); }
-    else if (o < nx + ny) {
-      const int e = (int)(o - nx), k = e / (d * f), l = (e / f) % d, j = e % f;
-      kind[sl] = 1; ou[sl] = k * d + l; ov[sl] = k * f + j;
-    } else {
-      const int e = (int)(o - nx - ny);
-      kind[sl] = 2; ou[sl] = e / f; ov[sl] = e % f;
-    }
-  }
-  T acc[kZSlots];
-#pragma unroll
-  for (int sl = 0; sl < kZSlots; ++sl) acc[sl] = 0;
-  for (int64_t rb = r0; rb < r1; rb += R) {
-    const int nr = (int)min((int64_t)R, r1 - rb);
-    __syncthreads();
-    for (int e = tid; e < nr * K; e += blockDim.x) {
-      const int r = e / K, k = e % K;
-      const int64_t i = rb + r;
-      const T pk = P[i * K + k];
-      const float *z = Z + i * Kf + k * f;
-      const T *zb = zbar + i * f;
-      T *zc = Zc + r * Kf + k * f, *ws = Ws + r * Kf + k * f;
-      for (int j = 0; j < f; ++j) {
-        const T c = (T)z[j] - zb[j];
-        zc[j] = c;
-        ws[j] = pk * c;
-      }
-    }
-    for (int e = tid; e < nr * p; e += blockDim.x) Xs[e] = X[rb * p + e];
-    for (int e = tid; e < nr * Kd; e += blockDim.x) Ys[e] = Y[rb * Kd + e];
-    __syncthreads();
-#pragma unroll
-    for (int sl = 0; sl < kZSlots; ++sl) {
-      T a = 0;
-      if (kind[sl] == 0) {
-        const float *u = Xs + ou[sl];
-        const T *v = Ws + ov[sl];
-        for (int r = 0; r < nr; ++r) a = fma((T)u[r * p], v[r * Kf], a);
-      } else if (kind[sl] == 1) {
-        const float *u = Ys + ou[sl];
-        const T *v = Ws + ov[sl];
-        for (int r = 0; r < nr; ++r) a = fma((T)u[r * Kd], v[r * Kf], a);
-      } else if (kind[sl] == 2) {
-        for (int r = 0; r < nr; ++r)
-          for (int k = 0; k < K; ++k) a = fma(Ws[r * Kf + k * f + ou[sl]], Zc[r * Kf + k * f + ov[sl]], a);
-      }
-      acc[sl] += a;
-    }
-  }
-#pragma unroll
-  for (int sl = 0; sl < kZSlots; ++sl) {
-    const int64_t oo = obase + tid + (int64_t)sl * blockDim.x;
-    if (oo < D.nzt) out_row[oo] = acc[sl];
-  }
+  const int nxp = D.zp.nl * D.zp.nc;
+  if (part < nxp) zx_part<T>(D, X, Z, P, zbar, r0, r1, part / D.zp.nc, part % D.zp.nc, out_row);
+  else if (part < nxp + D.zp.ny) zy_part<T>(D, Y, Z, P, zbar, r0, r1, part - nxp, out_row);
+  else za_part<T>(D, Z, P, zbar, r0, r1, out_row);
 }
 
 template <typename T>
@@ -338,7 +655,7 @@ __global__ void __launch_bounds__(kZThreads) zblocks_kernel(ZDims D, const float
                                                             const float *__restrict__ Y, const float *__restrict__ Z,
                                                             const T *__restrict__ P, const T *__restrict__ zbar,
                                                             T *__restrict__ out) {
-  zblocks_item<T>(D, X, Y, Z, P, zbar, blockIdx.x, blockIdx.y, out + (int64_t)blockIdx.x * D.nzt);
+  zblocks_item<T>(D, X, Y, Z, P, zbar, blockIdx.y, blockIdx.x, out + (int64_t)blockIdx.y * D.nzt);
 }
 
 template <typename T>
@@ -351,13 +668,13 @@ __global__ void __launch_bounds__(kZThreads) grouped_zblocks_kernel(const GroupP
   const GroupProblem &g = probs[it.problem];
   ZDims D;
   D.N = g.N; D.K = g.K; D.p = g.p; D.d = g.d; D.f = g.f;
-  D.rows = g.zrows;
   D.nsplit = g.zsplit;
   D.nzt = (int64_t)g.p * g.K * g.f + (int64_t)g.K * g.d * g.f + (int64_t)g.f * g.f;
-  const int chunks = (int)((D.nzt + (int64_t)kZThreads * kZSlots - 1) / ((int64_t)kZThreads * kZSlots));
-  const int split = it.idx / chunks, chunk = it.idx % chunks;
+  D.zp = make_zplan(g.K, g.p, g.d, g.f, (int)sizeof(T));
+  const int parts = D.zp.parts();
+  const int split = it.idx / parts, part = it.idx % parts;
   zblocks_item<T>(D, g.X, g.Y, g.Z, reinterpret_cast<const T *>(g.P), reinterpret_cast<const T *>(g.zbar), split,
-                  chunk, zpart + g.z_off + (int64_t)split * D.nzt);
+                  part, zpart + g.z_off + (int64_t)split * D.nzt);
 }
 
 // ---------------------------------------------------------------------------
@@ -462,16 +779,15 @@ void grid_2d(int64_t rows, int64_t cols, dim3 &grid, dim3 &block) {
 }  // namespace
 
 size_t build_smem_bytes(const Shape &s, OpType t, int ob, int kc) {
+  (void)ob;
   const size_t csz = t == OpType::F64 ? 8 : 4;
-  return ((2 * (size_t)ob * (s.K | 1) * csz + 15) & ~(size_t)15) + (((size_t)ob * (s.p | 1) + 3) & ~(size_t)3) * 4 +
-         (size_t)ob * ((kc * s.d) | 1) * 4;
+  return (size_t)2 * s.K * kBs * csz + ((size_t)s.p + (size_t)kc * s.d) * kBs * 4;
 }
 
 void build_blocking(const Shape &s, OpType t, int *ob, int *kc) {
-  *ob = 64;
+  *ob = kBob;
   *kc = std::max(1, s.K - 1);
-  while (*kc > 1 && build_smem_bytes(s, t, *ob, *kc) > 160 * 1024) *kc = (*kc + 1) / 2;
-  while (*ob > 16 && build_smem_bytes(s, t, *ob, *kc) > 160 * 1024) *ob /= 2;
+  while (*kc > 1 && build_smem_bytes(s, t, *ob, *kc) > 100 * 1024) *kc = (*kc + 1) / 2;
 }
 
 cudaError_t launch_build_operands(const Shape &s, OpType t, const float *X, const float *Y, const void *P, void *At,
@@ -580,15 +896,16 @@ int64_t zblocks_outputs(const Shape &s) {
   return (int64_t)s.p * s.K * s.f + (int64_t)s.K * s.d * s.f + (int64_t)s.f * s.f;
 }
 
-size_t zblocks_smem(const Shape &s, int rows, bool fp64) {
-  const size_t tsz = fp64 ? 8 : 4;
-  return (size_t)rows * (2 * (size_t)s.K * s.f * tsz + ((size_t)s.p + (size_t)s.K * s.d) * 4);
-}
+int zblocks_parts(const Shape &s, bool fp64) { return make_zplan(s.K, s.p, s.d, s.f, fp64 ? 8 : 4).parts(); }
 
-int zblocks_rows(const Shape &s, bool fp64) {
-  int rows = 32;
-  while (rows > 1 && zblocks_smem(s, rows, fp64) > 110 * 1024) rows /= 2;
-  return rows;
+size_t zblocks_smem(const Shape &s, bool fp64) {
+  const size_t tsz = fp64 ? 8 : 4;
+  const ZPlan z = make_zplan(s.K, s.p, s.d, s.f, (int)tsz);
+  const size_t x = (size_t)2 * kZxRows * kZxStride * (4 + tsz);
+  const size_t y = z.kspan ? (((size_t)z.ry * z.kspan * s.d * 4 + 15) & ~(size_t)15) + (size_t)z.ry * z.kspan * s.f * tsz
+                           : 0;
+  const size_t a = (size_t)2 * z.ra * s.K * z.fs * tsz + (size_t)kZThreads * 16 * tsz;
+  return std::max(x, std::max(y, a));
 }
 
 cudaError_t launch_grouped_syrk_f64(const GroupProblem *probs, const SyrkUnit *units, int nunits, const int *active,
@@ -604,13 +921,12 @@ cudaError_t launch_zblocks(const Shape &s, bool fp64, const float *X, const floa
                            const void *zbar, int nsplit, void *out, cudaStream_t st) {
   ZDims D;
   D.N = s.N; D.K = s.K; D.p = s.p; D.d = s.d; D.f = s.f;
-  D.rows = zblocks_rows(s, fp64);
   D.nsplit = nsplit;
   D.nzt = zblocks_outputs(s);
-  const size_t smem = zblocks_smem(s, D.rows, fp64);
-  if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  const int chunks = (int)((D.nzt + (int64_t)kZThreads * kZSlots - 1) / ((int64_t)kZThreads * kZSlots));
-  dim3 grid(nsplit, chunks);
+  D.zp = make_zplan(s.K, s.p, s.d, s.f, fp64 ? 8 : 4);
+  const size_t smem = zblocks_smem(s, fp64);
+  if (smem > 220 * 1024) return cudaErrorInvalidValue;
+  dim3 grid(D.zp.parts(), nsplit);  // the parts of one split are dispatched together
   cudaError_t e;
   if (fp64) {
     if ((e = cudaFuncSetAttribute(zblocks_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))

@@ -112,7 +112,7 @@ struct GroupProblem {
   void *P, *zbar;                // [N][K], [N][f] (float64 in FP64 mode, else float32)
   void *At, *Ad;                 // Hessian operands [mc_pad][ldn]
   int64_t ldn, mc_pad;
-  int nt1d, zsplit, zrows;
+  int nt1d, zsplit;
   int build_ob, build_kc;        // operand-builder blocking
   int64_t main_off, band_off, z_off;  // offsets of this problem's contraction partials (elements)
   int *band_of;                  // [nt1d][nt1d]
@@ -146,8 +146,8 @@ cudaError_t launch_grouped_assemble(bool fp64, const GroupProblem *probs, const 
                                     cudaStream_t st);
 size_t build_smem_bytes(const Shape &s, OpType t, int ob, int kc);
 void build_blocking(const Shape &s, OpType t, int *ob, int *kc);
-int zblocks_rows(const Shape &s, bool fp64);
-size_t zblocks_smem(const Shape &s, int rows, bool fp64);
+int zblocks_parts(const Shape &s, bool fp64);  // CTAs per observation split
+size_t zblocks_smem(const Shape &s, bool fp64);
 constexpr int kAssembleCols = 8;  // columns per grouped-assembly item
 
 // Grouped float64 contraction (FP64 mode): one CTA per unit, map 0 = At, 1 = Ad,
@@ -236,21 +236,26 @@ cudaError_t launch_assemble(const Shape &s, const AssembleIO &io, int nmain, dou
 // Mirror the lower triangle of F into a full symmetric matrix H = -F (column-major).
 cudaError_t launch_export_hessian(int64_t n, const double *F, double *H, cudaStream_t st);
 
-// Blocked FP64 Cholesky of F (lower, column-major, ld = n) in place (dinv[j] =
-// 1/L_jj), then solve F x = b.  status |= 4 when a pivot is not positive or
-// not finite.
+// Blocked Cholesky of F (lower, column-major, ld = n) in place by one
+// cooperative kernel, dinv[j] = 1/L_jj; work: chol_work_bytes(n) bytes.
+// status |= 4 when a pivot is not positive or not finite; *err != 0 when a
+// grid barrier wait ran out (the kernel then returns early).
+size_t chol_work_bytes(int64_t n);
 int cholesky_launches(int64_t n);
-cudaError_t launch_cholesky(int64_t n, double *F, double *dinv, int *status, cudaStream_t st);
+cudaError_t launch_cholesky(int64_t n, double *F, double *dinv, void *work, int *status, int *err, cudaStream_t st);
+// Solve L L^T x = b with the factor above (FP64; skipped when status & 4).
 cudaError_t launch_cholesky_solve(int64_t n, const double *L, const double *dinv, const double *b, double *x,
                                   const int *status, cudaStream_t st, int *launches);
-// Mixed solve: float32 factor of F (F kept intact, both triangles) and float64
-// iterative refinement of F delta = g.  status |= 8 when the float32 factor
-// fails, 16 when the refinement does not converge (use the FP64 path then).
-// rwork: mixed_solve_rwork_doubles(n); fwork: n floats; ref: 4 doubles.
-size_t mixed_solve_rwork_doubles(int64_t n);
-cudaError_t launch_mixed_solve(int64_t n, const double *F, float *F32, float *dinv32, const double *g, double *delta,
-                               double *rwork, float *fwork, double *ref, int *status, int iters, cudaStream_t st,
-                               int *launches);
+// Mixed solve: float32 factor and inverse of the factor (F kept intact, both
+// triangles; F32: n*n floats of scratch) and float64 iterative refinement of
+// F delta = g.  status |= 8 when the float32 factor fails, 16 when the
+// refinement does not converge (use the FP64 path then).  work:
+// mixed_solve_bytes(n); mixed_solve_ref(work, n) holds 4 doubles of
+// refinement state ([2] = refinement steps taken), zeroed by the caller.
+size_t mixed_solve_bytes(int64_t n);
+double *mixed_solve_ref(void *work, int64_t n);
+cudaError_t launch_mixed_solve(int64_t n, const double *F, float *F32, const double *g, double *delta, void *work,
+                               int *status, int *err, int iters, cudaStream_t st, int *launches);
 
 // Small FP64 vector kernels.
 cudaError_t launch_axpy_theta(int64_t n, double *theta, const double *delta, const double *tscale, double *scal_out,
