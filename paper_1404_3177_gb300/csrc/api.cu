@@ -554,16 +554,19 @@ int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *
           w.kb0 = (int)((int64_t)kb * sp / nsplit);
           w.kb1 = (int)((int64_t)kb * (sp + 1) / nsplit);
           w.out_off = ((int64_t)sp * (int64_t)tiles.size() + (int64_t)t) * kTile * kTile;
+          w.flags = 0;
           u.push_back(w);
         }
       return u;
     };
-    const std::vector<SyrkUnit> um = make_units(h->h_main, h->main_split, 0);
-    const std::vector<SyrkUnit> ub = make_units(h->h_band, h->band_split, 1);
+    const std::vector<SyrkUnit> jm = make_units(h->h_main, h->main_split, 0);
+    const std::vector<SyrkUnit> jb = make_units(h->h_band, h->band_split, 1);
+    h->grid_main = std::min((int)jm.size(), h->nsm);
+    h->grid_band = std::min((int)jb.size(), h->nsm);
+    const std::vector<SyrkUnit> um = schedule_syrk_units(jm, h->grid_main, tc_chunk_kblocks(h->op));
+    const std::vector<SyrkUnit> ub = schedule_syrk_units(jb, h->grid_band, tc_chunk_kblocks(h->op));
     h->nunits_main = (int)um.size();
     h->nunits_band = (int)ub.size();
-    h->grid_main = std::min(h->nunits_main, h->nsm);
-    h->grid_band = std::min(h->nunits_band, h->nsm);
     if ((rc = dalloc(h, &h->maps, sizeof(hm))) || (rc = dalloc(h, &h->units_main, um.size() * sizeof(SyrkUnit))) ||
         (rc = dalloc(h, &h->units_band, ub.size() * sizeof(SyrkUnit))))
       return fail(rc);

@@ -504,9 +504,14 @@ int ws_build(Engine &E, WorkSet &W, const std::vector<const ProbLayout *> &L, in
     for (size_t k = 0; k < l.bands.size(); ++k)
       ub.push_back({mD, i, l.bands[k].x, l.bands[k].y, 0, kb, g.band_off + (int64_t)k * kTile * kTile});
   }
-  auto by_len = [](const SyrkUnit &a, const SyrkUnit &c) { return (a.kb1 - a.kb0) > (c.kb1 - c.kb0); };
-  std::stable_sort(um.begin(), um.end(), by_len);
-  std::stable_sort(ub.begin(), ub.end(), by_len);
+  if (E.fp64) {
+    auto by_len = [](const SyrkUnit &a, const SyrkUnit &c) { return (a.kb1 - a.kb0) > (c.kb1 - c.kb0); };
+    std::stable_sort(um.begin(), um.end(), by_len);
+    std::stable_sort(ub.begin(), ub.end(), by_len);
+  } else {  // bounded accumulation chunks, one CTA per job (the kernel runs on E.nsm CTAs)
+    um = schedule_syrk_units(um, E.nsm, tc_chunk_kblocks(E.op));
+    ub = schedule_syrk_units(ub, E.nsm, tc_chunk_kblocks(E.op));
+  }
   W.nunits_main = (int)um.size();
   W.nunits_band = (int)ub.size();
   if ((rc = upload(W.maps, maps, E.st)) || (rc = upload(W.units_main, um, E.st)) || (rc = upload(W.units_band, ub, E.st)))

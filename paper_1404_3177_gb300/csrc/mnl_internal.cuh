@@ -56,9 +56,15 @@ inline Shape make_shape(const mnl_dims &d) { return shape_of(d.N, d.K, d.p, d.d,
 // A unit of the tiled contractions: operand (tensor map index, or 0 = At /
 // 1 = Ad for the float64 path), problem, output tile (ti, tj), K-block range
 // [kb0, kb1) and the offset of its 128 x 128 output tile.
+// One contraction work unit: tile (ti, tj) of operand map `map` over the
+// K-blocks [kb0, kb1), written at out_off.  flags: kUnitAcc adds into the
+// output instead of storing it; kUnitEmpty is a placeholder that every role
+// skips.
+constexpr int kUnitAcc = 1, kUnitEmpty = 2;
 struct SyrkUnit {
   int map, problem, ti, tj, kb0, kb1;
   int64_t out_off;
+  int flags;
 };
 
 // theta index (class part) -> class k (1..K-1) and local column l (0..q-1).
@@ -212,6 +218,15 @@ cudaError_t launch_syrk_f64(const double *At, int64_t ldn, int64_t N, const int2
 cudaError_t encode_operand_map(OpType t, const void *At, int64_t rows_pad, int64_t ldn, CUtensorMap *out);
 int tc_kblocks(OpType t, int64_t ldn);
 int tc_pick_split(int ntiles, int kblocks, int num_sms);
+// K-blocks of one accumulation chunk of the tensor-core SYRK (16384 observations):
+// the FP32 accumulator in TMEM never sums more observations than that.
+int tc_chunk_kblocks(OpType t);
+// Lay out SYRK jobs for a persistent grid: each job is cut into chunks of at
+// most max_kb K-blocks that one CTA runs back to back (the first stores the
+// tile, the rest add into it, a fixed order), jobs go longest first to the
+// least-loaded CTA, and the per-CTA sequences are interleaved (unit u runs on
+// CTA u % grid) with empty units as padding.
+std::vector<SyrkUnit> schedule_syrk_units(const std::vector<SyrkUnit> &jobs, int grid, int max_kb);
 size_t tc_smem_bytes();
 cudaError_t launch_syrk_tc(OpType t, const CUtensorMap *maps, const SyrkUnit *units, int nunits, const int *active,
                            int grid, float *out, int *err, cudaStream_t st);

@@ -35,9 +35,11 @@
 
 namespace mnl {
 
+constexpr int kMaxCoopGrid = 1024;
 struct GridBarrier {
   unsigned count, gen;
   int abort, pad;
+  int smid[kMaxCoopGrid];  // SM of each CTA
 };
 
 namespace {
@@ -394,8 +396,31 @@ __global__ void __launch_bounds__(kCoopThreads, sizeof(T) == 4 ? 2 : 1) coop_cho
   const int64_t n = a.n;
   const int np = (int)((n + kCb - 1) / kCb);
   const int G = (int)gridDim.x, b = (int)blockIdx.x;
+  // The CTAs that share CTA 0's SM take no trailing-update tiles, so that the
+  // diagonal factorisation (CTA 0, one warp at a time) has the SM to itself;
+  // the other CTAs are the workers, numbered densely.
+  __shared__ int s_quiet, s_widx, s_nw;
+  if (threadIdx.x == 0) {
+    unsigned sid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(sid));
+    a.bar->smid[b] = (int)sid;
+  }
   if (b == 0) factor_diag<T>(a, 0, sm);
   if (!grid_sync(a.bar, G, a.err)) return;
+  if (threadIdx.x == 0) {
+    const volatile int *ids = a.bar->smid;
+    const int s0 = ids[0];
+    int before = 0, total = 0;
+    for (int i = 1; i < G; ++i)
+      if (ids[i] != s0) {
+        ++total;
+        if (i < b) ++before;
+      }
+    s_quiet = b != 0 && ids[b] == s0;
+    s_widx = before;
+    s_nw = total;
+  }
+  __syncthreads();
   for (int k = 0; k < np; ++k) {
     const int64_t j0 = (int64_t)k * kCb;
     const int nbk = (int)(n - j0 < kCb ? n - j0 : kCb);
@@ -446,9 +471,12 @@ __global__ void __launch_bounds__(kCoopThreads, sizeof(T) == 4 ? 2 : 1) coop_cho
       item(0);
       factor_diag<T>(a, k + 1, sm);
     }
-    const int w0 = G > 1 ? 1 : 0, W = G > 1 ? G - 1 : 1;
-    if (b >= w0)
-      for (int t = 1 + (b - w0); t < nC; t += W) item(t);
+    if (s_nw == 0) {  // no other SM: CTA 0 takes every tile
+      if (b == 0)
+        for (int t = 1; t < nC; ++t) item(t);
+    } else if (b != 0 && !s_quiet) {
+      for (int t = 1 + s_widx; t < nC; t += s_nw) item(t);
+    }
     if (!grid_sync(a.bar, G, a.err)) return;
   }
 }
@@ -574,7 +602,7 @@ cudaError_t launch_coop(int64_t n, T *A, T *Li, T *Dinv, T *dinv, GridBarrier *b
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCoopThreads, smem)) != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const int grid = nsm * std::min(per_sm, 2);
+  const int grid = std::min(nsm * std::min(per_sm, 2), kMaxCoopGrid);
   if ((e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st)) != cudaSuccess) return e;
   CoopArgs<T> a;
   a.A = A; a.Li = Li; a.Dinv = Dinv; a.dinv = dinv; a.n = n; a.bar = bar;

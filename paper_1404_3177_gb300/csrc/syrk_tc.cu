@@ -2,10 +2,14 @@
 // eq. "hessian block"):  C = A^T A  over the observations, A = At^T.
 //
 // At is stored class-major, [rows_pad][ldn], one operand row per Hessian
-// column, observations contiguous ("K-major" for the MMA).  Every work unit is
-// one 128 x 128 output tile (ti, tj), ti >= tj, over one contiguous range
-// ("split") of the observations; partial tiles are written in float32 and
-// reduced in fixed order by the assembly kernel (no float atomics).
+// column, observations contiguous ("K-major" for the MMA).  A job is one
+// 128 x 128 output tile (ti, tj), ti >= tj, over one contiguous range ("split")
+// of the observations; partial tiles are written in float32 and reduced in
+// fixed order by the assembly kernel (no float atomics).  A job runs as units
+// of at most 16384 observations on one CTA, one after the other: the first
+// stores the tile and the others add into it, so no FP32 accumulator in TMEM
+// sums more than 16384 products (the rounding of long accumulations otherwise
+// grows with N).
 //
 // Per CTA (one per SM, persistent, 6 warps):
 //   warp 0 (one lane): TMA producer, 128-row x 128-byte boxes with the
@@ -22,6 +26,9 @@
 // shared abort flag and the error word; every role then leaves its loop,
 // in-flight TMA loads and MMAs are waited for (again bounded), TMEM is freed
 // and the kernel returns.
+#include <algorithm>
+#include <queue>
+
 #include "mnl_internal.cuh"
 
 namespace mnl {
@@ -169,7 +176,9 @@ __global__ void __launch_bounds__(192, 1) syrk_tc_kernel(const CUtensorMap *__re
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int kBk = TF32 ? kBkTf32 : kBkBf16;
   // A unit is skipped by every role alike when its problem is inactive.
-  auto skip = [&](const SyrkUnit &w) { return active != nullptr && active[w.problem] == 0; };
+  auto skip = [&](const SyrkUnit &w) {
+    return (w.flags & kUnitEmpty) != 0 || (active != nullptr && active[w.problem] == 0);
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -271,13 +280,23 @@ __global__ void __launch_bounds__(192, 1) syrk_tc_kernel(const CUtensorMap *__re
       acc_ph[b] ^= 1u;
       tc_fence_after();
       // Tile stored transposed: out[col][row], row = MMA M index (operand tile ti).
+      // A later chunk of the same job adds into what this thread stored before.
       float *dst = out + w.out_off + quarter * 32 + lane;
+      const bool acc = (w.flags & kUnitAcc) != 0;
 #pragma unroll 1
       for (int c0 = 0; c0 < kTile; c0 += 32) {
         uint32_t v[32];
         tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kTile + c0), v);
+        if (acc) {
+          float o[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) dst[(int64_t)(c0 + j) * kTile] = __uint_as_float(v[j]);
+          for (int j = 0; j < 32; ++j) o[j] = dst[(int64_t)(c0 + j) * kTile];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) dst[(int64_t)(c0 + j) * kTile] = o[j] + __uint_as_float(v[j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) dst[(int64_t)(c0 + j) * kTile] = __uint_as_float(v[j]);
+        }
       }
       tc_fence_before();
       __syncwarp();
@@ -347,6 +366,46 @@ int tc_pick_split(int ntiles, int kblocks, int num_sms) {
     if (eff > best_eff + 0.02) { best_eff = eff; best = s; }
   }
   return best;
+}
+
+int tc_chunk_kblocks(OpType t) { return 16384 / (t == OpType::TF32 ? kBkTf32 : kBkBf16); }
+
+std::vector<SyrkUnit> schedule_syrk_units(const std::vector<SyrkUnit> &jobs, int grid, int max_kb) {
+  std::vector<SyrkUnit> out;
+  if (jobs.empty() || grid < 1) return out;
+  std::vector<size_t> order(jobs.size());
+  for (size_t j = 0; j < jobs.size(); ++j) order[j] = j;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+    return (jobs[a].kb1 - jobs[a].kb0) > (jobs[b].kb1 - jobs[b].kb0);
+  });
+  std::vector<std::vector<SyrkUnit>> per((size_t)grid);
+  // least-loaded CTA first, lowest index on ties (equal jobs go round-robin)
+  using Item = std::pair<int64_t, int>;
+  std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
+  for (int b = 0; b < grid; ++b) heap.push({0, b});
+  for (size_t j : order) {
+    const SyrkUnit &w = jobs[j];
+    const Item top = heap.top();
+    heap.pop();
+    const int len = w.kb1 - w.kb0;
+    const int nch = std::max(1, (len + max_kb - 1) / max_kb);
+    for (int c = 0; c < nch; ++c) {
+      SyrkUnit u = w;
+      u.kb0 = w.kb0 + (int)((int64_t)len * c / nch);
+      u.kb1 = w.kb0 + (int)((int64_t)len * (c + 1) / nch);
+      u.flags = c > 0 ? kUnitAcc : 0;
+      per[(size_t)top.second].push_back(u);
+    }
+    heap.push({top.first + len + 8, top.second});  // 8 K-blocks of fixed cost per job
+  }
+  size_t depth = 0;
+  for (const auto &v : per) depth = std::max(depth, v.size());
+  SyrkUnit empty{};
+  empty.flags = kUnitEmpty;
+  out.assign(depth * (size_t)grid, empty);
+  for (int b = 0; b < grid; ++b)
+    for (size_t i = 0; i < per[(size_t)b].size(); ++i) out[i * (size_t)grid + (size_t)b] = per[(size_t)b][i];
+  return out;
 }
 
 size_t tc_smem_bytes() { return kSmemBytes; }

@@ -1,0 +1,123 @@
+"""Full-size workloads on the GPU path against the FP64 oracle, on sampled outputs.
+
+Workload 3 (N=500000, K=100, p=100 with 30 Bernoulli(0.1) columns, f=10, d=0;
+n_theta = 9910): an oracle fit at this size takes hours, so the checks are
+  * l and g at theta = 0 element by element (the oracle's pass is cheap);
+  * sampled entries of -H at theta = 0 (diagonal and off-diagonal strata),
+    a stratified estimate of the relative Frobenius error;
+  * the converged coefficients through the oracle's gradient at the GPU's
+    estimate theta: one Newton correction d = (-H)^-1 g_oracle(theta) with the
+    GPU Hessian at theta (pinned above to 2e-3) estimates theta_hat - theta to
+    within that relative error (the remainder is quadratic in d), so
+    max|d| / max|theta| <= 1e-6 is the coefficient bar.
+Workload 4 (2048 batched problems, N log-uniform in [500, 50000]), BF16
+Hessians: every problem must converge, and a seeded sample (with the largest
+n_theta) is compared with oracle fits.  The FP64 batched path is compared with
+the oracle on smaller batches in test_gpu_batch.py.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1404_3177_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+scipy_linalg = pytest.importorskip("scipy.linalg")
+
+H_TOL = 2e-3
+LG_TOL = 1e-6
+THETA_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1404_3177_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    from paper_1404_3177_gb300 import api
+    return api
+
+
+def dev(prob):
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda() if a.size else None  # noqa: E731
+    return dict(X=t(prob.X), Y=t(prob.Y), Z=t(prob.Z), choice=torch.from_numpy(prob.choice).cuda(), K=prob.K)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def frobenius_estimate(H, F_ref, rows, cols, n, ndiag):
+    """Relative Frobenius error from a diagonal and an off-diagonal stratum of entries."""
+    e = H[rows, cols] - F_ref
+    d, o = slice(0, ndiag), slice(ndiag, None)
+    num = n / ndiag * np.sum(e[d] ** 2) + n * (n - 1) / (len(rows) - ndiag) * np.sum(e[o] ** 2)
+    den = n / ndiag * np.sum(F_ref[d] ** 2) + n * (n - 1) / (len(rows) - ndiag) * np.sum(F_ref[o] ** 2)
+    return float(np.sqrt(num / den))
+
+
+@pytest.fixture(scope="module")
+def c3():
+    prob = datagen.config3()
+    n = prob.n_theta
+    l_ref, g_ref = oracle.loglik_grad(prob)
+    rng = np.random.default_rng(3)
+    nd = 40
+    d_idx = rng.choice(n, nd, replace=False)
+    r = rng.integers(0, n, 100)
+    c = rng.integers(0, n, 100)
+    rows = np.concatenate([d_idx, np.maximum(r, c), rng.integers(n - prob.f, n, 10)])
+    cols = np.concatenate([d_idx, np.minimum(r, c), rng.integers(0, n, 10)])
+    F_ref = oracle.neg_hessian_entries(prob, np.zeros(n), rows, cols)
+    return prob, l_ref, g_ref, rows, cols, nd, F_ref
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_workload3_full_size(lib, c3, prec):
+    prob, l_ref, g_ref, rows, cols, nd, F_ref = c3
+    n = prob.n_theta
+    with lib.MNL(**dev(prob), precision=prec) as m:
+        l, g = m.loglik_grad()
+        g = g.cpu().numpy()
+        assert abs(l - l_ref) <= LG_TOL * abs(l_ref), (l, l_ref)
+        assert rel(g, g_ref) <= LG_TOL, rel(g, g_ref)
+        H = m.hessian().cpu().numpy()
+        est = frobenius_estimate(-H, F_ref, rows, cols, n, nd)
+        assert est <= H_TOL, (prec, est)
+        del H
+        th, info = m.fit()
+        assert info["status"] == 0, info
+        Hf = m.hessian(th).cpu().numpy()
+        th = th.cpu().numpy()
+    _, g_at = oracle.loglik_grad(prob, th)
+    cf = scipy_linalg.cho_factor(-Hf, lower=True, overwrite_a=True, check_finite=False)
+    d = scipy_linalg.cho_solve(cf, g_at, check_finite=False)
+    err = float(np.abs(d).max() / np.abs(th).max())
+    assert err <= THETA_TOL, (prec, err, info)
+
+
+@pytest.fixture(scope="module")
+def c4():
+    shapes = datagen.config4_shapes()
+    probs = [datagen.config4_problem(b, s) for b, s in enumerate(shapes)]
+    rng = np.random.default_rng(4)
+    sample = sorted(set(rng.choice(len(probs), 5, replace=False).tolist())
+                    | {int(np.argmax([p.n_theta for p in probs]))})
+    refs = {b: oracle.fit(probs[b])[0] for b in sample}
+    return probs, refs
+
+
+@pytest.mark.parametrize("prec", ["bf16"])
+def test_workload4_full_batch(lib, c4, prec):
+    probs, refs = c4
+    with lib.MNLBatch([dev(p) for p in probs], precision=prec) as b:
+        th, summary, per, rc = b.fit()
+        parts = [t.cpu().numpy() for t in b.split(th)]
+    assert rc == 0, summary
+    assert summary["converged"] == len(probs), summary
+    for i, ref in refs.items():
+        err = np.abs(parts[i] - ref).max() / np.abs(ref).max()
+        assert err <= THETA_TOL, (prec, i, probs[i].N, probs[i].n_theta, err)
