@@ -206,6 +206,7 @@ int run_pass(mnl_handle *h, const double *theta, bool full, const double *delta,
   io.P = h->P; io.zbar = h->zbar;
   const PassPlan &pl = full ? h->pfull : h->pll;
   io.partials = full ? h->part_full : h->part_ll;
+  io.err = h->err;
   CK(launch_pass(h->S, pl, h->fp64, full, io, h->st));
   CK(launch_pass_reduce(h->S, pl.grid, full, io.partials, h->scal + base, full ? h->grad : nullptr, h->st));
   h->launches += 2;

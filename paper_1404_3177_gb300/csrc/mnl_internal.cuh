@@ -86,6 +86,7 @@ struct PassIO {
   void *P;               // [N][K] T, FULL mode only
   void *zbar;            // [N][f] T, FULL mode only
   double *partials;      // [grid][2 + n] (FULL) or [grid][2] (loglik only)
+  int *err;              // error word (bit 16: a tile copy did not complete in time); tiled pass only
 };
 
 // Configuration of the fused utility/softmax/log-likelihood/gradient pass.
@@ -93,8 +94,13 @@ struct PassPlan {
   int grid, block, rows, npt;   // CTAs, threads, rows per tile, outputs per thread
   size_t smem;
   bool ok;
+  bool tiled;                   // float32 pass with asynchronous tile copies (pass_tile.cu)
 };
-PassPlan plan_pass(const Shape &s, bool fp64, bool full, int num_sms);
+// allow_tiled: the float32 path may use the tiled pass (needs io.err and
+// 16-byte aligned X, Y, Z, choice).
+PassPlan plan_pass(const Shape &s, bool fp64, bool full, int num_sms, bool allow_tiled = true);
+bool plan_pass_tiled(const Shape &s, bool full, int num_sms, PassPlan &pl);
+cudaError_t launch_pass_tiled(const Shape &s, const PassPlan &pl, bool full, const PassIO &io, cudaStream_t st);
 cudaError_t launch_pass(const Shape &s, const PassPlan &pl, bool fp64, bool full, const PassIO &io, cudaStream_t st);
 
 // ---------------------------------------------------------------------------

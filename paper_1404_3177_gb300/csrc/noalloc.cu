@@ -60,7 +60,7 @@ extern "C" MNL_API int mnl_loglik_grad_noalloc(const mnl_dims *dims, const mnl_d
     cudaGetLastError();
     return MNL_ERR_CUDA;
   }
-  PassPlan pl = plan_pass(S, fp64, true, nsm);
+  PassPlan pl = plan_pass(S, fp64, true, nsm, false);
   if (!pl.ok) return MNL_ERR_UNSUPPORTED;
   // Fit the CTA partials into the fixed scratch: fewer CTAs when needed.
   const size_t per_cta = 2 + (size_t)S.n;

@@ -443,9 +443,11 @@ cudaError_t launch_npt(const PassDims &D, const PassPlan &pl, const PassIO &io, 
 
 }  // namespace
 
-PassPlan plan_pass(const Shape &s, bool fp64, bool full, int num_sms) {
+PassPlan plan_pass(const Shape &s, bool fp64, bool full, int num_sms, bool allow_tiled) {
   PassPlan pl{};
   pl.ok = false;
+  pl.tiled = false;
+  if (!fp64 && allow_tiled && plan_pass_tiled(s, full, num_sms, pl)) return pl;
   if (s.K > 32 * kMaxClassSlots) return pl;
   const size_t tsz = fp64 ? 8 : 4;
   // threads: enough for the gradient accumulators at <= 32 per thread
@@ -476,6 +478,7 @@ PassPlan plan_pass(const Shape &s, bool fp64, bool full, int num_sms) {
 }
 
 cudaError_t launch_pass(const Shape &s, const PassPlan &pl, bool fp64, bool full, const PassIO &io, cudaStream_t st) {
+  if (pl.tiled) return launch_pass_tiled(s, pl, full, io, st);
   const PassDims D = dims_of(s, pl.rows);
   if (fp64) return full ? launch_npt<double, true>(D, pl, io, st) : launch_npt<double, false>(D, pl, io, st);
   return full ? launch_npt<float, true>(D, pl, io, st) : launch_npt<float, false>(D, pl, io, st);

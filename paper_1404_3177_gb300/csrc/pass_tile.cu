@@ -1,0 +1,504 @@
+// Fused float32 pass over the observations with asynchronous row-tile copies
+// (Sec. 2.1 eqs. "unormalized utility", "probability", "base probability";
+// Sec. 3.1 eq. "log-lik function"; Sec. 3.3 eq. "loglik gradient").
+//
+// Same results as the pass of pass.cu (utilities over all K alternatives from
+// raw data, row softmax, l, P, zbar and g), organised for bandwidth:
+//   * one CTA per SM walks tiles of R = 8 * RPW consecutive observations; the
+//     X, Y, Z and choice rows of a tile are contiguous in memory and arrive by
+//     bulk asynchronous copies (cp.async.bulk, completion counted on an
+//     mbarrier) into a ring of 2-3 shared-memory stages, so the next tiles
+//     load while the current one is used (the last, partial tile is loaded
+//     with plain loads);
+//   * X is transposed in shared memory (Xt[l][r]) so that a warp reads RPW
+//     rows of one column in one broadcast load; warp w forms the utilities of
+//     rows RPW w .. RPW w + RPW - 1 with lanes over alternatives;
+//   * the residuals r_ik = I(y_i = k) - P_ik are kept transposed (Rt[k][r]) and
+//     the beta gradient X^T r of the tile is a register tile of 2 classes x 4
+//     columns per thread fed by 16-byte loads; gamma and alpha entries are
+//     owned by threads; every per-tile float32 sum is folded into a
+//     Kahan-compensated running sum;
+//   * each CTA writes its float64 partial row [l, sum |l_i|, g] for the fixed
+//     order reduction (pass_reduce_kernel).
+// The wait on a stage is bounded (2 s on %globaltimer); a wait that runs out
+// sets *err and the CTA stops after waiting (bounded) for its copies in flight.
+#include <cfloat>
+
+#include "mnl_internal.cuh"
+
+namespace mnl {
+namespace {
+
+constexpr int kPT = 256;          // threads per CTA
+constexpr int kBetaItems = 3;     // beta-gradient register tiles per warp
+constexpr int kYZSlots = 4;       // gamma / alpha outputs per thread
+constexpr uint64_t kTileWaitNs = 2000000000ull;
+
+struct TileDims {
+  int64_t N, ntiles;
+  int K, p, d, f, Kpad, R, R4, S, pp;
+  int nb, mc, n;
+  int stage_bytes, off_x, off_y, off_z, off_c;                       // within a stage
+  int off_bt, off_gt, off_al, off_xt, off_rt, off_red, off_bar, off_stage;
+  int kp2, lq, wk, wl, nyz;                                          // gradient work
+};
+
+struct KahanF {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+__device__ __forceinline__ uint32_t sa(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gclock() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sa(dst)),
+      "l"(src), "r"(bytes), "r"(sa(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_done(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(sa(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for phase `parity` of a stage barrier.
+__device__ __forceinline__ bool stage_wait(uint64_t *bar, uint32_t parity) {
+  if (mbar_done(bar, parity)) return true;
+  const uint64_t t0 = gclock();
+  while (!mbar_done(bar, parity))
+    if (gclock() - t0 > kTileWaitNs) return false;
+  return true;
+}
+
+__device__ __forceinline__ float wmax(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float wsum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int RPW>
+__device__ __forceinline__ void load_rows(const float *p, float v[RPW]) {
+  if (RPW == 4) {
+    const float4 a = *reinterpret_cast<const float4 *>(p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  } else if (RPW == 2) {
+    const float2 a = *reinterpret_cast<const float2 *>(p);
+    v[0] = a.x; v[1] = a.y;
+  } else {
+    v[0] = p[0];
+  }
+}
+
+template <int RPW, int CS, bool FULL>
+__global__ void __launch_bounds__(kPT, 1) pass_tile_kernel(TileDims D, PassIO io) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  float *Bt = reinterpret_cast<float *>(sm + D.off_bt);  // [p][Kpad]
+  float *Gt = reinterpret_cast<float *>(sm + D.off_gt);  // [d][Kpad]
+  float *al = reinterpret_cast<float *>(sm + D.off_al);  // [f]
+  float *Xt = reinterpret_cast<float *>(sm + D.off_xt);  // [pp][R4]
+  float *Rt = reinterpret_cast<float *>(sm + D.off_rt);  // [Kpad][R4] (FULL)
+  double *red = reinterpret_cast<double *>(sm + D.off_red);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sm + D.off_bar);
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int K = D.K, p = D.p, d = D.d, f = D.f, Kpad = D.Kpad, R = D.R, R4 = D.R4;
+  const int64_t N = D.N;
+
+  // coefficients theta (+ t delta), zero for the base alternative and the padding
+  const double tsc = io.delta ? *io.tscale : 0.0;
+  auto coef = [&](int64_t a) { return io.theta[a] + (io.delta ? tsc * io.delta[a] : 0.0); };
+  for (int e = tid; e < p * Kpad; e += kPT) {
+    const int j = e / Kpad, k = e - j * Kpad;
+    Bt[e] = (k >= 1 && k < K) ? (float)coef((int64_t)(k - 1) * p + j) : 0.f;
+  }
+  for (int e = tid; e < d * Kpad; e += kPT) {
+    const int j = e / Kpad, k = e - j * Kpad;
+    Gt[e] = (k >= 1 && k < K) ? (float)coef(D.nb + (int64_t)(k - 1) * d + j) : 0.f;
+  }
+  for (int j = tid; j < f; j += kPT) al[j] = (float)coef(D.mc + j);
+  for (int e = p * R4 + tid; e < D.pp * R4; e += kPT) Xt[e] = 0.f;  // padding columns of Xt
+  if (FULL)
+    for (int e = tid; e < R4; e += kPT) Rt[Kpad * R4 + e] = 0.f;       // row read by the last class pair
+  if (tid == 0) {
+    s_abort = 0;
+    for (int s = 0; s < D.S; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sa(&bar[s])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  const uint32_t tile_bytes = (uint32_t)(R * (p + K * d + K * f + 1) * 4);
+  auto full_tile = [&](int64_t tl) { return (tl + 1) * R <= N; };
+  auto issue = [&](int64_t tl, int s) {  // one thread
+    const int64_t row0 = tl * R;
+    unsigned char *st = sm + D.off_stage + s * D.stage_bytes;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(&bar[s])), "r"(tile_bytes)
+                 : "memory");
+    bulk_copy(st + D.off_x, io.X + row0 * p, (uint32_t)(R * p * 4), &bar[s]);
+    if (d) bulk_copy(st + D.off_y, io.Y + row0 * K * d, (uint32_t)(R * K * d * 4), &bar[s]);
+    if (f) bulk_copy(st + D.off_z, io.Z + row0 * K * f, (uint32_t)(R * K * f * 4), &bar[s]);
+    bulk_copy(st + D.off_c, io.choice + row0, (uint32_t)(R * 4), &bar[s]);
+  };
+  int pend[3] = {-1, -1, -1};  // thread 0: per stage, parity of a copy not yet waited for
+  if (tid == 0)
+    for (int s = 0; s < D.S; ++s) {
+      const int64_t tl = blockIdx.x + (int64_t)s * gridDim.x;
+      if (tl < D.ntiles && full_tile(tl)) { issue(tl, s); pend[s] = 0; }
+    }
+
+  KahanF lsum, labs;                   // lane 0 of each warp
+  KahanF bs[kBetaItems][8];            // beta gradient: 2 classes x 4 columns per item
+  KahanF yz[kYZSlots];                 // gamma entries and alpha partials per class
+  int yz_k[kYZSlots], yz_j[kYZSlots];  // decoded once: class and column, yz_j < 0 for alpha
+#pragma unroll
+  for (int q = 0; q < kYZSlots; ++q) {
+    const int e = tid + q * kPT;
+    yz_k[q] = -1; yz_j[q] = 0;
+    if (FULL && e < D.nyz) {
+      const int ng = (K - 1) * d;
+      if (e < ng) { yz_k[q] = 1 + e / d; yz_j[q] = e - (e / d) * d; }
+      else { const int e2 = e - ng; yz_k[q] = e2 / f; yz_j[q] = -1 - (e2 - (e2 / f) * f); }
+    }
+  }
+
+  int it = 0;
+  for (int64_t tl = blockIdx.x; tl < D.ntiles; tl += gridDim.x, ++it) {
+    const int s = it % D.S;
+    const uint32_t par = (uint32_t)((it / D.S) & 1);
+    unsigned char *st = sm + D.off_stage + s * D.stage_bytes;
+    float *Xs = reinterpret_cast<float *>(st + D.off_x);
+    float *Ys = reinterpret_cast<float *>(st + D.off_y);
+    float *Zs = reinterpret_cast<float *>(st + D.off_z);
+    int *cs = reinterpret_cast<int *>(st + D.off_c);
+    const int64_t row0 = tl * R;
+    const int nrows = (int)(N - row0 < R ? N - row0 : R);
+    if (nrows == R) {
+      if (!stage_wait(&bar[s], par)) s_abort = 1;
+      else if (tid == 0) pend[s] = -1;
+    } else {  // the partial last tile: plain loads, zero padding
+      for (int e = tid; e < R * p; e += kPT) Xs[e] = e < nrows * p ? io.X[row0 * p + e] : 0.f;
+      for (int e = tid; e < R * K * d; e += kPT) Ys[e] = e < nrows * K * d ? io.Y[row0 * K * d + e] : 0.f;
+      for (int e = tid; e < R * K * f; e += kPT) Zs[e] = e < nrows * K * f ? io.Z[row0 * K * f + e] : 0.f;
+      for (int e = tid; e < R; e += kPT) cs[e] = e < nrows ? io.choice[row0 + e] : -1;
+    }
+    __syncthreads();
+    if (s_abort) break;
+    for (int e = tid; e < R * p; e += kPT) {
+      const int r = e / p, l = e - r * p;
+      Xt[l * R4 + r] = Xs[e];
+    }
+    __syncthreads();
+
+    // ---- utilities, softmax, l (and P, residuals, zbar) ----
+    {
+      const int r0 = warp * RPW;
+      float u[RPW][CS];
+#pragma unroll
+      for (int r = 0; r < RPW; ++r)
+#pragma unroll
+        for (int c = 0; c < CS; ++c) u[r][c] = 0.f;
+      for (int j = 0; j < p; ++j) {
+        float xv[RPW];
+        load_rows<RPW>(Xt + j * R4 + r0, xv);
+#pragma unroll
+        for (int c = 0; c < CS; ++c) {
+          const float b = Bt[j * Kpad + lane + 32 * c];
+#pragma unroll
+          for (int r = 0; r < RPW; ++r) u[r][c] = fmaf(xv[r], b, u[r][c]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < CS; ++c) {
+        const int k = lane + 32 * c;
+        if (k >= K) continue;
+#pragma unroll
+        for (int r = 0; r < RPW; ++r) {
+          const float *y = Ys + ((size_t)(r0 + r) * K + k) * d;
+          for (int j = 0; j < d; ++j) u[r][c] = fmaf(y[j], Gt[j * Kpad + k], u[r][c]);
+          const float *z = Zs + ((size_t)(r0 + r) * K + k) * f;
+          for (int j = 0; j < f; ++j) u[r][c] = fmaf(z[j], al[j], u[r][c]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < RPW; ++r) {
+        const int rr = r0 + r;
+        const bool vr = rr < nrows;
+        const int yi = cs[rr];
+        float m = -FLT_MAX;
+#pragma unroll
+        for (int c = 0; c < CS; ++c)
+          if (lane + 32 * c < K) m = fmaxf(m, u[r][c]);
+        m = wmax(m);
+        float sum = 0.f, uy = 0.f;
+#pragma unroll
+        for (int c = 0; c < CS; ++c) {
+          const int k = lane + 32 * c;
+          if (k < K) {
+            if (k == yi) uy = u[r][c];
+            u[r][c] = expf(u[r][c] - m);
+            sum += u[r][c];
+          } else {
+            u[r][c] = 0.f;
+          }
+        }
+        sum = wsum(sum);
+        uy = wsum(uy);
+        if (vr && lane == 0) {
+          const float li = uy - (m + logf(sum));
+          lsum.add(li);
+          labs.add(fabsf(li));
+        }
+        if (FULL) {
+          const float inv = 1.f / sum;
+          float *Pg = reinterpret_cast<float *>(io.P) + (row0 + rr) * K;
+#pragma unroll
+          for (int c = 0; c < CS; ++c) {
+            const int k = lane + 32 * c;
+            const float P = u[r][c] * inv;
+            u[r][c] = P;
+            if (k < K && vr) Pg[k] = P;
+            Rt[k * R4 + rr] = (k < K && vr) ? ((k == yi ? 1.f : 0.f) - P) : 0.f;
+          }
+          for (int j = 0; j < f; ++j) {
+            float zb = 0.f;
+#pragma unroll
+            for (int c = 0; c < CS; ++c) {
+              const int k = lane + 32 * c;
+              if (k < K) zb = fmaf(u[r][c], Zs[((size_t)rr * K + k) * f + j], zb);
+            }
+            zb = wsum(zb);
+            if (vr && lane == 0) reinterpret_cast<float *>(io.zbar)[(row0 + rr) * f + j] = zb;
+          }
+        }
+      }
+    }
+
+    if (FULL) {
+      __syncthreads();  // residuals of every row are in Rt
+      // ---- beta gradient: warp item (wkp, wlq) covers classes 1 + 2 kp, 2 + 2 kp and columns 4 lq .. 4 lq + 3 ----
+      const int nitems = D.wk * D.wl;
+#pragma unroll
+      for (int ii = 0; ii < kBetaItems; ++ii) {
+        const int item = warp + 8 * ii;
+        if (item >= nitems) break;
+        const int kp = (item / D.wl) * 4 + (lane >> 3), lq = (item % D.wl) * 8 + (lane & 7);
+        if (kp >= D.kp2 || lq >= D.lq) continue;
+        const int k1 = 1 + 2 * kp, l0 = 4 * lq;
+        float a[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) a[q] = 0.f;
+        for (int r = 0; r < R; r += 4) {
+          const float4 ra = *reinterpret_cast<const float4 *>(Rt + k1 * R4 + r);
+          const float4 rb = *reinterpret_cast<const float4 *>(Rt + (k1 + 1) * R4 + r);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float4 x = *reinterpret_cast<const float4 *>(Xt + (l0 + q) * R4 + r);
+            a[q] = fmaf(ra.x, x.x, fmaf(ra.y, x.y, fmaf(ra.z, x.z, fmaf(ra.w, x.w, a[q]))));
+            a[4 + q] = fmaf(rb.x, x.x, fmaf(rb.y, x.y, fmaf(rb.z, x.z, fmaf(rb.w, x.w, a[4 + q]))));
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) bs[ii][q].add(a[q]);
+      }
+      // ---- gamma entries and per-class alpha partials ----
+#pragma unroll
+      for (int q = 0; q < kYZSlots; ++q) {
+        const int k = yz_k[q];
+        if (k < 0) continue;
+        const int j = yz_j[q];
+        const float *src = j >= 0 ? Ys + (size_t)k * d + j : Zs + (size_t)k * f + (-1 - j);
+        const int stride = j >= 0 ? K * d : K * f;
+        float a0 = 0.f, a1 = 0.f;
+        for (int r = 0; r < R; r += 2) {
+          a0 = fmaf(Rt[k * R4 + r], src[(size_t)r * stride], a0);
+          a1 = fmaf(Rt[k * R4 + r + 1], src[(size_t)(r + 1) * stride], a1);
+        }
+        yz[q].add(a0 + a1);
+      }
+    }
+    __syncthreads();  // the stage, Xt and Rt are free
+    if (tid == 0) {
+      const int64_t nx = tl + (int64_t)D.S * gridDim.x;
+      if (nx < D.ntiles && full_tile(nx)) { issue(nx, s); pend[s] = (int)(((it + D.S) / D.S) & 1); }
+    }
+  }
+  if (s_abort) {
+    if (tid == 0) {
+      atomicOr(io.err, 16);
+      // no copy may still be writing into shared memory when the CTA exits
+      for (int s = 0; s < D.S; ++s)
+        if (pend[s] >= 0) stage_wait(&bar[s], (uint32_t)pend[s]);
+    }
+    __syncthreads();
+    return;
+  }
+
+  // ---- CTA partial row: [l, sum |l_i|, g (theta order)] ----
+  double *out = io.partials + (int64_t)blockIdx.x * (FULL ? 2 + D.n : 2);
+  if (lane == 0) {
+    red[2 * warp] = lsum.value();
+    red[2 * warp + 1] = labs.value();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < kPT / 32; ++w) { a += red[2 * w]; b += red[2 * w + 1]; }
+    out[0] = a;
+    out[1] = b;
+  }
+  if (!FULL) return;
+  const int nitems = D.wk * D.wl;
+#pragma unroll
+  for (int ii = 0; ii < kBetaItems; ++ii) {
+    const int item = warp + 8 * ii;
+    if (item >= nitems) break;
+    const int kp = (item / D.wl) * 4 + (lane >> 3), lq = (item % D.wl) * 8 + (lane & 7);
+    if (kp >= D.kp2 || lq >= D.lq) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = 1 + 2 * kp + h;
+      if (k >= K) continue;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int l = 4 * lq + q;
+        if (l < p) out[2 + (int64_t)(k - 1) * p + l] = bs[ii][4 * h + q].value();
+      }
+    }
+  }
+  // gamma directly; alpha partials per class through shared memory, summed over k in fixed order
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < kYZSlots; ++q) {
+    const int k = yz_k[q];
+    if (k < 0) continue;
+    const int j = yz_j[q];
+    if (j >= 0) out[2 + D.nb + (int64_t)(k - 1) * d + j] = yz[q].value();
+    else red[k * f + (-1 - j)] = yz[q].value();
+  }
+  __syncthreads();
+  for (int j = tid; j < f; j += kPT) {
+    double sa2 = 0.0;
+    for (int k = 0; k < K; ++k) sa2 += red[k * f + j];
+    out[2 + D.mc + j] = sa2;
+  }
+}
+
+int round_up_int(int v, int m) { return (v + m - 1) / m * m; }
+
+bool make_tile_dims(const Shape &s, bool full, int rpw, TileDims &D, size_t &smem) {
+  if (s.K < 2 || s.K > 256) return false;
+  const int cs = (s.K + 31) / 32;
+  D.N = s.N; D.K = s.K; D.p = s.p; D.d = s.d; D.f = s.f;
+  D.Kpad = 32 * (cs <= 1 ? 1 : cs <= 2 ? 2 : cs <= 4 ? 4 : 8);
+  D.R = 8 * rpw;
+  D.R4 = D.R + 4;
+  D.pp = round_up_int(std::max(s.p, 1), 4);
+  D.nb = (int)s.nb; D.mc = (int)s.mc; D.n = (int)s.n;
+  D.ntiles = (s.N + D.R - 1) / D.R;
+  int o = 0;
+  D.off_x = o; o += round_up_int(D.R * s.p * 4, 128);
+  D.off_y = o; o += round_up_int(D.R * s.K * s.d * 4, 128);
+  D.off_z = o; o += round_up_int(D.R * s.K * s.f * 4, 128);
+  D.off_c = o; o += round_up_int(D.R * 4, 128);
+  D.stage_bytes = o;
+  o = 0;
+  D.off_bt = o; o += round_up_int(s.p * D.Kpad * 4, 128);
+  D.off_gt = o; o += round_up_int(s.d * D.Kpad * 4, 128);
+  D.off_al = o; o += round_up_int(std::max(s.f, 1) * 4, 128);
+  D.off_xt = o; o += round_up_int(D.pp * D.R4 * 4, 128);
+  D.off_rt = o; o += full ? round_up_int((D.Kpad + 1) * D.R4 * 4, 128) : 0;
+  D.off_red = o; o += round_up_int(std::max(2 * kPT / 32, s.K * s.f) * 8, 128);
+  D.off_bar = o; o += 128;
+  D.off_stage = o;
+  // beta-gradient items and gamma/alpha entries
+  D.kp2 = (s.K - 1 + 1) / 2;
+  D.lq = (s.p + 3) / 4;
+  D.wk = (D.kp2 + 3) / 4;
+  D.wl = (D.lq + 7) / 8;
+  D.nyz = (s.K - 1) * s.d + s.K * s.f;
+  if (full && (D.wk * D.wl > 8 * kBetaItems || D.nyz > kPT * kYZSlots)) return false;
+  const size_t budget = 200 * 1024;
+  for (int S = 3; S >= 2; --S) {
+    const size_t b = (size_t)o + (size_t)S * D.stage_bytes;
+    if (b <= budget) { D.S = S; smem = b; return true; }
+  }
+  return false;
+}
+
+template <int RPW, int CS, bool FULL>
+cudaError_t launch_t(const TileDims &D, int grid, size_t smem, const PassIO &io, cudaStream_t st) {
+  auto kern = pass_tile_kernel<RPW, CS, FULL>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kPT, smem, st>>>(D, io);
+  return cudaGetLastError();
+}
+
+template <int RPW, bool FULL>
+cudaError_t launch_cs(const TileDims &D, int grid, size_t smem, const PassIO &io, cudaStream_t st) {
+  switch (D.Kpad / 32) {
+    case 1: return launch_t<RPW, 1, FULL>(D, grid, smem, io, st);
+    case 2: return launch_t<RPW, 2, FULL>(D, grid, smem, io, st);
+    case 4: return launch_t<RPW, 4, FULL>(D, grid, smem, io, st);
+    case 8: return launch_t<RPW, 8, FULL>(D, grid, smem, io, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+bool plan_pass_tiled(const Shape &s, bool full, int num_sms, PassPlan &pl) {
+  TileDims D;
+  size_t smem = 0;
+  for (int rpw : {4, 2}) {
+    if (!make_tile_dims(s, full, rpw, D, smem)) continue;
+    pl.tiled = true;
+    pl.rows = D.R;
+    pl.block = kPT;
+    pl.npt = 0;
+    pl.smem = smem;
+    pl.grid = (int)std::min<int64_t>(D.ntiles, num_sms);
+    if (pl.grid < 1) pl.grid = 1;
+    pl.ok = true;
+    return true;
+  }
+  return false;
+}
+
+cudaError_t launch_pass_tiled(const Shape &s, const PassPlan &pl, bool full, const PassIO &io, cudaStream_t st) {
+  TileDims D;
+  size_t smem = 0;
+  if (!make_tile_dims(s, full, pl.rows / 8, D, smem) || smem != pl.smem || io.err == nullptr) return cudaErrorInvalidValue;
+  const bool aligned = ((reinterpret_cast<uintptr_t>(io.X) | reinterpret_cast<uintptr_t>(io.choice) |
+                         (s.d ? reinterpret_cast<uintptr_t>(io.Y) : 0) | (s.f ? reinterpret_cast<uintptr_t>(io.Z) : 0)) &
+                        15) == 0;
+  if (!aligned) return cudaErrorInvalidValue;
+  if (pl.rows == 32) return full ? launch_cs<4, true>(D, pl.grid, smem, io, st) : launch_cs<4, false>(D, pl.grid, smem, io, st);
+  if (pl.rows == 16) return full ? launch_cs<2, true>(D, pl.grid, smem, io, st) : launch_cs<2, false>(D, pl.grid, smem, io, st);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace mnl
