@@ -40,9 +40,18 @@ struct mnl_handle {
   std::vector<int2> h_main, h_band;
   void *main_part, *band_part, *z_part;
   int main_split, band_split, z_split;
-  CUtensorMap *maps;       // device: [0] At, [1] Ad (tensor-core modes)
+  CUtensorMap *maps;       // device: [0] At, [1] Ad, [2] Az (tensor-core modes)
   SyrkUnit *units_main, *units_band;
   int nunits_main, nunits_band, grid_main, grid_band;
+  // Z blocks on the tensor cores (TF32 / BF16 with f > 0): operand Az, contracted tile pairs
+  bool tcz;
+  void *Az;
+  ZopLayout zl;
+  float *zt_part;
+  int *zt_index;
+  int zt_split, zt_npairs, zt_nt;
+  SyrkUnit *units_z;
+  int nunits_z, grid_z;
   double *F;
   // solve
   int solve_mode;  // MNL_SOLVE_FP64 or MNL_SOLVE_MIXED (resolved)
@@ -88,9 +97,10 @@ bool dims_ok(const mnl_dims *d) {
 }
 
 struct Sizes {
-  size_t P, zbar, part_full, part_ll, ops, main_part, band_part, z_part, F, owned, solve;
+  size_t P, zbar, part_full, part_ll, ops, main_part, band_part, z_part, F, owned, solve, zop, zt_part;
   size_t total() const {
-    return P + zbar + part_full + part_ll + 2 * ops + main_part + band_part + z_part + F + owned + solve;
+    return P + zbar + part_full + part_ll + 2 * ops + main_part + band_part + z_part + F + owned + solve + zop +
+           zt_part;
   }
 };
 
@@ -117,7 +127,7 @@ int simt_split(int ntiles, int64_t nchunks, int nsm) {
 }
 
 Sizes plan_sizes(const mnl_dims &d, int prec_in, bool owned, int nsm, int *main_split, int *band_split, int *z_split,
-                 PassPlan *pf, PassPlan *pl, int64_t *ldn, int64_t *mc_pad, int *nt1d, int *nband) {
+                 PassPlan *pf, PassPlan *pl, int64_t *ldn, int64_t *mc_pad, int *nt1d, int *nband, int *zt_split) {
   const Shape S = make_shape(d);
   const int prec = (prec_in == MNL_BF16 && d.N < kBf16MinRows) ? MNL_TF32 : prec_in;
   const bool fp64 = prec == MNL_FP64;
@@ -151,13 +161,25 @@ Sizes plan_sizes(const mnl_dims &d, int prec_in, bool owned, int nsm, int *main_
   z.main_part = (size_t)(*main_split) * nmain * kTile * kTile * csz;
   z.band_part = (size_t)(*band_split) * (*nband) * kTile * kTile * csz;
   const int64_t nzt = zblocks_outputs(S);
-  // observation splits of the Z blocks: about 1024 observations each, at least four CTAs per SM,
-  // at least 256 observations each, and at most 64 MB of partial sums
-  const int64_t zparts = S.f ? zblocks_parts(S, fp64) : 1;
-  int64_t zs = std::max<int64_t>((4 * nsm + zparts - 1) / zparts, S.N / 1024);
-  zs = std::min<int64_t>(zs, std::max<int64_t>(1, ((int64_t)64 << 20) / std::max<int64_t>(1, nzt * (int64_t)tsz)));
-  *z_split = (int)std::max<int64_t>(1, std::min<int64_t>(zs, S.N / 256));
-  z.z_part = S.f ? (size_t)(*z_split) * nzt * tsz : 0;
+  *zt_split = 1;
+  *z_split = 1;
+  if (!fp64 && S.f > 0) {  // Z blocks on the tensor cores
+    const OpType op = prec == MNL_TF32 ? OpType::TF32 : OpType::BF16;
+    const ZopLayout L = zop_layout(S);
+    const ZTiles zt = zop_tiles(S, L);
+    *zt_split = tc_pick_split((int)zt.pairs.size(), tc_kblocks(op, *ldn), nsm);
+    z.zop = (size_t)L.rows_pad * (*ldn) * esz;
+    z.zt_part = (size_t)(*zt_split) * zt.pairs.size() * kTile * kTile * 4;
+    z.z_part = 0;
+  } else {
+    // observation splits of the Z blocks: about 1024 observations each, at least four CTAs per SM,
+    // at least 256 observations each, and at most 64 MB of partial sums
+    const int64_t zparts = S.f ? zblocks_parts(S, fp64) : 1;
+    int64_t zs = std::max<int64_t>((4 * nsm + zparts - 1) / zparts, S.N / 1024);
+    zs = std::min<int64_t>(zs, std::max<int64_t>(1, ((int64_t)64 << 20) / std::max<int64_t>(1, nzt * (int64_t)tsz)));
+    *z_split = (int)std::max<int64_t>(1, std::min<int64_t>(zs, S.N / 256));
+    z.z_part = S.f ? (size_t)(*z_split) * nzt * tsz : 0;
+  }
   z.F = (size_t)S.n * S.n * 8;
   // dinv (float64), F32 (float32), the mixed-solve and float64-factor workspaces
   z.solve = (size_t)S.n * 8 + (size_t)S.n * S.n * 4 + mixed_solve_bytes(S.n) + chol_work_bytes(S.n);
@@ -247,7 +269,11 @@ int run_hessian(mnl_handle *h, cudaEvent_t *ev = nullptr) {
     for (int i = 0; i < 3; ++i)
       if ((rc = mark(h, ev ? ev + i : nullptr))) return rc;
   }
-  if (S.f > 0) {
+  if (S.f > 0 && h->tcz) {
+    CK(launch_build_zop(S, h->op, h->X, h->Y, h->Z, h->P, h->zbar, h->Az, h->ldn, h->st));
+    CK(launch_syrk_tc(h->op, h->maps, h->units_z, h->nunits_z, nullptr, h->grid_z, h->zt_part, h->err, h->st));
+    h->launches += 2;
+  } else if (S.f > 0) {
     CK(launch_zblocks(S, h->fp64, h->X, h->Y, h->Z, h->P, h->zbar, h->z_split, h->z_part, h->st));
     h->launches += 1;
   }
@@ -258,6 +284,16 @@ int run_hessian(mnl_handle *h, cudaEvent_t *ev = nullptr) {
   io.z_part = h->z_part; io.z_split = h->z_split;
   io.tl = &h->tl;
   io.fp64 = h->fp64;
+  if (h->tcz) {
+    io.zt.part = h->zt_part;
+    io.zt.split = h->zt_split;
+    io.zt.npairs = h->zt_npairs;
+    io.zt.nt = h->zt_nt;
+    io.zt.index = h->zt_index;
+    io.zt.oY = h->zl.oY;
+    io.zt.oW = h->zl.oW;
+    io.zt.oZ = h->zl.oZ;
+  }
   CK(launch_assemble(S, io, nmain, h->F, h->st));
   h->launches += 1;
   return MNL_OK;
@@ -453,7 +489,8 @@ size_t mnl_workspace_bytes(const mnl_dims *d, int precision) {
   int ms, bs, zs, nt1d, nband;
   PassPlan pf, pl;
   int64_t ldn, mcp;
-  Sizes z = plan_sizes(*d, precision, false, nsm, &ms, &bs, &zs, &pf, &pl, &ldn, &mcp, &nt1d, &nband);
+  int zts = 1;
+  Sizes z = plan_sizes(*d, precision, false, nsm, &ms, &bs, &zs, &pf, &pl, &ldn, &mcp, &nt1d, &nband, &zts);
   return z.total();
 }
 
@@ -486,7 +523,7 @@ int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *
   cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev);
   int nband = 0;
   Sizes z = plan_sizes(*dims, precision, data == nullptr, h->nsm, &h->main_split, &h->band_split, &h->z_split,
-                       &h->pfull, &h->pll, &h->ldn, &h->mc_pad, &h->nt1d, &nband);
+                       &h->pfull, &h->pll, &h->ldn, &h->mc_pad, &h->nt1d, &nband, &h->zt_split);
   if (!h->pfull.ok || !h->pll.ok) return fail(MNL_ERR_UNSUPPORTED);
 
   for (auto &e : h->ev)
@@ -539,10 +576,34 @@ int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *
     cudaGetLastError();
     return fail(MNL_ERR_CUDA);
   }
-  if (!h->fp64 && S.mc > 0) {
-    CUtensorMap hm[2];
-    cudaError_t e = encode_operand_map(h->op, h->At, h->mc_pad, h->ldn, &hm[0]);
-    if (e == cudaSuccess) e = encode_operand_map(h->op, h->Ad, h->mc_pad, h->ldn, &hm[1]);
+  h->tcz = !h->fp64 && S.f > 0;
+  if (!h->fp64 && (S.mc > 0 || h->tcz)) {
+    CUtensorMap hm[3];
+    std::memset(hm, 0, sizeof(hm));
+    cudaError_t e = cudaSuccess;
+    if (S.mc > 0) {
+      e = encode_operand_map(h->op, h->At, h->mc_pad, h->ldn, &hm[0]);
+      if (e == cudaSuccess) e = encode_operand_map(h->op, h->Ad, h->mc_pad, h->ldn, &hm[1]);
+    }
+    ZTiles zt;
+    if (e == cudaSuccess && h->tcz) {
+      h->zl = zop_layout(S);
+      zt = zop_tiles(S, h->zl);
+      h->zt_npairs = (int)zt.pairs.size();
+      h->zt_nt = zt.nt;
+      const size_t zbytes = (size_t)h->zl.rows_pad * h->ldn * (h->op == OpType::TF32 ? 4 : 2);
+      if ((rc = dalloc(h, &h->Az, zbytes)) ||
+          (rc = dalloc(h, &h->zt_part, (size_t)h->zt_split * zt.pairs.size() * kTile * kTile * 4)) ||
+          (rc = dalloc(h, &h->zt_index, zt.index.size() * sizeof(int))))
+        return fail(rc);
+      if (cudaMemsetAsync(h->Az, 0, zbytes, h->st) != cudaSuccess ||
+          cudaMemcpy(h->zt_index, zt.index.data(), zt.index.size() * sizeof(int), cudaMemcpyHostToDevice) !=
+              cudaSuccess) {
+        cudaGetLastError();
+        return fail(MNL_ERR_CUDA);
+      }
+      e = encode_operand_map(h->op, h->Az, h->zl.rows_pad, h->ldn, &hm[2]);
+    }
     if (e != cudaSuccess) return fail(cuda_fail(e));
     // Units: split-major, so CTAs running at the same time read the same observation range (L2 reuse).
     const int kb = tc_kblocks(h->op, h->ldn);
@@ -560,22 +621,27 @@ int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *
         }
       return u;
     };
-    const std::vector<SyrkUnit> jm = make_units(h->h_main, h->main_split, 0);
-    const std::vector<SyrkUnit> jb = make_units(h->h_band, h->band_split, 1);
+    const std::vector<SyrkUnit> jm = S.mc > 0 ? make_units(h->h_main, h->main_split, 0) : std::vector<SyrkUnit>();
+    const std::vector<SyrkUnit> jb = S.mc > 0 ? make_units(h->h_band, h->band_split, 1) : std::vector<SyrkUnit>();
+    const std::vector<SyrkUnit> jz = h->tcz ? make_units(zt.pairs, h->zt_split, 2) : std::vector<SyrkUnit>();
     h->grid_main = std::min((int)jm.size(), h->nsm);
     h->grid_band = std::min((int)jb.size(), h->nsm);
+    h->grid_z = std::min((int)jz.size(), h->nsm);
     const std::vector<SyrkUnit> um = schedule_syrk_units(jm, h->grid_main, tc_chunk_kblocks(h->op));
     const std::vector<SyrkUnit> ub = schedule_syrk_units(jb, h->grid_band, tc_chunk_kblocks(h->op));
+    const std::vector<SyrkUnit> uz = schedule_syrk_units(jz, h->grid_z, tc_chunk_kblocks(h->op));
     h->nunits_main = (int)um.size();
     h->nunits_band = (int)ub.size();
+    h->nunits_z = (int)uz.size();
     if ((rc = dalloc(h, &h->maps, sizeof(hm))) || (rc = dalloc(h, &h->units_main, um.size() * sizeof(SyrkUnit))) ||
-        (rc = dalloc(h, &h->units_band, ub.size() * sizeof(SyrkUnit))))
+        (rc = dalloc(h, &h->units_band, ub.size() * sizeof(SyrkUnit))) ||
+        (rc = dalloc(h, &h->units_z, uz.size() * sizeof(SyrkUnit))))
       return fail(rc);
-    if (cudaMemcpy(h->maps, hm, sizeof(hm), cudaMemcpyHostToDevice) != cudaSuccess ||
-        (!um.empty() && cudaMemcpy(h->units_main, um.data(), um.size() * sizeof(SyrkUnit), cudaMemcpyHostToDevice) !=
-                            cudaSuccess) ||
-        (!ub.empty() && cudaMemcpy(h->units_band, ub.data(), ub.size() * sizeof(SyrkUnit), cudaMemcpyHostToDevice) !=
-                            cudaSuccess)) {
+    auto up = [&](SyrkUnit *dst, const std::vector<SyrkUnit> &v) {
+      return v.empty() || cudaMemcpy(dst, v.data(), v.size() * sizeof(SyrkUnit), cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    if (cudaMemcpy(h->maps, hm, sizeof(hm), cudaMemcpyHostToDevice) != cudaSuccess || !up(h->units_main, um) ||
+        !up(h->units_band, ub) || !up(h->units_z, uz)) {
       cudaGetLastError();
       return fail(MNL_ERR_CUDA);
     }

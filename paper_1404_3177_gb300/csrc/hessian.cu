@@ -94,6 +94,11 @@ __device__ __forceinline__ uint32_t remix(uint32_t h, uint32_t k) {
 constexpr int kBob = 64;        // observations per builder block (8 lanes x 8)
 constexpr int kBs = kBob + 4;   // shared row stride (16-byte aligned rows)
 
+struct ZopDims {
+  int64_t N, ldn, oY, oW, oZ;
+  int K, p, d, f, kc;
+};
+
 struct BuildDims {
   int64_t N, ldn;
   int K, p, d, q;
@@ -230,6 +235,106 @@ __global__ void __launch_bounds__(256) grouped_build_kernel(const GroupProblem *
   D.N = g.N; D.ldn = g.ldn; D.K = g.K; D.p = g.p; D.d = g.d; D.q = g.p + g.d;
   D.ob = g.build_ob; D.kc = g.build_kc;
   build_block<OT, PT>(D, g.X, g.Y, reinterpret_cast<const PT *>(g.P), g.At, g.Ad, it.idx);
+}
+
+// ---------------------------------------------------------------------------
+// Z-block operand for the tensor-core contraction (TF32 / BF16 modes).  Rows,
+// in blocks that start on 128-row tiles, observations contiguous:
+//   X  rows l          x_il                      (oX = 0)
+//   Y  rows (k-1) d + l  y_ikl, k >= 1             (oY)
+//   W  rows k f + j    P_ik (z_ikj - zbar_ij)     (oW)
+//   Zc rows k f + j    z_ikj - zbar_ij            (oZ)
+// so that C_X = X W^T, C_Y = the class-diagonal blocks of Y W^T and
+// A = sum_k W_k Zc_k^T are tiles of the Gram matrix of this operand.
+// Staging is transposed like the class-operand builder (8 observations per
+// lane, 16-byte stores, stochastic rounding for BF16).
+// ---------------------------------------------------------------------------
+
+template <OpType OT, typename PT>
+__global__ void __launch_bounds__(256) build_zop_kernel(ZopDims D, const float *__restrict__ X,
+                                                        const float *__restrict__ Y, const float *__restrict__ Z,
+                                                        const PT *__restrict__ P, const PT *__restrict__ zbar,
+                                                        void *Az) {
+  using CT = typename OpStore<OT>::CT;
+  constexpr int esz = OT == OpType::F64 ? 8 : OT == OpType::TF32 ? 4 : 2;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int K = D.K, p = D.p, d = D.d, f = D.f, kc = D.kc;
+  float *XsT = reinterpret_cast<float *>(smem);                 // [p][kBs]
+  float *YsT = XsT + (size_t)p * kBs;                            // [kc d][kBs]
+  CT *ZcT = reinterpret_cast<CT *>(YsT + (size_t)kc * d * kBs);  // [kc f][kBs]
+  CT *PsT = ZcT + (size_t)kc * f * kBs;                          // [kc][kBs]
+  CT *zbT = PsT + (size_t)kc * kBs;                              // [f][kBs]
+  const int64_t i0 = (int64_t)blockIdx.x * kBob;
+  const int nobs = (int)min((int64_t)kBob, D.N - i0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int cl = lane >> 3, oc = (lane & 7) * 8;
+  const uint32_t iobs = (uint32_t)(i0 + oc);
+  auto put_row = [&](int64_t row, const CT v[8]) {
+    const uint32_t h = mix3(5u, (uint32_t)row, iobs);
+    OpStore<OT>::put8(reinterpret_cast<unsigned char *>(Az) + (row * D.ldn + i0 + oc) * esz, v, h, remix(h, 1u));
+  };
+  for (int e = tid; e < kBob * p; e += 256) {
+    const int r = e / p, l = e - r * p;
+    XsT[l * kBs + r] = r < nobs ? __ldg(X + i0 * p + e) : 0.f;
+  }
+  for (int e = tid; e < kBob * f; e += 256) {
+    const int r = e / f, j = e - r * f;
+    zbT[j * kBs + r] = r < nobs ? (CT)zbar[i0 * f + e] : (CT)0;
+  }
+  __syncthreads();
+  for (int cg = warp * 4; cg < p; cg += nw * 4) {  // X rows
+    const int l = cg + cl;
+    if (l >= p) continue;
+    CT v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = (CT)XsT[l * kBs + oc + u];
+    put_row(l, v);
+  }
+  for (int k0 = 0; k0 < K; k0 += kc) {
+    const int k1 = min(K, k0 + kc), nk = k1 - k0;
+    __syncthreads();
+    for (int e = tid; e < kBob * nk; e += 256) {
+      const int r = e / nk, kk = e - r * nk;
+      PsT[kk * kBs + r] = r < nobs ? (CT)P[(i0 + r) * K + k0 + kk] : (CT)0;
+    }
+    if (d)
+      for (int e = tid; e < kBob * nk * d; e += 256) {
+        const int r = e / (nk * d), c = e - r * (nk * d);
+        YsT[c * kBs + r] = r < nobs ? __ldg(Y + ((i0 + r) * K + k0) * d + c) : 0.f;
+      }
+    __syncthreads();
+    for (int e = tid; e < kBob * nk * f; e += 256) {
+      const int r = e / (nk * f), c = e - r * (nk * f), j = c % f;
+      ZcT[c * kBs + r] = r < nobs ? (CT)__ldg(Z + ((i0 + r) * K + k0) * f + c) - zbT[j * kBs + r] : (CT)0;
+    }
+    __syncthreads();
+    const int ny = (k0 == 0 ? nk - 1 : nk) * d;  // Y rows of classes >= 1 in this chunk
+    const int nwz = nk * f;
+    const int rows = ny + 2 * nwz;
+    for (int cg = warp * 4; cg < rows; cg += nw * 4) {
+      const int c = cg + cl;
+      if (c >= rows) continue;
+      CT v[8];
+      int64_t row;
+      if (c < ny) {  // y_ikl
+        const int kk = (k0 == 0 ? 1 : 0) + c / d, l = c - (c / d) * d;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = (CT)YsT[(kk * d + l) * kBs + oc + u];
+        row = D.oY + (int64_t)(k0 + kk - 1) * d + l;
+      } else if (c < ny + nwz) {  // P_ik (z_ikj - zbar_ij)
+        const int c2 = c - ny, kk = c2 / f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = PsT[kk * kBs + oc + u] * ZcT[c2 * kBs + oc + u];
+        row = D.oW + (int64_t)k0 * f + c2;
+      } else {  // z_ikj - zbar_ij
+        const int c2 = c - ny - nwz;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = ZcT[c2 * kBs + oc + u];
+        row = D.oZ + (int64_t)k0 * f + c2;
+      }
+      put_row(row, v);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -682,11 +787,21 @@ __global__ void __launch_bounds__(kZThreads) grouped_zblocks_kernel(const GroupP
 // ---------------------------------------------------------------------------
 
 // F(r, c), r >= c, from the partial sums.
+// Entry (a, b) of the Gram matrix of the Z-block operand, summed over the splits.
+__device__ __forceinline__ double zop_entry(const ZTileView &zv, int64_t a, int64_t b) {
+  const int pair = zv.index[(a / kTile) * zv.nt + (b / kTile)];
+  const int64_t within = (b % kTile) * kTile + (a % kTile);  // tiles are stored [b][a]
+  double v = 0.0;
+  for (int s = 0; s < zv.split; ++s) v += (double)zv.part[((int64_t)s * zv.npairs + pair) * kTile * kTile + within];
+  return v;
+}
+
 template <typename CT, typename ZT>
 __device__ __forceinline__ double assemble_entry(const Shape &S, const CT *__restrict__ mainp, int msplit, int nmain,
                                                  const CT *__restrict__ bandp, int bsplit, int nband,
                                                  const int *__restrict__ band_of, int nt1d,
-                                                 const ZT *__restrict__ zp, int zsplit, int64_t r, int64_t c) {
+                                                 const ZT *__restrict__ zp, int zsplit, int64_t r, int64_t c,
+                                                 const ZTileView &zv = ZTileView()) {
   const int q = S.q, f = S.f, K = S.K;
   const int64_t nx = (int64_t)S.p * K * f, ny = (int64_t)K * S.d * f, nzt = nx + ny + (int64_t)f * f;
   double v = 0.0;
@@ -709,11 +824,19 @@ __device__ __forceinline__ double assemble_entry(const Shape &S, const CT *__res
     const int j = (int)(r - S.mc);
     int kc, lc;
     theta_class_local(S, c, kc, lc);
+    if (zv.part) {  // C_X = X W^T, C_Y = Y W^T (class kc)
+      const int64_t a = lc < S.p ? (int64_t)lc : zv.oY + (int64_t)(kc - 1) * S.d + (lc - S.p);
+      return zop_entry(zv, a, zv.oW + (int64_t)kc * f + j);
+    }
     const int64_t off = lc < S.p ? (int64_t)lc * K * f + (int64_t)kc * f + j
                                  : nx + (int64_t)kc * S.d * f + (int64_t)(lc - S.p) * f + j;
     for (int s = 0; s < zsplit; ++s) v += (double)zp[s * nzt + off];
   } else {
     const int j1 = (int)(r - S.mc), j2 = (int)(c - S.mc);
+    if (zv.part) {  // A = sum_k W_k Zc_k^T
+      for (int k = 0; k < K; ++k) v += zop_entry(zv, zv.oW + (int64_t)k * f + j1, zv.oZ + (int64_t)k * f + j2);
+      return v;
+    }
     const int64_t off = nx + ny + (int64_t)j1 * f + j2;
     for (int s = 0; s < zsplit; ++s) v += (double)zp[s * nzt + off];
   }
@@ -723,13 +846,13 @@ __device__ __forceinline__ double assemble_entry(const Shape &S, const CT *__res
 template <typename CT, typename ZT>
 __global__ void assemble_kernel(Shape S, const CT *__restrict__ mainp, int msplit, int nmain,
                                 const CT *__restrict__ bandp, int bsplit, int nband, const int *__restrict__ band_of,
-                                int nt1d, const ZT *__restrict__ zp, int zsplit, double *__restrict__ F) {
+                                int nt1d, const ZT *__restrict__ zp, int zsplit, ZTileView zv, double *__restrict__ F) {
   const int64_t n = S.n;
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t c = blockIdx.y + (int64_t)gridDim.y * blockIdx.z;
   if (r >= n || c >= n || r < c) return;  // (r, c) in the lower triangle; both mirror entries are written
   const double v = assemble_entry<CT, ZT>(S, mainp, msplit, nmain, bandp, bsplit, nband, band_of, nt1d, zp, zsplit,
-                                          r, c);
+                                          r, c, zv);
   F[c * n + r] = v;
   F[r * n + c] = v;
 }
@@ -953,12 +1076,88 @@ cudaError_t launch_assemble(const Shape &s, const AssembleIO &io, int nmain, dou
     assemble_kernel<double, double><<<grid, block, 0, st>>>(
         s, reinterpret_cast<const double *>(io.main_part), io.main_split, nmain,
         reinterpret_cast<const double *>(io.band_part), io.band_split, tl.nband, tl.band_of, nt1d,
-        reinterpret_cast<const double *>(io.z_part), io.z_split, F);
+        reinterpret_cast<const double *>(io.z_part), io.z_split, io.zt, F);
   } else {
     assemble_kernel<float, float><<<grid, block, 0, st>>>(
         s, reinterpret_cast<const float *>(io.main_part), io.main_split, nmain,
         reinterpret_cast<const float *>(io.band_part), io.band_split, tl.nband, tl.band_of, nt1d,
-        reinterpret_cast<const float *>(io.z_part), io.z_split, F);
+        reinterpret_cast<const float *>(io.z_part), io.z_split, io.zt, F);
+  }
+  return cudaGetLastError();
+}
+
+ZopLayout zop_layout(const Shape &s) {
+  auto r128 = [](int64_t v) { return (v + kTile - 1) / kTile * kTile; };
+  ZopLayout L;
+  L.oY = r128(s.p);
+  L.oW = L.oY + r128((int64_t)(s.K - 1) * s.d);
+  L.oZ = L.oW + r128((int64_t)s.K * s.f);
+  L.rows_pad = L.oZ + r128((int64_t)s.K * s.f);
+  return L;
+}
+
+ZTiles zop_tiles(const Shape &s, const ZopLayout &L) {
+  ZTiles z;
+  z.nt = (int)(L.rows_pad / kTile);
+  z.index.assign((size_t)z.nt * z.nt, -1);
+  auto add = [&](int64_t ti, int64_t tj) {
+    int &slot = z.index[(size_t)ti * z.nt + tj];
+    if (slot < 0) { slot = (int)z.pairs.size(); z.pairs.push_back(make_int2((int)ti, (int)tj)); }
+  };
+  const int f = s.f, d = s.d;
+  if (f == 0) return z;
+  // C_X: every X tile with every W tile
+  for (int64_t ti = 0; ti * kTile < s.p; ++ti)
+    for (int64_t tj = L.oW / kTile; tj * kTile < L.oW + (int64_t)s.K * f; ++tj) add(ti, tj);
+  // C_Y and A: tiles that hold rows of the same class
+  for (int k = 0; k < s.K; ++k) {
+    const int64_t w0 = (L.oW + (int64_t)k * f) / kTile, w1 = (L.oW + (int64_t)k * f + f - 1) / kTile;
+    if (k >= 1 && d > 0) {
+      const int64_t y0 = (L.oY + (int64_t)(k - 1) * d) / kTile, y1 = (L.oY + (int64_t)(k - 1) * d + d - 1) / kTile;
+      for (int64_t a = y0; a <= y1; ++a)
+        for (int64_t b = w0; b <= w1; ++b) add(a, b);
+    }
+    const int64_t z0 = (L.oZ + (int64_t)k * f) / kTile, z1 = (L.oZ + (int64_t)k * f + f - 1) / kTile;
+    for (int64_t a = w0; a <= w1; ++a)
+      for (int64_t b = z0; b <= z1; ++b) add(a, b);
+  }
+  return z;
+}
+
+size_t zop_smem(const Shape &s, OpType t, int kc) {
+  const size_t csz = t == OpType::F64 ? 8 : 4;
+  return ((size_t)s.p + (size_t)kc * s.d) * kBs * 4 + ((size_t)kc * s.f + kc + s.f) * kBs * csz;
+}
+
+int zop_kc(const Shape &s, OpType t) {
+  int kc = std::max(1, s.K);
+  while (kc > 1 && zop_smem(s, t, kc) > 100 * 1024) kc = (kc + 1) / 2;
+  return kc;
+}
+
+cudaError_t launch_build_zop(const Shape &s, OpType t, const float *X, const float *Y, const float *Z, const void *P,
+                             const void *zbar, void *Az, int64_t ldn, cudaStream_t st) {
+  const ZopLayout L = zop_layout(s);
+  ZopDims D;
+  D.N = s.N; D.ldn = ldn; D.oY = L.oY; D.oW = L.oW; D.oZ = L.oZ;
+  D.K = s.K; D.p = s.p; D.d = s.d; D.f = s.f;
+  D.kc = zop_kc(s, t);
+  const size_t smem = zop_smem(s, t, D.kc);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  const int blocks = (int)((s.N + kBob - 1) / kBob);
+  cudaError_t e;
+  if (t == OpType::TF32) {
+    auto k = build_zop_kernel<OpType::TF32, float>;
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+    k<<<blocks, 256, smem, st>>>(D, X, Y, Z, reinterpret_cast<const float *>(P),
+                                 reinterpret_cast<const float *>(zbar), Az);
+  } else if (t == OpType::BF16) {
+    auto k = build_zop_kernel<OpType::BF16, float>;
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+    k<<<blocks, 256, smem, st>>>(D, X, Y, Z, reinterpret_cast<const float *>(P),
+                                 reinterpret_cast<const float *>(zbar), Az);
+  } else {
+    return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }

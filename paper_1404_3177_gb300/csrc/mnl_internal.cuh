@@ -245,12 +245,37 @@ cudaError_t launch_zblocks(const Shape &s, bool fp64, const float *X, const floa
 
 // Assemble F = -H (n x n, column-major, both triangles) from the contraction
 // partials.  main/band partials are FP32 (tensor path) or FP64.
+// Z blocks from the tensor-core contraction of the Z-block operand (TF32 /
+// BF16 modes): row offsets of its blocks (X at 0), and the tile pairs that are
+// contracted (index[ti * nt + tj] = pair or -1; partial tiles [split][pair]).
+struct ZopLayout {
+  int64_t oY, oW, oZ, rows_pad;
+};
+ZopLayout zop_layout(const Shape &s);
+struct ZTiles {
+  std::vector<int2> pairs;
+  std::vector<int> index;  // [nt * nt]
+  int nt = 0;
+};
+ZTiles zop_tiles(const Shape &s, const ZopLayout &L);
+size_t zop_smem(const Shape &s, OpType t, int kc);
+int zop_kc(const Shape &s, OpType t);
+cudaError_t launch_build_zop(const Shape &s, OpType t, const float *X, const float *Y, const float *Z, const void *P,
+                             const void *zbar, void *Az, int64_t ldn, cudaStream_t st);
+struct ZTileView {
+  const float *part = nullptr;  // nullptr: Z blocks come from z_part (CUDA-core kernel)
+  int split = 0, npairs = 0, nt = 0;
+  const int *index = nullptr;
+  int64_t oY = 0, oW = 0, oZ = 0;
+};
+
 struct AssembleIO {
   const void *main_part; int main_split;
   const void *band_part; int band_split;
   const void *z_part;    int z_split;
   const TileLists *tl;   // device pointers inside
   bool fp64;
+  ZTileView zt;
 };
 cudaError_t launch_assemble(const Shape &s, const AssembleIO &io, int nmain, double *F, cudaStream_t st);
 

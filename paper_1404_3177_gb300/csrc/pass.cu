@@ -357,32 +357,34 @@ __global__ void __launch_bounds__(128) grouped_reduce_kernel(const GroupProblem 
   }
 }
 
-// Fixed-order float64 reduction of the CTA partials: one thread per output,
-// four interleaved accumulators (so four loads are in flight), added in a
-// fixed order at the end.
-__global__ void __launch_bounds__(128) pass_reduce_kernel(PassDims D, int grid, int full,
+// Fixed-order float64 reduction of the CTA partials (rows of `stride` values,
+// `grid` rows): a CTA takes 32 consecutive columns; warp w adds rows w, w + 8,
+// ... with lanes over the columns (coalesced), two accumulators per lane, and
+// the 8 warp sums are added in warp order.  Column 0, 1 -> scal[0], scal[1];
+// column 2 + o -> grad[o].
+__global__ void __launch_bounds__(256) pass_reduce_kernel(int64_t ncols, int64_t stride, int grid,
                                                           const double *__restrict__ part, double *__restrict__ scal,
                                                           double *__restrict__ grad) {
-  const int64_t n = D.mc + D.f;
-  const int64_t stride = full ? 2 + n : 2;
-  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (blockIdx.x == 0 && threadIdx.x < 2) {
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
-    int g = 0;
-    for (; g + 4 <= grid; g += 4)
-#pragma unroll
-      for (int u = 0; u < 4; ++u) s[u] += part[(g + u) * stride + threadIdx.x];
-    for (; g < grid; ++g) s[0] += part[g * stride + threadIdx.x];
-    scal[threadIdx.x] = (s[0] + s[1]) + (s[2] + s[3]);
+  __shared__ double red[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t col = (int64_t)blockIdx.x * 32 + lane;
+  double s0 = 0.0, s1 = 0.0;
+  if (col < ncols) {
+    int g = warp;
+    for (; g + 8 < grid; g += 16) {
+      s0 += part[(int64_t)g * stride + col];
+      s1 += part[(int64_t)(g + 8) * stride + col];
+    }
+    if (g < grid) s0 += part[(int64_t)g * stride + col];
   }
-  if (!full || o >= n) return;
-  double s[4] = {0.0, 0.0, 0.0, 0.0};
-  int g = 0;
-  for (; g + 4 <= grid; g += 4)
-#pragma unroll
-    for (int u = 0; u < 4; ++u) s[u] += part[(g + u) * stride + 2 + o];
-  for (; g < grid; ++g) s[0] += part[g * stride + 2 + o];
-  grad[o] = (s[0] + s[1]) + (s[2] + s[3]);
+  red[warp][lane] = s0 + s1;
+  __syncthreads();
+  if (warp == 0 && col < ncols) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w][lane];
+    if (col < 2) scal[col] = t;
+    else grad[col - 2] = t;
+  }
 }
 
 __global__ void validate_kernel(int64_t N, int K, int p, int d, int f, const float *X, const float *Y, const float *Z,
@@ -486,11 +488,9 @@ cudaError_t launch_pass(const Shape &s, const PassPlan &pl, bool fp64, bool full
 
 cudaError_t launch_pass_reduce(const Shape &s, int grid, bool full, const double *partials, double *scal,
                                double *grad, cudaStream_t st) {
-  const PassDims D = dims_of(s, 1);
-  const int64_t n = full ? s.n : 1;
-  const int threads = 128;
-  const int blocks = (int)((n + threads - 1) / threads);
-  pass_reduce_kernel<<<blocks, threads, 0, st>>>(D, grid, full ? 1 : 0, partials, scal, grad);
+  const int64_t stride = full ? 2 + s.n : 2;
+  const int blocks = (int)((stride + 31) / 32);
+  pass_reduce_kernel<<<blocks, 256, 0, st>>>(stride, stride, grid, partials, scal, grad);
   return cudaGetLastError();
 }
 

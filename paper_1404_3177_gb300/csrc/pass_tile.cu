@@ -4,7 +4,7 @@
 //
 // Same results as the pass of pass.cu (utilities over all K alternatives from
 // raw data, row softmax, l, P, zbar and g), organised for bandwidth:
-//   * one CTA per SM walks tiles of R = 8 * RPW consecutive observations; the
+//   * one or two CTAs per SM walk tiles of R = 8 * RPW consecutive observations; the
 //     X, Y, Z and choice rows of a tile are contiguous in memory and arrive by
 //     bulk asynchronous copies (cp.async.bulk, completion counted on an
 //     mbarrier) into a ring of 2-3 shared-memory stages, so the next tiles
@@ -30,8 +30,8 @@ namespace mnl {
 namespace {
 
 constexpr int kPT = 256;          // threads per CTA
-constexpr int kBetaItems = 3;     // beta-gradient register tiles per warp
-constexpr int kYZSlots = 4;       // gamma / alpha outputs per thread
+constexpr int kBetaItems = 2;     // beta-gradient register tiles per warp
+constexpr int kYZSlots = 2;       // gamma / alpha outputs per thread
 constexpr uint64_t kTileWaitNs = 2000000000ull;
 
 struct TileDims {
@@ -113,7 +113,7 @@ __device__ __forceinline__ void load_rows(const float *p, float v[RPW]) {
 }
 
 template <int RPW, int CS, bool FULL>
-__global__ void __launch_bounds__(kPT, 1) pass_tile_kernel(TileDims D, PassIO io) {
+__global__ void __launch_bounds__(kPT, 2) pass_tile_kernel(TileDims D, PassIO io) {
   extern __shared__ __align__(128) unsigned char sm[];
   float *Bt = reinterpret_cast<float *>(sm + D.off_bt);  // [p][Kpad]
   float *Gt = reinterpret_cast<float *>(sm + D.off_gt);  // [d][Kpad]
@@ -220,6 +220,7 @@ __global__ void __launch_bounds__(kPT, 1) pass_tile_kernel(TileDims D, PassIO io
       for (int r = 0; r < RPW; ++r)
 #pragma unroll
         for (int c = 0; c < CS; ++c) u[r][c] = 0.f;
+#pragma unroll 2
       for (int j = 0; j < p; ++j) {
         float xv[RPW];
         load_rows<RPW>(Xt + j * R4 + r0, xv);
@@ -242,6 +243,7 @@ __global__ void __launch_bounds__(kPT, 1) pass_tile_kernel(TileDims D, PassIO io
           for (int j = 0; j < f; ++j) u[r][c] = fmaf(z[j], al[j], u[r][c]);
         }
       }
+      float res[CS][RPW];  // residuals of this lane's classes for the warp's rows
 #pragma unroll
       for (int r = 0; r < RPW; ++r) {
         const int rr = r0 + r;
@@ -280,7 +282,7 @@ __global__ void __launch_bounds__(kPT, 1) pass_tile_kernel(TileDims D, PassIO io
             const float P = u[r][c] * inv;
             u[r][c] = P;
             if (k < K && vr) Pg[k] = P;
-            Rt[k * R4 + rr] = (k < K && vr) ? ((k == yi ? 1.f : 0.f) - P) : 0.f;
+            res[c][r] = (k < K && vr) ? ((k == yi ? 1.f : 0.f) - P) : 0.f;
           }
           for (int j = 0; j < f; ++j) {
             float zb = 0.f;
@@ -292,6 +294,15 @@ __global__ void __launch_bounds__(kPT, 1) pass_tile_kernel(TileDims D, PassIO io
             zb = wsum(zb);
             if (vr && lane == 0) reinterpret_cast<float *>(io.zbar)[(row0 + rr) * f + j] = zb;
           }
+        }
+      }
+      if (FULL) {
+#pragma unroll
+        for (int c = 0; c < CS; ++c) {
+          float *dst = Rt + (lane + 32 * c) * R4 + r0;
+          if (RPW == 4) *reinterpret_cast<float4 *>(dst) = make_float4(res[c][0], res[c][1], res[c][2], res[c][3]);
+          else if (RPW == 2) *reinterpret_cast<float2 *>(dst) = make_float2(res[c][0], res[c][1]);
+          else dst[0] = res[c][0];
         }
       }
     }
@@ -440,11 +451,12 @@ bool make_tile_dims(const Shape &s, bool full, int rpw, TileDims &D, size_t &sme
   D.wl = (D.lq + 7) / 8;
   D.nyz = (s.K - 1) * s.d + s.K * s.f;
   if (full && (D.wk * D.wl > 8 * kBetaItems || D.nyz > kPT * kYZSlots)) return false;
-  const size_t budget = 200 * 1024;
-  for (int S = 3; S >= 2; --S) {
-    const size_t b = (size_t)o + (size_t)S * D.stage_bytes;
-    if (b <= budget) { D.S = S; smem = b; return true; }
-  }
+  // two CTAs per SM when a 2-stage ring fits in half of the shared memory, else one
+  for (size_t budget : {(size_t)110 * 1024, (size_t)200 * 1024})
+    for (int S = 3; S >= 2; --S) {
+      const size_t b = (size_t)o + (size_t)S * D.stage_bytes;
+      if (b <= budget) { D.S = S; smem = b; return true; }
+    }
   return false;
 }
 
@@ -473,14 +485,14 @@ cudaError_t launch_cs(const TileDims &D, int grid, size_t smem, const PassIO &io
 bool plan_pass_tiled(const Shape &s, bool full, int num_sms, PassPlan &pl) {
   TileDims D;
   size_t smem = 0;
-  for (int rpw : {4, 2}) {
+  for (int rpw : {2}) {
     if (!make_tile_dims(s, full, rpw, D, smem)) continue;
     pl.tiled = true;
     pl.rows = D.R;
     pl.block = kPT;
     pl.npt = 0;
     pl.smem = smem;
-    pl.grid = (int)std::min<int64_t>(D.ntiles, num_sms);
+    pl.grid = (int)std::min<int64_t>(D.ntiles, (int64_t)num_sms * (smem <= 110 * 1024 ? 2 : 1));
     if (pl.grid < 1) pl.grid = 1;
     pl.ok = true;
     return true;
@@ -496,7 +508,6 @@ cudaError_t launch_pass_tiled(const Shape &s, const PassPlan &pl, bool full, con
                          (s.d ? reinterpret_cast<uintptr_t>(io.Y) : 0) | (s.f ? reinterpret_cast<uintptr_t>(io.Z) : 0)) &
                         15) == 0;
   if (!aligned) return cudaErrorInvalidValue;
-  if (pl.rows == 32) return full ? launch_cs<4, true>(D, pl.grid, smem, io, st) : launch_cs<4, false>(D, pl.grid, smem, io, st);
   if (pl.rows == 16) return full ? launch_cs<2, true>(D, pl.grid, smem, io, st) : launch_cs<2, false>(D, pl.grid, smem, io, st);
   return cudaErrorInvalidValue;
 }
