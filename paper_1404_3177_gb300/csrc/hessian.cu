@@ -250,6 +250,30 @@ __global__ void __launch_bounds__(256) grouped_build_kernel(const GroupProblem *
 // lane, 16-byte stores, stochastic rounding for BF16).
 // ---------------------------------------------------------------------------
 
+// dst[c * kBs + r] = get(r, c) for r < kBob, c < w (zero for r >= nobs), with 8
+// loads in flight per thread.
+template <typename T, typename Get>
+__device__ __forceinline__ void stage_transposed(T *dst, int w, int nobs, Get get) {
+  const int tot = kBob * w;
+  for (int e0 = 0; e0 < tot; e0 += 8 * 256) {
+    T v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + (int)threadIdx.x + u * 256;
+      const int r = e / w;
+      v[u] = (e < tot && r < nobs) ? get(r, e - r * w) : (T)0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + (int)threadIdx.x + u * 256;
+      if (e < tot) {
+        const int r = e / w;
+        dst[(e - r * w) * kBs + r] = v[u];
+      }
+    }
+  }
+}
+
 template <OpType OT, typename PT>
 __global__ void __launch_bounds__(256) build_zop_kernel(ZopDims D, const float *__restrict__ X,
                                                         const float *__restrict__ Y, const float *__restrict__ Z,
@@ -273,14 +297,8 @@ __global__ void __launch_bounds__(256) build_zop_kernel(ZopDims D, const float *
     const uint32_t h = mix3(5u, (uint32_t)row, iobs);
     OpStore<OT>::put8(reinterpret_cast<unsigned char *>(Az) + (row * D.ldn + i0 + oc) * esz, v, h, remix(h, 1u));
   };
-  for (int e = tid; e < kBob * p; e += 256) {
-    const int r = e / p, l = e - r * p;
-    XsT[l * kBs + r] = r < nobs ? __ldg(X + i0 * p + e) : 0.f;
-  }
-  for (int e = tid; e < kBob * f; e += 256) {
-    const int r = e / f, j = e - r * f;
-    zbT[j * kBs + r] = r < nobs ? (CT)zbar[i0 * f + e] : (CT)0;
-  }
+  stage_transposed<float>(XsT, p, nobs, [&](int r, int l) { return __ldg(X + (i0 + r) * p + l); });
+  stage_transposed<CT>(zbT, f, nobs, [&](int r, int j) { return (CT)zbar[(i0 + r) * f + j]; });
   __syncthreads();
   for (int cg = warp * 4; cg < p; cg += nw * 4) {  // X rows
     const int l = cg + cl;
@@ -293,20 +311,12 @@ __global__ void __launch_bounds__(256) build_zop_kernel(ZopDims D, const float *
   for (int k0 = 0; k0 < K; k0 += kc) {
     const int k1 = min(K, k0 + kc), nk = k1 - k0;
     __syncthreads();
-    for (int e = tid; e < kBob * nk; e += 256) {
-      const int r = e / nk, kk = e - r * nk;
-      PsT[kk * kBs + r] = r < nobs ? (CT)P[(i0 + r) * K + k0 + kk] : (CT)0;
-    }
+    stage_transposed<CT>(PsT, nk, nobs, [&](int r, int kk) { return (CT)P[(i0 + r) * K + k0 + kk]; });
     if (d)
-      for (int e = tid; e < kBob * nk * d; e += 256) {
-        const int r = e / (nk * d), c = e - r * (nk * d);
-        YsT[c * kBs + r] = r < nobs ? __ldg(Y + ((i0 + r) * K + k0) * d + c) : 0.f;
-      }
-    __syncthreads();
-    for (int e = tid; e < kBob * nk * f; e += 256) {
-      const int r = e / (nk * f), c = e - r * (nk * f), j = c % f;
-      ZcT[c * kBs + r] = r < nobs ? (CT)__ldg(Z + ((i0 + r) * K + k0) * f + c) - zbT[j * kBs + r] : (CT)0;
-    }
+      stage_transposed<float>(YsT, nk * d, nobs, [&](int r, int c) { return __ldg(Y + ((i0 + r) * K + k0) * d + c); });
+    stage_transposed<CT>(ZcT, nk * f, nobs, [&](int r, int c) {
+      return (CT)__ldg(Z + ((i0 + r) * K + k0) * f + c) - zbT[(c % f) * kBs + r];
+    });
     __syncthreads();
     const int ny = (k0 == 0 ? nk - 1 : nk) * d;  // Y rows of classes >= 1 in this chunk
     const int nwz = nk * f;
