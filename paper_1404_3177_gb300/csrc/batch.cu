@@ -373,7 +373,8 @@ void build_pass_lists(const std::vector<Shape> &shapes, int rows, int grid, std:
   for (int i = 0; i < count; ++i) {
     const Shape &s = shapes[i];
     const int64_t nt = (s.N + rows - 1) / rows;
-    const double c = (double)rows * s.K * (s.p + s.d + s.f + 1) + (double)s.nout;
+    // modelled cost of one tile: its arithmetic, its outputs, and a fixed part (staging latency, barriers)
+    const double c = (double)rows * s.K * (s.p + s.d + s.f + 1) + (double)s.nout + 4096.0;
     runs.push_back({i, nt, c});
     total += c * nt;
   }
@@ -635,7 +636,7 @@ int autotune_rows(Engine &E, WorkSet &W, const std::vector<const ProbLayout *> &
   // a scratch copy of the descriptors with theta = delta = 0 and every problem pending
   std::vector<GroupProblem> saved = W.hp;
   for (size_t i = 0; i < W.hp.size(); ++i) { W.hp[i].theta = theta0; W.hp[i].delta = theta0; }
-  static const int cands[] = {8, 16, 32};
+  static const int cands[] = {16, 32, 64};
   float best = 1e30f;
   int best_rows = 16;
   for (int rows : cands) {

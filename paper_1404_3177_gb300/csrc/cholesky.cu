@@ -154,6 +154,7 @@ constexpr int kCtaThreads = 256;
 
 template <typename T, int W>
 __device__ bool cta_cholesky(T *__restrict__ A, int64_t n, T *__restrict__ Ps, T *__restrict__ dinv) {
+  constexpr int PS = W + 1;  // panel row stride: rows of the panel fall in different banks
   __shared__ int bad;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) bad = 0;
@@ -164,26 +165,26 @@ __device__ bool cta_cholesky(T *__restrict__ A, int64_t n, T *__restrict__ Ps, T
     for (int64_t e = tid; e < m * nb; e += blockDim.x) {
       const int k = (int)(e / m);
       const int64_t rr = e % m;
-      Ps[rr * W + k] = A[(j0 + k) * n + j0 + rr];
+      Ps[rr * PS + k] = A[(j0 + k) * n + j0 + rr];
     }
     __syncthreads();
     if (warp == 0) {  // diagonal block, lane = row
       for (int c = 0; c < nb; ++c) {
         T lcc = (T)1;
         if (lane == c) {
-          const T piv = Ps[c * W + c];
+          const T piv = Ps[c * PS + c];
           if (!(piv > (T)0) || !isfinite(piv)) bad = 1;
           else lcc = sqrt(piv);
-          Ps[c * W + c] = lcc;
+          Ps[c * PS + c] = lcc;
           dinv[c] = (T)1 / lcc;
         }
         __syncwarp();
         const T ri = dinv[c];
-        if (lane > c && lane < nb) Ps[lane * W + c] *= ri;
+        if (lane > c && lane < nb) Ps[lane * PS + c] *= ri;
         __syncwarp();
         if (lane > c && lane < nb) {
-          const T lrc = Ps[lane * W + c];
-          for (int cc = c + 1; cc <= lane; ++cc) Ps[lane * W + cc] -= lrc * Ps[cc * W + c];
+          const T lrc = Ps[lane * PS + c];
+          for (int cc = c + 1; cc <= lane; ++cc) Ps[lane * PS + cc] -= lrc * Ps[cc * PS + c];
         }
         __syncwarp();
       }
@@ -192,19 +193,19 @@ __device__ bool cta_cholesky(T *__restrict__ A, int64_t n, T *__restrict__ Ps, T
     for (int64_t rr = nb + tid; rr < m; rr += blockDim.x) {  // rows below: solve against the block
       T x[W];
 #pragma unroll
-      for (int c = 0; c < W; ++c) x[c] = c < nb ? Ps[rr * W + c] : (T)0;
+      for (int c = 0; c < W; ++c) x[c] = c < nb ? Ps[rr * PS + c] : (T)0;
 #pragma unroll
       for (int c = 0; c < W; ++c) {
         if (c < nb) {
           T v = x[c];
 #pragma unroll
-          for (int t = 0; t < c; ++t) v -= x[t] * Ps[c * W + t];
+          for (int t = 0; t < c; ++t) v -= x[t] * Ps[c * PS + t];
           x[c] = v * dinv[c];
         }
       }
 #pragma unroll
       for (int c = 0; c < W; ++c)
-        if (c < nb) Ps[rr * W + c] = x[c];
+        if (c < nb) Ps[rr * PS + c] = x[c];
     }
     __syncthreads();
     // panel back to A: L (lower) and L^T (upper)
@@ -212,7 +213,7 @@ __device__ bool cta_cholesky(T *__restrict__ A, int64_t n, T *__restrict__ Ps, T
       const int k = (int)(e / m);
       const int64_t rr = e % m;
       if (rr >= k) {
-        const T v = Ps[rr * W + k];
+        const T v = Ps[rr * PS + k];
         A[(j0 + k) * n + j0 + rr] = v;
         A[(j0 + rr) * n + j0 + k] = v;
       }
@@ -236,8 +237,8 @@ __device__ bool cta_cholesky(T *__restrict__ A, int64_t n, T *__restrict__ Ps, T
         T a[4], b[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          a[u] = r0 + u < m ? Ps[(r0 + u) * W + k] : (T)0;
-          b[u] = c0 + u < m ? Ps[(c0 + u) * W + k] : (T)0;
+          a[u] = r0 + u < m ? Ps[(r0 + u) * PS + k] : (T)0;
+          b[u] = c0 + u < m ? Ps[(c0 + u) * PS + k] : (T)0;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
@@ -259,23 +260,65 @@ __device__ bool cta_cholesky(T *__restrict__ A, int64_t n, T *__restrict__ Ps, T
   return bad == 0;
 }
 
-// x <- (L L^T)^{-1} x for a factor with L^T in the upper triangle; x in shared memory.
+// x <- (L L^T)^{-1} x for a factor with L^T in the upper triangle; x in shared
+// memory.  Blocks of 32 unknowns: warp 0 solves the diagonal block (lane = row,
+// the block's pivots broadcast by shuffles), then every thread updates the
+// unknowns below (forward) or above (backward) from the block's 32 columns,
+// which are contiguous in the stored factor (L below the diagonal for the
+// forward sweep, L^T above it for the backward one).
 template <typename T, typename V>
 __device__ void cta_chol_solve(const T *__restrict__ A, int64_t n, V *__restrict__ x) {
-  const int tid = threadIdx.x;
-  for (int64_t j = 0; j < n; ++j) {  // forward, one column at a time (n is small)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t nblk = (n + 31) / 32;
+  for (int64_t bb = 0; bb < nblk; ++bb) {  // forward: L y = x
+    const int64_t b0 = bb * 32;
+    const int w = (int)(n - b0 < 32 ? n - b0 : 32);
     __syncthreads();
-    const V xj = x[j] / (V)A[j * n + j];
+    if (warp == 0) {
+      V v = lane < w ? x[b0 + lane] : (V)0;
+      for (int c = 0; c < w; ++c) {
+        const V xc = __shfl_sync(0xffffffffu, v, c) / (V)A[(b0 + c) * n + b0 + c];
+        if (lane == c) v = xc;
+        else if (lane > c && lane < w) v -= (V)A[(b0 + c) * n + b0 + lane] * xc;
+      }
+      if (lane < w) x[b0 + lane] = v;
+    }
     __syncthreads();
-    if (tid == 0) x[j] = xj;
-    for (int64_t r = j + 1 + tid; r < n; r += blockDim.x) x[r] -= (V)A[j * n + r] * xj;
+    for (int64_t r = b0 + w + tid; r < n; r += blockDim.x) {
+      V s0 = (V)0, s1 = (V)0;
+      int c = 0;
+      for (; c + 1 < w; c += 2) {
+        s0 += (V)A[(b0 + c) * n + r] * x[b0 + c];
+        s1 += (V)A[(b0 + c + 1) * n + r] * x[b0 + c + 1];
+      }
+      if (c < w) s0 += (V)A[(b0 + c) * n + r] * x[b0 + c];
+      x[r] -= s0 + s1;
+    }
   }
-  for (int64_t j = n - 1; j >= 0; --j) {  // backward with U = L^T: column j of U lies above the diagonal
+  for (int64_t bb = nblk - 1; bb >= 0; --bb) {  // backward: L^T z = y
+    const int64_t b0 = bb * 32;
+    const int w = (int)(n - b0 < 32 ? n - b0 : 32);
     __syncthreads();
-    const V xj = x[j] / (V)A[j * n + j];
+    if (warp == 0) {
+      V v = lane < w ? x[b0 + lane] : (V)0;
+      for (int c = w - 1; c >= 0; --c) {
+        const V xc = __shfl_sync(0xffffffffu, v, c) / (V)A[(b0 + c) * n + b0 + c];
+        if (lane == c) v = xc;
+        else if (lane < c) v -= (V)A[(b0 + c) * n + b0 + lane] * xc;  // (L^T)(b0+lane, b0+c), above the diagonal
+      }
+      if (lane < w) x[b0 + lane] = v;
+    }
     __syncthreads();
-    if (tid == 0) x[j] = xj;
-    for (int64_t r = tid; r < j; r += blockDim.x) x[r] -= (V)A[j * n + r] * xj;
+    for (int64_t r = tid; r < b0; r += blockDim.x) {
+      V s0 = (V)0, s1 = (V)0;
+      int c = 0;
+      for (; c + 1 < w; c += 2) {
+        s0 += (V)A[(b0 + c) * n + r] * x[b0 + c];
+        s1 += (V)A[(b0 + c + 1) * n + r] * x[b0 + c + 1];
+      }
+      if (c < w) s0 += (V)A[(b0 + c) * n + r] * x[b0 + c];
+      x[r] -= s0 + s1;
+    }
   }
   __syncthreads();
 }
@@ -408,7 +451,7 @@ namespace mnl {
 
 size_t grouped_chol_smem(int64_t nmax) {
   const size_t vec = (((size_t)2 * nmax * sizeof(double) + 15) & ~(size_t)15);
-  const size_t p32 = (size_t)nmax * 32 * sizeof(float), p64 = (size_t)nmax * 16 * sizeof(double);
+  const size_t p32 = (size_t)nmax * 33 * sizeof(float), p64 = (size_t)nmax * 17 * sizeof(double);
   return vec + std::max(p32, p64);
 }
 

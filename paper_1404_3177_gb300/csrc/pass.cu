@@ -551,7 +551,8 @@ GroupedPassPlan plan_grouped_pass(const std::vector<Shape> &shapes, bool fp64, i
   if (!pl.npt || smem > 220 * 1024) return pl;
   pl.rows = rows;
   pl.smem = smem;
-  const int per_sm = (smem <= 100 * 1024 && pl.block == 256) ? 2 : 1;
+  // as many CTAs per SM as shared memory and threads allow (latency hiding for the staged tiles)
+  const int per_sm = std::max(1, std::min<int>(2048 / pl.block, (int)((227 * 1024) / (smem + 1024))));
   pl.grid = num_sms * per_sm;
   pl.ok = true;
   return pl;
