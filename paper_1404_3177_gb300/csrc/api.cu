@@ -87,7 +87,8 @@ int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 // Below this many observations MNL_BF16 forms the Hessian operands in TF32.
 constexpr int64_t kBf16MinRows = 1024;
 // Refinement steps of a mixed solve at most (each skipped once converged).
-constexpr int kRefineIters = 5;
+constexpr int kRefineIters = 5;   // refinement steps per round of launches
+constexpr int kRefineMax = 30;    // refinement steps in all
 // Relative step below which a non-shrinking step means the float32 noise floor.
 constexpr double kNoiseStep = 1e-5;
 
@@ -367,6 +368,18 @@ int step_impl(mnl_handle *h, double *theta, mnl_step_info *info, double gtol, bo
   const double l0 = h->h_scal[kL], labs = h->h_scal[kLabs], ginf = h->h_scal[kGinf];
   if (!std::isfinite(l0) || !std::isfinite(ginf)) return MNL_ERR_NONFINITE;
   loc.solve_mode = h->solve_mode;
+  // A refinement that is still converging (ref[1] == 0) continues, 5 steps at a time, up to kRefineMax.
+  for (int done = kRefineIters; mixed && (h->h_flags[0] & 16) && !(h->h_flags[0] & 8) && h->h_scal[13] == 0.0 &&
+                                done < kRefineMax;
+       done += kRefineIters) {
+    const int clear = ~16;
+    CK(launch_status_and(h->status, clear, h->st));
+    CK(launch_mixed_refine(n, h->F, h->grad, h->delta, h->mwork, h->status, kRefineIters, h->st, &nl));
+    h->launches += nl + 1;
+    CK(cudaMemcpyAsync(h->h_flags, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(h->h_scal + 12, h->ref, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+  }
   if (mixed) loc.refine_steps = (int)h->h_scal[14];
   float t_fallback = 0.f;
   if (mixed && (h->h_flags[0] & (8 | 16))) {

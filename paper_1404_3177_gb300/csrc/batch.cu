@@ -344,8 +344,14 @@ struct WorkSet {
   std::vector<GroupProblem> hp;     // host copy of the descriptors
   std::vector<Shape> shapes;
   DBuf probs, flags, counts, err, segs, seg_start, slot_start, slot_segs, partials;
-  DBuf build_items, z_items, asm_items, maps, units_main, units_band, main_part, band_part, z_part;
+  DBuf build_items, z_items, asm_items, maps, units_main, units_band, main_part, band_part, z_part, chol_list;
   GroupedPassPlan pfull{}, pll{};
+  // per-problem solves by size class (each launch sizes its shared memory for its largest member)
+  struct CholBucket {
+    int offset, count;
+    size_t smem;
+  };
+  std::vector<CholBucket> chol_buckets;
   int n_build = 0, n_z = 0, n_asm = 0, nunits_main = 0, nunits_band = 0;
   size_t build_smem = 0, z_smem = 0, chol_smem = 0;
   int64_t nmax = 0;
@@ -356,7 +362,8 @@ struct WorkSet {
   int *stop() const { return flags.as<int>() + 4 * count; }
   void release() {
     for (DBuf *d : {&probs, &flags, &counts, &err, &segs, &seg_start, &slot_start, &slot_segs, &partials, &build_items,
-                    &z_items, &asm_items, &maps, &units_main, &units_band, &main_part, &band_part, &z_part})
+                    &z_items, &asm_items, &maps, &units_main, &units_band, &main_part, &band_part, &z_part,
+                    &chol_list})
       d->release();
   }
 };
@@ -483,6 +490,25 @@ int ws_build(Engine &E, WorkSet &W, const std::vector<const ProbLayout *> &L, in
   W.z_smem = zsm;
   W.chol_smem = grouped_chol_smem(W.nmax);
   if (bsm > 200 * 1024 || zsm > 200 * 1024 || W.chol_smem > 220 * 1024) return MNL_ERR_UNSUPPORTED;
+  {  // size classes of the per-problem solves, largest first within a class
+    std::vector<int> order;
+    for (int i = 0; i < count; ++i)
+      if (!L[i]->large) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return L[a]->s.n > L[b]->s.n; });
+    static const int64_t bounds[] = {128, 256, 512, kCtaSolveMaxN};
+    W.chol_buckets.clear();
+    size_t at = order.size();  // walk from the smallest
+    int64_t lo = 0;
+    for (int64_t hi : bounds) {
+      size_t from = at;
+      while (from > 0 && L[order[from - 1]]->s.n <= hi) --from;
+      if (from < at) W.chol_buckets.push_back({(int)from, (int)(at - from), grouped_chol_smem(L[order[from]]->s.n)});
+      at = from;
+      lo = hi;
+    }
+    (void)lo;
+    if ((rc = upload(W.chol_list, order, E.st))) return rc;
+  }
   if ((rc = upload(W.build_items, bi, E.st)) || (rc = upload(W.z_items, zi, E.st)) ||
       (rc = upload(W.asm_items, ai, E.st)))
     return rc;
@@ -563,7 +589,11 @@ int enqueue_iteration(Engine &E, WorkSet &W, const mnl_fit_opts &o, bool with_ls
   BCK(launch_grouped_zblocks(E.fp64, P, W.z_items.as<GroupItem>(), W.n_z, W.active(), W.z_smem, W.z_part.p, E.st));
   BCK(launch_grouped_assemble(E.fp64, P, W.asm_items.as<GroupItem>(), W.n_asm, W.active(), W.main_part.p,
                               W.band_part.p, W.z_part.p, E.st));
-  BCK(launch_grouped_chol_solve(E.mixed, P, np, W.active(), 5, W.status(), W.chol_smem, kCtaSolveMaxN, E.st));
+  // up to 30 refinement steps: each gains a factor of about cond(F) * 2^-24, so ill-conditioned problems need
+  // more than a few; the float64 fallback is kept for stagnation and failed float32 factors
+  for (const auto &cb : W.chol_buckets)
+    BCK(launch_grouped_chol_solve(E.mixed, P, W.chol_list.as<int>() + cb.offset, cb.count, W.active(), 30,
+                                  W.status(), cb.smem, kCtaSolveMaxN, E.st));
   if (!with_ls_init) return MNL_OK;
   ls_init_kernel<<<nb, tb, 0, E.st>>>(np, P, W.active(), W.pending(), W.status());
   BCK(cudaGetLastError());

@@ -245,12 +245,21 @@ __device__ bool cta_cholesky(T *__restrict__ A, int64_t n, T *__restrict__ Ps, T
 #pragma unroll
           for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
       }
+      // the 16 old values are loaded before any store (no load waits on a possibly aliasing store)
+      T old[4][4];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const int64_t r = r0 + u, c = c0 + v;
-          if (r < m && c < m && r >= c) A[(j0 + c) * n + j0 + r] -= acc[u][v];
+          old[u][v] = (r < m && c < m && r >= c) ? A[(j0 + c) * n + j0 + r] : (T)0;
+        }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int64_t r = r0 + u, c = c0 + v;
+          if (r < m && c < m && r >= c) A[(j0 + c) * n + j0 + r] = old[u][v] - acc[u][v];
         }
     }
     __syncthreads();
@@ -342,13 +351,14 @@ __device__ double cta_max_abs(const double *v, int64_t n, double *red) {
 // status[b] = MNL_ERR_NOT_PD when -H is not positive definite.
 template <bool MIXED>
 __global__ void __launch_bounds__(kCtaThreads) grouped_chol_solve_kernel(const GroupProblem *__restrict__ probs,
+                                                                         const int *__restrict__ plist,
                                                                          const int *__restrict__ active, int iters,
                                                                          int *__restrict__ status, int64_t max_n) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
   __shared__ float dinv32[32];
   __shared__ double dinv64[16];
-  const int b = blockIdx.x;
+  const int b = plist[blockIdx.x];
   if (active[b] == 0) return;
   const GroupProblem &g = probs[b];
   const int64_t n = g.n;
@@ -455,19 +465,21 @@ size_t grouped_chol_smem(int64_t nmax) {
   return vec + std::max(p32, p64);
 }
 
-cudaError_t launch_grouped_chol_solve(bool mixed, const GroupProblem *probs, int nprob, const int *active,
-                                      int iters, int *status, size_t smem, int64_t max_n, cudaStream_t st) {
+cudaError_t launch_grouped_chol_solve(bool mixed, const GroupProblem *probs, const int *plist, int nprob,
+                                      const int *active, int iters, int *status, size_t smem, int64_t max_n,
+                                      cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
   cudaError_t e;
   if (mixed) {
     if ((e = cudaFuncSetAttribute(grouped_chol_solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)))
       return e;
-    grouped_chol_solve_kernel<true><<<nprob, kCtaThreads, smem, st>>>(probs, active, iters, status, max_n);
+    grouped_chol_solve_kernel<true><<<nprob, kCtaThreads, smem, st>>>(probs, plist, active, iters, status, max_n);
   } else {
     if ((e = cudaFuncSetAttribute(grouped_chol_solve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)))
       return e;
-    grouped_chol_solve_kernel<false><<<nprob, kCtaThreads, smem, st>>>(probs, active, iters, status, max_n);
+    grouped_chol_solve_kernel<false><<<nprob, kCtaThreads, smem, st>>>(probs, plist, active, iters, status, max_n);
   }
   return cudaGetLastError();
 }

@@ -172,8 +172,10 @@ int f64_chunk_rows();
 // Problems with n_theta above max_n are skipped (solved by the multi-CTA path).
 constexpr int64_t kCtaSolveMaxN = 1400;
 size_t grouped_chol_smem(int64_t nmax);
-cudaError_t launch_grouped_chol_solve(bool mixed, const GroupProblem *probs, int nprob, const int *active,
-                                      int iters, int *status, size_t smem, int64_t max_n, cudaStream_t st);
+// One CTA per listed problem (plist[0 .. nprob)), shared memory `smem` sized for the largest listed n.
+cudaError_t launch_grouped_chol_solve(bool mixed, const GroupProblem *probs, const int *plist, int nprob,
+                                      const int *active, int iters, int *status, size_t smem, int64_t max_n,
+                                      cudaStream_t st);
 
 struct GroupedPassPlan {
   int grid, block, rows, npt;
@@ -302,6 +304,11 @@ size_t mixed_solve_bytes(int64_t n);
 double *mixed_solve_ref(void *work, int64_t n);
 cudaError_t launch_mixed_solve(int64_t n, const double *F, float *F32, const double *g, double *delta, void *work,
                                int *status, int *err, int iters, cudaStream_t st, int *launches);
+// status &= mask (device word).
+cudaError_t launch_status_and(int *status, int mask, cudaStream_t st);
+// `iters` more refinement steps after launch_mixed_solve (the caller first clears status bit 16).
+cudaError_t launch_mixed_refine(int64_t n, const double *F, const double *g, double *delta, void *work, int *status,
+                                int iters, cudaStream_t st, int *launches);
 
 // Small FP64 vector kernels.
 cudaError_t launch_axpy_theta(int64_t n, double *theta, const double *delta, const double *tscale, double *scal_out,

@@ -586,6 +586,8 @@ __global__ void refine_check_kernel(const double *ref, int *status) {
   if (ref[1] != 1.0) atomicOr(status, 16);
 }
 
+__global__ void status_and_kernel(int *status, int mask) { atomicAnd(status, mask); }
+
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 int64_t panels(int64_t n) { return (n + kCb - 1) / kCb; }
@@ -684,6 +686,32 @@ cudaError_t launch_mixed_solve(int64_t n, const double *F, float *F32, const dou
   refine_check_kernel<<<1, 1, 0, st>>>(ref, status);
   ++cnt;
   if (launches) *launches = cnt;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_status_and(int *status, int mask, cudaStream_t st) {
+  status_and_kernel<<<1, 1, 0, st>>>(status, mask);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mixed_refine(int64_t n, const double *F, const double *g, double *delta, void *work, int *status,
+                                int iters, cudaStream_t st, int *launches) {
+  const MixedLayout L = mixed_layout(n);
+  unsigned char *w = static_cast<unsigned char *>(work);
+  float *Li = reinterpret_cast<float *>(w + L.li), *y = reinterpret_cast<float *>(w + L.y);
+  float *z = reinterpret_cast<float *>(w + L.z);
+  double *r = reinterpret_cast<double *>(w + L.r), *ref = reinterpret_cast<double *>(w + L.ref);
+  const unsigned gb = (unsigned)((n + 7) / 8);
+  int cnt = 0;
+  for (int it = 0; it < iters; ++it) {
+    gemv_col_kernel<double, double, double, 2><<<gb, 256, 0, st>>>(n, F, delta, r, g, ref);
+    gemv_col_kernel<float, double, float, 0><<<gb, 256, 0, st>>>(n, Li, r, y, nullptr, ref);
+    gemv_col_kernel<float, float, float, 1><<<gb, 256, 0, st>>>(n, Li, y, z, nullptr, ref);
+    refine_update_kernel<<<1, 1024, 0, st>>>(n, z, delta, ref, status, 0);
+    cnt += 4;
+  }
+  refine_check_kernel<<<1, 1, 0, st>>>(ref, status);
+  if (launches) *launches = cnt + 1;
   return cudaGetLastError();
 }
 
