@@ -248,9 +248,14 @@ int run_hessian(mnl_handle *h, cudaEvent_t *ev = nullptr) {
   const Shape &S = h->S;
   const int nmain = (int)h->h_main.size();
   int rc;
+  // class operands (and the Z-block operand's rows, from the same staged blocks)
+  if (S.mc > 0 || h->tcz) {
+    CK(launch_build_operands(S, h->op, h->X, h->Y, h->P, h->At, h->Ad, h->ldn, h->st, h->tcz ? h->Z : nullptr,
+                             h->zbar, h->tcz ? h->Az : nullptr));
+    h->launches += 1;
+  }
+  if ((rc = mark(h, ev ? ev + 0 : nullptr))) return rc;
   if (S.mc > 0) {
-    CK(launch_build_operands(S, h->op, h->X, h->Y, h->P, h->At, h->Ad, h->ldn, h->st));
-    if ((rc = mark(h, ev ? ev + 0 : nullptr))) return rc;
     if (h->fp64) {
       CK(launch_syrk_f64(reinterpret_cast<const double *>(h->At), h->ldn, S.N, h->tl.main, nmain, h->main_split,
                          reinterpret_cast<double *>(h->main_part), h->st));
@@ -264,16 +269,14 @@ int run_hessian(mnl_handle *h, cudaEvent_t *ev = nullptr) {
       CK(launch_syrk_tc(h->op, h->maps, h->units_band, h->nunits_band, nullptr, h->grid_band,
                         reinterpret_cast<float *>(h->band_part), h->err, h->st));
     }
-    h->launches += 3;
-    if ((rc = mark(h, ev ? ev + 2 : nullptr))) return rc;
-  } else {
-    for (int i = 0; i < 3; ++i)
-      if ((rc = mark(h, ev ? ev + i : nullptr))) return rc;
-  }
-  if (S.f > 0 && h->tcz) {
-    CK(launch_build_zop(S, h->op, h->X, h->Y, h->Z, h->P, h->zbar, h->Az, h->ldn, h->st));
-    CK(launch_syrk_tc(h->op, h->maps, h->units_z, h->nunits_z, nullptr, h->grid_z, h->zt_part, h->err, h->st));
     h->launches += 2;
+  } else {
+    if ((rc = mark(h, ev ? ev + 1 : nullptr))) return rc;
+  }
+  if ((rc = mark(h, ev ? ev + 2 : nullptr))) return rc;
+  if (S.f > 0 && h->tcz) {
+    CK(launch_syrk_tc(h->op, h->maps, h->units_z, h->nunits_z, nullptr, h->grid_z, h->zt_part, h->err, h->st));
+    h->launches += 1;
   } else if (S.f > 0) {
     CK(launch_zblocks(S, h->fp64, h->X, h->Y, h->Z, h->P, h->zbar, h->z_split, h->z_part, h->st));
     h->launches += 1;

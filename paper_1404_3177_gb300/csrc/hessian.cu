@@ -103,26 +103,34 @@ struct BuildDims {
   int64_t N, ldn;
   int K, p, d, q;
   int ob;  // observations per block (kBob)
-  int kc;  // classes per Y staging chunk
+  int kc;  // classes per Y (and Z) staging chunk
+  int f;   // Z operand (Az != nullptr): generic columns and its row-block offsets
+  int64_t oY, oW, oZ;
 };
 
 // Shared memory, transposed so that observations are contiguous:
 //   PsT[K][kBs], WsT[K][kBs] (P and sqrt(P(1-P)), compute type),
-//   XsT[p][kBs], YsT[kc*d][kBs] (float32).
+//   XsT[p][kBs], YsT[kc*d][kBs] (float32), and with the Z operand
+//   ZcT[kc*f][kBs], zbT[f][kBs] (z - zbar, zbar; compute type).
 // A warp writes 4 operand rows at a time: lanes 8c..8c+7 take row c of the
 // group, 8 observations each (one 16-byte store per lane and operand for BF16).
+// With Az, the same staged block also gives the rows of the Z-block operand
+// (X, Y, W = P (z - zbar), Zc = z - zbar; see the Z-block section below).
 template <OpType OT, typename PT>
 __device__ __forceinline__ void build_block(const BuildDims &D, const float *__restrict__ X,
                                             const float *__restrict__ Y, const PT *__restrict__ P, void *At,
-                                            void *Ad, int64_t blk) {
+                                            void *Ad, int64_t blk, const float *__restrict__ Z = nullptr,
+                                            const PT *__restrict__ zbar = nullptr, void *Az = nullptr) {
   using CT = typename OpStore<OT>::CT;
   constexpr int esz = OT == OpType::F64 ? 8 : OT == OpType::TF32 ? 4 : 2;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int K = D.K, p = D.p, d = D.d, q = D.q;
+  const int K = D.K, p = D.p, d = D.d, q = D.q, f = Az ? D.f : 0;
   CT *PsT = reinterpret_cast<CT *>(smem);
   CT *WsT = PsT + (size_t)K * kBs;
   float *XsT = reinterpret_cast<float *>(WsT + (size_t)K * kBs);
   float *YsT = XsT + (size_t)p * kBs;
+  CT *ZcT = reinterpret_cast<CT *>(YsT + (size_t)D.kc * d * kBs);
+  CT *zbT = ZcT + (size_t)D.kc * f * kBs;
   const int64_t i0 = blk * kBob;
   const int nobs = (int)min((int64_t)kBob, D.N - i0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -162,12 +170,31 @@ __device__ __forceinline__ void build_block(const BuildDims &D, const float *__r
       }
     }
   }
+  for (int e = tid; e < kBob * f; e += 256) {
+    const int r = e / f, j = e - r * f;
+    zbT[j * kBs + r] = r < nobs ? (CT)zbar[i0 * f + e] : (CT)0;
+  }
 
   const int cl = lane >> 3, oc = (lane & 7) * 8;
   const uint32_t iobs = (uint32_t)(i0 + oc);
-  for (int k0 = 1; k0 < K; k0 += D.kc) {
-    const int k1 = min(K, k0 + D.kc);
-    const int w = (k1 - k0) * d;
+  auto put_z = [&](int64_t row, const CT v[8]) {  // one row of the Z-block operand
+    const uint32_t h = mix3(5u, (uint32_t)row, iobs);
+    OpStore<OT>::put8(reinterpret_cast<unsigned char *>(Az) + (row * D.ldn + i0 + oc) * esz, v, h, remix(h, 1u));
+  };
+  if (Az) {
+    __syncthreads();
+    for (int cg = warp * 4; cg < p; cg += nw * 4) {  // X rows
+      const int l = cg + cl;
+      if (l >= p) continue;
+      CT v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = (CT)XsT[l * kBs + oc + u];
+      put_z(l, v);
+    }
+  }
+  for (int k0 = Az ? 0 : 1; k0 < K; k0 += D.kc) {
+    const int k1 = min(K, k0 + D.kc), nk = k1 - k0;
+    const int w = nk * d;
     __syncthreads();
     if (d) {
       for (int e0 = 0; e0 < kBob * w; e0 += 8 * 256) {
@@ -188,12 +215,33 @@ __device__ __forceinline__ void build_block(const BuildDims &D, const float *__r
         }
       }
     }
+    if (f) {
+      const int wz = nk * f;
+      for (int e0 = 0; e0 < kBob * wz; e0 += 8 * 256) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int e = e0 + tid + u * 256;
+          const int r = e / wz;
+          v[u] = (e < kBob * wz && r < nobs) ? __ldg(Z + ((i0 + r) * K + k0) * f + (e - r * wz)) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int e = e0 + tid + u * 256;
+          if (e < kBob * wz) {
+            const int r = e / wz, c = e - r * wz;
+            ZcT[c * kBs + r] = r < nobs ? (CT)v[u] - zbT[(c % f) * kBs + r] : (CT)0;
+          }
+        }
+      }
+    }
     __syncthreads();
-    const int ncols = (k1 - k0) * q;
+    const int ks = k0 == 0 ? 1 : k0;  // the class operands start at class 1
+    const int ncols = (k1 - ks) * q;
     for (int cg = warp * 4; cg < ncols; cg += nw * 4) {
       const int cc = cg + cl;
       if (cc >= ncols) continue;
-      const int kk = cc / q, l = cc - kk * q, k = k0 + kk;
+      const int kq = cc / q, l = cc - kq * q, k = ks + kq, kk = k - k0;
       const int64_t c = (int64_t)(k - 1) * q + l;
       const float *mrow = l < p ? XsT + l * kBs : YsT + (kk * d + (l - p)) * kBs;
       float m[8];
@@ -214,7 +262,41 @@ __device__ __forceinline__ void build_block(const BuildDims &D, const float *__r
       OpStore<OT>::put8(rowA, pv, h, remix(h, 1u));
       OpStore<OT>::put8(rowD, wv, remix(h, 2u), remix(h, 3u));
     }
+    if (Az) {  // Y rows (classes >= 1), W and Zc rows of this chunk's classes
+      const int ny = (k1 - ks) * d, nwz = nk * f, rows = ny + 2 * nwz;
+      for (int cg = warp * 4; cg < rows; cg += nw * 4) {
+        const int c = cg + cl;
+        if (c >= rows) continue;
+        CT v[8];
+        int64_t row;
+        if (c < ny) {
+          const int kq = c / d, l = c - kq * d, kk = ks + kq - k0;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] = (CT)YsT[(kk * d + l) * kBs + oc + u];
+          row = D.oY + (int64_t)(ks + kq - 1) * d + l;
+        } else if (c < ny + nwz) {
+          const int c2 = c - ny, kk = c2 / f;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] = PsT[(k0 + kk) * kBs + oc + u] * ZcT[c2 * kBs + oc + u];
+          row = D.oW + (int64_t)k0 * f + c2;
+        } else {
+          const int c2 = c - ny - nwz;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] = ZcT[c2 * kBs + oc + u];
+          row = D.oZ + (int64_t)k0 * f + c2;
+        }
+        put_z(row, v);
+      }
+    }
   }
+}
+
+template <OpType OT, typename PT>
+__global__ void __launch_bounds__(256) build_operands_z_kernel(BuildDims D, const float *__restrict__ X,
+                                                               const float *__restrict__ Y, const PT *__restrict__ P,
+                                                               void *At, void *Ad, const float *__restrict__ Z,
+                                                               const PT *__restrict__ zbar, void *Az) {
+  build_block<OT, PT>(D, X, Y, P, At, Ad, blockIdx.x, Z, zbar, Az);
 }
 
 template <OpType OT, typename PT>
@@ -245,107 +327,9 @@ __global__ void __launch_bounds__(256) grouped_build_kernel(const GroupProblem *
 //   W  rows k f + j    P_ik (z_ikj - zbar_ij)     (oW)
 //   Zc rows k f + j    z_ikj - zbar_ij            (oZ)
 // so that C_X = X W^T, C_Y = the class-diagonal blocks of Y W^T and
-// A = sum_k W_k Zc_k^T are tiles of the Gram matrix of this operand.
-// Staging is transposed like the class-operand builder (8 observations per
-// lane, 16-byte stores, stochastic rounding for BF16).
+// A = sum_k W_k Zc_k^T are tiles of the Gram matrix of this operand.  Its rows
+// are written by the class-operand builder from the same staged block.
 // ---------------------------------------------------------------------------
-
-// dst[c * kBs + r] = get(r, c) for r < kBob, c < w (zero for r >= nobs), with 8
-// loads in flight per thread.
-template <typename T, typename Get>
-__device__ __forceinline__ void stage_transposed(T *dst, int w, int nobs, Get get) {
-  const int tot = kBob * w;
-  for (int e0 = 0; e0 < tot; e0 += 8 * 256) {
-    T v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + (int)threadIdx.x + u * 256;
-      const int r = e / w;
-      v[u] = (e < tot && r < nobs) ? get(r, e - r * w) : (T)0;
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + (int)threadIdx.x + u * 256;
-      if (e < tot) {
-        const int r = e / w;
-        dst[(e - r * w) * kBs + r] = v[u];
-      }
-    }
-  }
-}
-
-template <OpType OT, typename PT>
-__global__ void __launch_bounds__(256) build_zop_kernel(ZopDims D, const float *__restrict__ X,
-                                                        const float *__restrict__ Y, const float *__restrict__ Z,
-                                                        const PT *__restrict__ P, const PT *__restrict__ zbar,
-                                                        void *Az) {
-  using CT = typename OpStore<OT>::CT;
-  constexpr int esz = OT == OpType::F64 ? 8 : OT == OpType::TF32 ? 4 : 2;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int K = D.K, p = D.p, d = D.d, f = D.f, kc = D.kc;
-  float *XsT = reinterpret_cast<float *>(smem);                 // [p][kBs]
-  float *YsT = XsT + (size_t)p * kBs;                            // [kc d][kBs]
-  CT *ZcT = reinterpret_cast<CT *>(YsT + (size_t)kc * d * kBs);  // [kc f][kBs]
-  CT *PsT = ZcT + (size_t)kc * f * kBs;                          // [kc][kBs]
-  CT *zbT = PsT + (size_t)kc * kBs;                              // [f][kBs]
-  const int64_t i0 = (int64_t)blockIdx.x * kBob;
-  const int nobs = (int)min((int64_t)kBob, D.N - i0);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  const int cl = lane >> 3, oc = (lane & 7) * 8;
-  const uint32_t iobs = (uint32_t)(i0 + oc);
-  auto put_row = [&](int64_t row, const CT v[8]) {
-    const uint32_t h = mix3(5u, (uint32_t)row, iobs);
-    OpStore<OT>::put8(reinterpret_cast<unsigned char *>(Az) + (row * D.ldn + i0 + oc) * esz, v, h, remix(h, 1u));
-  };
-  stage_transposed<float>(XsT, p, nobs, [&](int r, int l) { return __ldg(X + (i0 + r) * p + l); });
-  stage_transposed<CT>(zbT, f, nobs, [&](int r, int j) { return (CT)zbar[(i0 + r) * f + j]; });
-  __syncthreads();
-  for (int cg = warp * 4; cg < p; cg += nw * 4) {  // X rows
-    const int l = cg + cl;
-    if (l >= p) continue;
-    CT v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = (CT)XsT[l * kBs + oc + u];
-    put_row(l, v);
-  }
-  for (int k0 = 0; k0 < K; k0 += kc) {
-    const int k1 = min(K, k0 + kc), nk = k1 - k0;
-    __syncthreads();
-    stage_transposed<CT>(PsT, nk, nobs, [&](int r, int kk) { return (CT)P[(i0 + r) * K + k0 + kk]; });
-    if (d)
-      stage_transposed<float>(YsT, nk * d, nobs, [&](int r, int c) { return __ldg(Y + ((i0 + r) * K + k0) * d + c); });
-    stage_transposed<CT>(ZcT, nk * f, nobs, [&](int r, int c) {
-      return (CT)__ldg(Z + ((i0 + r) * K + k0) * f + c) - zbT[(c % f) * kBs + r];
-    });
-    __syncthreads();
-    const int ny = (k0 == 0 ? nk - 1 : nk) * d;  // Y rows of classes >= 1 in this chunk
-    const int nwz = nk * f;
-    const int rows = ny + 2 * nwz;
-    for (int cg = warp * 4; cg < rows; cg += nw * 4) {
-      const int c = cg + cl;
-      if (c >= rows) continue;
-      CT v[8];
-      int64_t row;
-      if (c < ny) {  // y_ikl
-        const int kk = (k0 == 0 ? 1 : 0) + c / d, l = c - (c / d) * d;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = (CT)YsT[(kk * d + l) * kBs + oc + u];
-        row = D.oY + (int64_t)(k0 + kk - 1) * d + l;
-      } else if (c < ny + nwz) {  // P_ik (z_ikj - zbar_ij)
-        const int c2 = c - ny, kk = c2 / f;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = PsT[kk * kBs + oc + u] * ZcT[c2 * kBs + oc + u];
-        row = D.oW + (int64_t)k0 * f + c2;
-      } else {  // z_ikj - zbar_ij
-        const int c2 = c - ny - nwz;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = ZcT[c2 * kBs + oc + u];
-        row = D.oZ + (int64_t)k0 * f + c2;
-      }
-      put_row(row, v);
-    }
-  }
-}
 
 // ---------------------------------------------------------------------------
 // FP64 CUDA-core SYRK tile: C[a][b] = sum_i At[a0+a][i] At[b0+b][i], 128 x 128,
@@ -911,24 +895,32 @@ void grid_2d(int64_t rows, int64_t cols, dim3 &grid, dim3 &block) {
 
 }  // namespace
 
-size_t build_smem_bytes(const Shape &s, OpType t, int ob, int kc) {
+size_t build_smem_bytes(const Shape &s, OpType t, int ob, int kc, bool with_z) {
   (void)ob;
   const size_t csz = t == OpType::F64 ? 8 : 4;
-  return (size_t)2 * s.K * kBs * csz + ((size_t)s.p + (size_t)kc * s.d) * kBs * 4;
+  return (size_t)2 * s.K * kBs * csz + ((size_t)s.p + (size_t)kc * s.d) * kBs * 4 +
+         (with_z ? ((size_t)kc * s.f + s.f) * kBs * csz : 0);
 }
 
-void build_blocking(const Shape &s, OpType t, int *ob, int *kc) {
+void build_blocking(const Shape &s, OpType t, int *ob, int *kc, bool with_z) {
   *ob = kBob;
-  *kc = std::max(1, s.K - 1);
-  while (*kc > 1 && build_smem_bytes(s, t, *ob, *kc) > 100 * 1024) *kc = (*kc + 1) / 2;
+  *kc = std::max(1, with_z ? s.K : s.K - 1);
+  while (*kc > 1 && build_smem_bytes(s, t, *ob, *kc, with_z) > 100 * 1024) *kc = (*kc + 1) / 2;
 }
 
 cudaError_t launch_build_operands(const Shape &s, OpType t, const float *X, const float *Y, const void *P, void *At,
-                                  void *Ad, int64_t ldn, cudaStream_t st) {
+                                  void *Ad, int64_t ldn, cudaStream_t st, const float *Z, const void *zbar, void *Az) {
   BuildDims D;
   D.N = s.N; D.ldn = ldn; D.K = s.K; D.p = s.p; D.d = s.d; D.q = s.q;
-  build_blocking(s, t, &D.ob, &D.kc);
-  const size_t smem = build_smem_bytes(s, t, D.ob, D.kc);
+  const bool with_z = Az != nullptr && s.f > 0;
+  build_blocking(s, t, &D.ob, &D.kc, with_z);
+  D.f = with_z ? s.f : 0;
+  D.oY = D.oW = D.oZ = 0;
+  if (with_z) {
+    const ZopLayout L = zop_layout(s);
+    D.oY = L.oY; D.oW = L.oW; D.oZ = L.oZ;
+  }
+  const size_t smem = build_smem_bytes(s, t, D.ob, D.kc, with_z);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   const int blocks = (int)((s.N + D.ob - 1) / D.ob);
   cudaError_t e;
@@ -940,15 +932,29 @@ cudaError_t launch_build_operands(const Shape &s, OpType t, const float *X, cons
       break;
     }
     case OpType::TF32: {
-      auto k = build_operands_kernel<OpType::TF32, float>;
-      if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
-      k<<<blocks, 256, smem, st>>>(D, X, Y, reinterpret_cast<const float *>(P), At, Ad);
+      if (with_z) {
+        auto k = build_operands_z_kernel<OpType::TF32, float>;
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+        k<<<blocks, 256, smem, st>>>(D, X, Y, reinterpret_cast<const float *>(P), At, Ad, Z,
+                                     reinterpret_cast<const float *>(zbar), Az);
+      } else {
+        auto k = build_operands_kernel<OpType::TF32, float>;
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+        k<<<blocks, 256, smem, st>>>(D, X, Y, reinterpret_cast<const float *>(P), At, Ad);
+      }
       break;
     }
     case OpType::BF16: {
-      auto k = build_operands_kernel<OpType::BF16, float>;
-      if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
-      k<<<blocks, 256, smem, st>>>(D, X, Y, reinterpret_cast<const float *>(P), At, Ad);
+      if (with_z) {
+        auto k = build_operands_z_kernel<OpType::BF16, float>;
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+        k<<<blocks, 256, smem, st>>>(D, X, Y, reinterpret_cast<const float *>(P), At, Ad, Z,
+                                     reinterpret_cast<const float *>(zbar), Az);
+      } else {
+        auto k = build_operands_kernel<OpType::BF16, float>;
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+        k<<<blocks, 256, smem, st>>>(D, X, Y, reinterpret_cast<const float *>(P), At, Ad);
+      }
       break;
     }
   }
@@ -1134,43 +1140,6 @@ ZTiles zop_tiles(const Shape &s, const ZopLayout &L) {
   return z;
 }
 
-size_t zop_smem(const Shape &s, OpType t, int kc) {
-  const size_t csz = t == OpType::F64 ? 8 : 4;
-  return ((size_t)s.p + (size_t)kc * s.d) * kBs * 4 + ((size_t)kc * s.f + kc + s.f) * kBs * csz;
-}
-
-int zop_kc(const Shape &s, OpType t) {
-  int kc = std::max(1, s.K);
-  while (kc > 1 && zop_smem(s, t, kc) > 100 * 1024) kc = (kc + 1) / 2;
-  return kc;
-}
-
-cudaError_t launch_build_zop(const Shape &s, OpType t, const float *X, const float *Y, const float *Z, const void *P,
-                             const void *zbar, void *Az, int64_t ldn, cudaStream_t st) {
-  const ZopLayout L = zop_layout(s);
-  ZopDims D;
-  D.N = s.N; D.ldn = ldn; D.oY = L.oY; D.oW = L.oW; D.oZ = L.oZ;
-  D.K = s.K; D.p = s.p; D.d = s.d; D.f = s.f;
-  D.kc = zop_kc(s, t);
-  const size_t smem = zop_smem(s, t, D.kc);
-  if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  const int blocks = (int)((s.N + kBob - 1) / kBob);
-  cudaError_t e;
-  if (t == OpType::TF32) {
-    auto k = build_zop_kernel<OpType::TF32, float>;
-    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
-    k<<<blocks, 256, smem, st>>>(D, X, Y, Z, reinterpret_cast<const float *>(P),
-                                 reinterpret_cast<const float *>(zbar), Az);
-  } else if (t == OpType::BF16) {
-    auto k = build_zop_kernel<OpType::BF16, float>;
-    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
-    k<<<blocks, 256, smem, st>>>(D, X, Y, Z, reinterpret_cast<const float *>(P),
-                                 reinterpret_cast<const float *>(zbar), Az);
-  } else {
-    return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
 
 cudaError_t launch_export_hessian(int64_t n, const double *F, double *H, cudaStream_t st) {
   dim3 grid, block;

@@ -156,8 +156,8 @@ cudaError_t launch_grouped_zblocks(bool fp64, const GroupProblem *probs, const G
 cudaError_t launch_grouped_assemble(bool fp64, const GroupProblem *probs, const GroupItem *items, int nitems,
                                     const int *active, const void *mainp, const void *bandp, const void *zpart,
                                     cudaStream_t st);
-size_t build_smem_bytes(const Shape &s, OpType t, int ob, int kc);
-void build_blocking(const Shape &s, OpType t, int *ob, int *kc);
+size_t build_smem_bytes(const Shape &s, OpType t, int ob, int kc, bool with_z = false);
+void build_blocking(const Shape &s, OpType t, int *ob, int *kc, bool with_z = false);
 int zblocks_parts(const Shape &s, bool fp64);  // CTAs per observation split
 size_t zblocks_smem(const Shape &s, bool fp64);
 constexpr int kAssembleCols = 8;  // columns per grouped-assembly item
@@ -204,8 +204,10 @@ cudaError_t launch_validate(const Shape &s, const float *X, const float *Y, cons
 //   At  [c][i] = P_ik m_ik[l]                   (c = (k-1)q + l)
 //   Ad  [c][i] = sqrt(P_ik (1 - P_ik)) m_ik[l]
 // T = double (FP64), float rounded to TF32 (TF32), or bf16 (BF16).
-cudaError_t launch_build_operands(const Shape &s, OpType t, const float *X, const float *Y, const void *P,
-                                  void *At, void *Ad, int64_t ldn, cudaStream_t st);
+// Class operands At, Ad (and, when Az != nullptr, the rows of the Z-block operand from the same staged block).
+cudaError_t launch_build_operands(const Shape &s, OpType t, const float *X, const float *Y, const void *P, void *At,
+                                  void *Ad, int64_t ldn, cudaStream_t st, const float *Z = nullptr,
+                                  const void *zbar = nullptr, void *Az = nullptr);
 
 // Tile lists (pairs (ti, tj), ti >= tj) of the two contractions.
 struct TileLists {
@@ -260,10 +262,6 @@ struct ZTiles {
   int nt = 0;
 };
 ZTiles zop_tiles(const Shape &s, const ZopLayout &L);
-size_t zop_smem(const Shape &s, OpType t, int kc);
-int zop_kc(const Shape &s, OpType t);
-cudaError_t launch_build_zop(const Shape &s, OpType t, const float *X, const float *Y, const float *Z, const void *P,
-                             const void *zbar, void *Az, int64_t ldn, cudaStream_t st);
 struct ZTileView {
   const float *part = nullptr;  // nullptr: Z blocks come from z_part (CUDA-core kernel)
   int split = 0, npairs = 0, nt = 0;
