@@ -156,7 +156,9 @@ Sizes plan_sizes(const mnl_dims &d, int prec_in, bool owned, int nsm, int *main_
     *band_split = simt_split(*nband, *ldn / 16, nsm);
   } else {
     const int kb = tc_kblocks(prec == MNL_TF32 ? OpType::TF32 : OpType::BF16, *ldn);
-    *main_split = nmain ? tc_pick_split(nmain, kb, nsm) : 1;
+    int nmain256 = 0;  // 256-wide main tiles (rows ti, columns tj, tj + 1 with tj even, tj <= ti)
+    for (int ti = 0; ti < *nt1d; ++ti) nmain256 += ti / 2 + 1;
+    *main_split = nmain ? tc_pick_split(nmain256, kb, nsm) : 1;
     *band_split = *nband ? tc_pick_split(*nband, kb, nsm) : 1;
   }
   z.main_part = (size_t)(*main_split) * nmain * kTile * kTile * csz;
@@ -264,7 +266,7 @@ int run_hessian(mnl_handle *h, cudaEvent_t *ev = nullptr) {
                          h->band_split, reinterpret_cast<double *>(h->band_part), h->st));
     } else {
       CK(launch_syrk_tc(h->op, h->maps, h->units_main, h->nunits_main, nullptr, h->grid_main,
-                        reinterpret_cast<float *>(h->main_part), h->err, h->st));
+                        reinterpret_cast<float *>(h->main_part), h->err, h->st, 256));
       if ((rc = mark(h, ev ? ev + 1 : nullptr))) return rc;
       CK(launch_syrk_tc(h->op, h->maps, h->units_band, h->nunits_band, nullptr, h->grid_band,
                         reinterpret_cast<float *>(h->band_part), h->err, h->st));
@@ -633,11 +635,31 @@ int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *
           w.kb1 = (int)((int64_t)kb * (sp + 1) / nsplit);
           w.out_off = ((int64_t)sp * (int64_t)tiles.size() + (int64_t)t) * kTile * kTile;
           w.flags = 0;
+          w.out_off2 = -1;
           u.push_back(w);
         }
       return u;
     };
-    const std::vector<SyrkUnit> jm = S.mc > 0 ? make_units(h->h_main, h->main_split, 0) : std::vector<SyrkUnit>();
+    // main contraction with 256-wide tiles: B = tiles (2c, 2c + 1), the second half stored when below the diagonal
+    auto make_main_units = [&](int nsplit) {
+      std::vector<SyrkUnit> u;
+      const int64_t nmain = (int64_t)h->h_main.size();
+      auto slot = [](int ti, int tj) { return (int64_t)ti * (ti + 1) / 2 + tj; };
+      for (int sp = 0; sp < nsplit; ++sp)
+        for (int ti = 0; ti < h->nt1d; ++ti)
+          for (int tj = 0; tj <= ti; tj += 2) {
+            SyrkUnit w;
+            w.map = 0; w.problem = 0; w.ti = ti; w.tj = tj;
+            w.kb0 = (int)((int64_t)kb * sp / nsplit);
+            w.kb1 = (int)((int64_t)kb * (sp + 1) / nsplit);
+            w.out_off = ((int64_t)sp * nmain + slot(ti, tj)) * kTile * kTile;
+            w.out_off2 = tj + 1 <= ti ? ((int64_t)sp * nmain + slot(ti, tj + 1)) * kTile * kTile : -1;
+            w.flags = 0;
+            u.push_back(w);
+          }
+      return u;
+    };
+    const std::vector<SyrkUnit> jm = S.mc > 0 ? make_main_units(h->main_split) : std::vector<SyrkUnit>();
     const std::vector<SyrkUnit> jb = S.mc > 0 ? make_units(h->h_band, h->band_split, 1) : std::vector<SyrkUnit>();
     const std::vector<SyrkUnit> jz = h->tcz ? make_units(zt.pairs, h->zt_split, 2) : std::vector<SyrkUnit>();
     h->grid_main = std::min((int)jm.size(), h->nsm);

@@ -57,7 +57,8 @@ inline Shape make_shape(const mnl_dims &d) { return shape_of(d.N, d.K, d.p, d.d,
 // 1 = Ad for the float64 path), problem, output tile (ti, tj), K-block range
 // [kb0, kb1) and the offset of its 128 x 128 output tile.
 // One contraction work unit: tile (ti, tj) of operand map `map` over the
-// K-blocks [kb0, kb1), written at out_off.  flags: kUnitAcc adds into the
+// K-blocks [kb0, kb1), written at out_off (with 256-wide tiles, rows tj and
+// tj + 1 of the B operand, the second half at out_off2).  flags: kUnitAcc adds into the
 // output instead of storing it; kUnitEmpty is a placeholder that every role
 // skips.
 constexpr int kUnitAcc = 1, kUnitEmpty = 2;
@@ -65,6 +66,7 @@ struct SyrkUnit {
   int map, problem, ti, tj, kb0, kb1;
   int64_t out_off;
   int flags;
+  int64_t out_off2;  // 256-wide tiles: offset of the second 128 x 128 half (tile tj + 1), < 0 when not stored
 };
 
 // theta index (class part) -> class k (1..K-1) and local column l (0..q-1).
@@ -239,7 +241,7 @@ int tc_chunk_kblocks(OpType t);
 std::vector<SyrkUnit> schedule_syrk_units(const std::vector<SyrkUnit> &jobs, int grid, int max_kb);
 size_t tc_smem_bytes();
 cudaError_t launch_syrk_tc(OpType t, const CUtensorMap *maps, const SyrkUnit *units, int nunits, const int *active,
-                           int grid, float *out, int *err, cudaStream_t st);
+                           int grid, float *out, int *err, cudaStream_t st, int bn = 128);
 
 // Z blocks (FP32 or FP64 accumulation) per observation split s:
 // out[s][zblocks_outputs()] = [C_X: p*K*f | C_Y: K*d*f | A: f*f] (see hessian.cu).

@@ -34,19 +34,27 @@
 namespace mnl {
 namespace {
 
-constexpr int kStages = 6;
 constexpr int kOpBytes = kTile * 128;        // one operand box: 128 rows x 128 bytes
-constexpr int kStageBytes = 2 * kOpBytes;    // A and B operands
-constexpr int kSmemBytes = kStages * kStageBytes + 256 + 1024;
-constexpr int kTmemCols = 2 * kTile;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 
+// Tile width BN (the MMA's N): 128, or 256 for the main contraction (the B
+// operand is two adjacent 128-row tiles), which halves the shared-memory
+// operand traffic of A per flop.
+template <int BN>
+struct TcCfg {
+  static constexpr int kStages = BN == 128 ? 6 : 4;
+  static constexpr int kStageBytes = kOpBytes * (1 + BN / kTile);  // A and B operands
+  static constexpr int kSmemBytes = kStages * kStageBytes + 256 + 1024;
+  static constexpr int kTmemCols = 2 * BN;                         // two FP32 accumulators
+};
+
 // Instruction descriptors (kind::f16 with BF16 inputs / kind::tf32): FP32
-// accumulator, both operands K-major, N = 128, M = 128.
-constexpr uint32_t kIdescBf16 =
-    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTile >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
-constexpr uint32_t kIdescTf32 =
-    (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTile >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
+// accumulator, both operands K-major, N = BN, M = 128.
+template <bool TF32, int BN>
+constexpr uint32_t idesc() {
+  return (1u << 4) | (TF32 ? (2u << 7) | (2u << 10) : (1u << 7) | (1u << 10)) | ((uint32_t)(BN >> 3) << 17) |
+         ((uint32_t)(kTile >> 4) << 24);
+}
 
 __device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -125,19 +133,19 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
   return d;
 }
 
-template <bool TF32>
+template <bool TF32, int BN>
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
   if (TF32) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(kIdescTf32), "r"(accumulate)
+        "l"(a), "l"(b), "r"(idesc<true, BN>()), "r"(accumulate)
         : "memory");
   } else {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(kIdescBf16), "r"(accumulate)
+        "l"(a), "l"(b), "r"(idesc<false, BN>()), "r"(accumulate)
         : "memory");
   }
 }
@@ -158,13 +166,15 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&v)
 // Error word bits.
 constexpr int kErrProducer = 1, kErrMma = 2, kErrEpilogue = 4, kErrDrain = 8;
 
-template <bool TF32>
+template <bool TF32, int BN>
 __global__ void __launch_bounds__(192, 1) syrk_tc_kernel(const CUtensorMap *__restrict__ maps,
                                                          const SyrkUnit *__restrict__ units, int nunits,
                                                          const int *__restrict__ active, float *__restrict__ out,
                                                          int *__restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  constexpr int kStages = TcCfg<BN>::kStages, kStageBytes = TcCfg<BN>::kStageBytes;
+  constexpr int kTmemCols = TcCfg<BN>::kTmemCols;
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
   uint64_t *empty = full + kStages;
   uint64_t *tfull = empty + kStages;
@@ -210,13 +220,16 @@ __global__ void __launch_bounds__(192, 1) syrk_tc_kernel(const CUtensorMap *__re
         const SyrkUnit w = units[u];
         if (skip(w)) continue;
         const CUtensorMap *map = maps + w.map;
-        const bool diag = w.ti == w.tj;
+        const bool diag = BN == kTile && w.ti == w.tj;  // a 128-wide diagonal tile loads its operand once
         for (int kb = w.kb0; kb < w.kb1; ++kb) {
           if (!wait_bounded(&empty[stage], phase ^ 1u, abort_flag, err, kErrProducer)) { ok = false; break; }
           uint8_t *dst = smem + stage * kStageBytes;
-          mbar_arrive_expect_tx(&full[stage], diag ? kOpBytes : 2 * kOpBytes);
+          mbar_arrive_expect_tx(&full[stage], diag ? kOpBytes : (1 + BN / kTile) * kOpBytes);
           tma_load_2d(map, &full[stage], dst, kb * kBk, w.ti * kTile);
-          if (!diag) tma_load_2d(map, &full[stage], dst + kOpBytes, kb * kBk, w.tj * kTile);
+          if (!diag)
+#pragma unroll
+            for (int h = 0; h < BN / kTile; ++h)  // B: BN / 128 consecutive tiles (zero-filled past the last row)
+              tma_load_2d(map, &full[stage], dst + (1 + h) * kOpBytes, kb * kBk, (w.tj + h) * kTile);
           last_par[stage] = (int)phase;
           if (++stage == kStages) { stage = 0; phase ^= 1u; }
         }
@@ -237,13 +250,13 @@ __global__ void __launch_bounds__(192, 1) syrk_tc_kernel(const CUtensorMap *__re
         const SyrkUnit w = units[u];
         if (skip(w)) continue;
         const int kb0 = w.kb0, kb1 = w.kb1;
-        const bool diag = w.ti == w.tj;
+        const bool diag = BN == kTile && w.ti == w.tj;
         const int b = local & 1;
         ++local;
         if (!wait_bounded(&tempty[b], acc_ph[b] ^ 1u, abort_flag, err, kErrMma)) break;
         acc_ph[b] ^= 1u;
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(b * kTile);
+        const uint32_t d_tmem = tmem_base + (uint32_t)(b * BN);
         for (int kb = kb0; kb < kb1; ++kb) {
           if (!wait_bounded(&full[stage], phase, abort_flag, err, kErrMma)) { ok = false; break; }
           tc_fence_after();
@@ -252,7 +265,7 @@ __global__ void __launch_bounds__(192, 1) syrk_tc_kernel(const CUtensorMap *__re
           const uint64_t ad = sw128_desc(a_addr), bd = sw128_desc(b_addr);
 #pragma unroll
           for (int k = 0; k < 4; ++k)  // 4 x 32 bytes along K inside the 128-byte row
-            tc_mma<TF32>(d_tmem, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), (kb > kb0 || k > 0) ? 1u : 0u);
+            tc_mma<TF32, BN>(d_tmem, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), (kb > kb0 || k > 0) ? 1u : 0u);
           tc_commit(&empty[stage]);
           if (++stage == kStages) { stage = 0; phase ^= 1u; }
         }
@@ -281,21 +294,25 @@ __global__ void __launch_bounds__(192, 1) syrk_tc_kernel(const CUtensorMap *__re
       tc_fence_after();
       // Tile stored transposed: out[col][row], row = MMA M index (operand tile ti).
       // A later chunk of the same job adds into what this thread stored before.
-      float *dst = out + w.out_off + quarter * 32 + lane;
+      // A BN = 256 tile is two 128 x 128 output tiles (out_off, out_off2; out_off2 < 0: not stored).
       const bool acc = (w.flags & kUnitAcc) != 0;
 #pragma unroll 1
-      for (int c0 = 0; c0 < kTile; c0 += 32) {
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        const int64_t o = c0 < kTile ? w.out_off : w.out_off2;
         uint32_t v[32];
-        tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kTile + c0), v);
+        tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c0), v);
+        if (o < 0) continue;
+        const int cl = c0 < kTile ? c0 : c0 - kTile;  // column within its 128 x 128 output tile
+        float *dst = out + o + quarter * 32 + lane;
         if (acc) {
-          float o[32];
+          float prev[32];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) o[j] = dst[(int64_t)(c0 + j) * kTile];
+          for (int j = 0; j < 32; ++j) prev[j] = dst[(int64_t)(cl + j) * kTile];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) dst[(int64_t)(c0 + j) * kTile] = o[j] + __uint_as_float(v[j]);
+          for (int j = 0; j < 32; ++j) dst[(int64_t)(cl + j) * kTile] = prev[j] + __uint_as_float(v[j]);
         } else {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) dst[(int64_t)(c0 + j) * kTile] = __uint_as_float(v[j]);
+          for (int j = 0; j < 32; ++j) dst[(int64_t)(cl + j) * kTile] = __uint_as_float(v[j]);
         }
       }
       tc_fence_before();
@@ -408,22 +425,26 @@ std::vector<SyrkUnit> schedule_syrk_units(const std::vector<SyrkUnit> &jobs, int
   return out;
 }
 
-size_t tc_smem_bytes() { return kSmemBytes; }
+size_t tc_smem_bytes() { return TcCfg<kTile>::kSmemBytes; }
+
+template <bool TF32, int BN>
+cudaError_t launch_tc(const CUtensorMap *maps, const SyrkUnit *units, int nunits, const int *active, int grid,
+                      float *out, int *err, cudaStream_t st) {
+  auto kern = syrk_tc_kernel<TF32, BN>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN>::kSmemBytes);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, 192, TcCfg<BN>::kSmemBytes, st>>>(maps, units, nunits, active, out, err);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_syrk_tc(OpType t, const CUtensorMap *maps, const SyrkUnit *units, int nunits, const int *active,
-                           int grid, float *out, int *err, cudaStream_t st) {
+                           int grid, float *out, int *err, cudaStream_t st, int bn) {
   if (nunits <= 0) return cudaSuccess;
-  cudaError_t e;
-  if (t == OpType::TF32) {
-    if ((e = cudaFuncSetAttribute(syrk_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)))
-      return e;
-    syrk_tc_kernel<true><<<grid, 192, kSmemBytes, st>>>(maps, units, nunits, active, out, err);
-  } else {
-    if ((e = cudaFuncSetAttribute(syrk_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)))
-      return e;
-    syrk_tc_kernel<false><<<grid, 192, kSmemBytes, st>>>(maps, units, nunits, active, out, err);
-  }
-  return cudaGetLastError();
+  if (bn == 256)
+    return t == OpType::TF32 ? launch_tc<true, 256>(maps, units, nunits, active, grid, out, err, st)
+                             : launch_tc<false, 256>(maps, units, nunits, active, grid, out, err, st);
+  return t == OpType::TF32 ? launch_tc<true, 128>(maps, units, nunits, active, grid, out, err, st)
+                           : launch_tc<false, 128>(maps, units, nunits, active, grid, out, err, st);
 }
 
 }  // namespace mnl
