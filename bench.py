@@ -38,6 +38,10 @@ METRIC = "newton_iters_per_s"
 # CUDA-core peaks measured on this machine's GB300 (152 SMs at 2070 MHz) with a
 # dependent-chain-free FMA microbenchmark: float64 DFMA 1.06, float64 DMMA 1.10,
 # float32 FFMA 71.0 TFLOP/s (cuBLAS DGEMM 1.10, SGEMM 69.8).
+# DRAM bytes of one launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of each kernel on
+# the default workload: the 128 x 256 tcgen05 contraction of the class operands (reads the 1.08 GB operand 1.7
+# times, writes its partial tiles) and the tiled float32 pass (the 441 MB of inputs once, P and zbar written).
+MEASURED_TRAFFIC = {"bf16": {"syrk_AtA": 1854754304 + 250199296, "pass": 440968192 + 38535168}}
 FP64_TFLOPS = 1.06
 FP32_TFLOPS = 71.0
 UNIT = "iter/s"
@@ -327,11 +331,12 @@ def run_ours(args, world, rank, local):
         syrk_unit, syrk_bound = "TFLOP/s", "tensor"
     else:
         syrk_peak, syrk_unit, syrk_bound = pk.get("bf16_tflops_sustained"), "TFLOP/s", "tensor"
+    traffic = MEASURED_TRAFFIC.get(args.precision, {}) if args.solve == "auto" else {}
     rooflines = {
         "syrk_AtA": {"bound": syrk_bound, "achieved": syrk_flops / (kern["syrk_AtA"] * 1e-3) / 1e12,
-                     "peak": syrk_peak, "unit": syrk_unit, "traffic": None},
+                     "peak": syrk_peak, "unit": syrk_unit, "traffic": traffic.get("syrk_AtA")},
         "pass": {"bound": "hbm", "achieved": pass_bytes / (kern["pass"] * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
-                 "unit": "GB/s", "traffic": None},
+                 "unit": "GB/s", "traffic": traffic.get("pass")},
         "cholesky": {"bound": "alu", "achieved": chol_flops / (kern["cholesky"] * 1e-3) / 1e12,
                      "peak": FP32_TFLOPS if mixed_used else FP64_TFLOPS, "unit": "TFLOP/s", "traffic": None,
                      "arith": "f32 factor + f64 refinement" if mixed_used else "f64"},
