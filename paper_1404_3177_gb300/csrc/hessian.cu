@@ -22,22 +22,22 @@ namespace {
 // ---------------------------------------------------------------------------
 
 // Rounding of the operands.  TF32 rounds to nearest (cvt.rna).  BF16 rounds
-// stochastically: a random dither is added below the kept bits of the float32
-// value before truncation, so the rounded value is unbiased (to within 2^-8 of
-// a BF16 unit with the 8 dither bits used here).  With round-to-nearest,
-// designs in which many observations share the same P_ik (an intercept-only
-// model, indicator columns) would give every product the same rounding error;
-// unbiased rounding turns that into independent errors that average out over
-// the observations.  The dither is a hash of (column, observation), so results
-// are reproducible.
+// stochastically (the conversion instruction with random bits, 16 per value):
+// the rounded value is unbiased.  With round-to-nearest, designs in which many
+// observations share the same P_ik (an intercept-only model, indicator
+// columns) would give every product the same rounding error; unbiased rounding
+// turns that into independent errors that average out over the observations.
+// The random bits are a hash of (operand, row, observation), so results are
+// reproducible.
 //
-// put8 stores 8 consecutive observations of one operand row (16-byte stores).
+// put8 stores 8 consecutive observations of one operand row (16-byte stores);
+// r holds the random words of the BF16 conversion (one per pair of values).
 template <OpType OT>
 struct OpStore;
 template <>
 struct OpStore<OpType::F64> {
   using CT = double;
-  __device__ static void put8(void *row, const double v[8], uint32_t, uint32_t) {
+  __device__ __forceinline__ static void put8(void *row, const double v[8], uint4) {
     double2 *d = reinterpret_cast<double2 *>(row);
 #pragma unroll
     for (int u = 0; u < 4; ++u) d[u] = make_double2(v[2 * u], v[2 * u + 1]);
@@ -51,31 +51,21 @@ __device__ __forceinline__ float to_tf32(float x) {
 template <>
 struct OpStore<OpType::TF32> {
   using CT = float;
-  __device__ static void put8(void *row, const float v[8], uint32_t, uint32_t) {
+  __device__ __forceinline__ static void put8(void *row, const float v[8], uint4) {
     float4 *d = reinterpret_cast<float4 *>(row);
     d[0] = make_float4(to_tf32(v[0]), to_tf32(v[1]), to_tf32(v[2]), to_tf32(v[3]));
     d[1] = make_float4(to_tf32(v[4]), to_tf32(v[5]), to_tf32(v[6]), to_tf32(v[7]));
   }
 };
-// Byte b of w placed in bits 8..15 (zero elsewhere): the dither of one value.
-__device__ __forceinline__ uint32_t dither(uint32_t w, int b) {
-  uint32_t r;
-  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(w), "r"(0u), "r"(0x4404u | ((uint32_t)b << 4)));
-  return r;
-}
 template <>
 struct OpStore<OpType::BF16> {
   using CT = float;
-  // w0, w1: 8 random bytes, one per value.
-  __device__ static void put8(void *row, const float v[8], uint32_t w0, uint32_t w1) {
+  __device__ __forceinline__ static void put8(void *row, const float v[8], uint4 r) {
+    const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
     uint32_t o[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const uint32_t w = u < 2 ? w0 : w1;
-      const uint32_t ua = __float_as_uint(v[2 * u]) + dither(w, (2 * u) & 3);
-      const uint32_t ub = __float_as_uint(v[2 * u + 1]) + dither(w, (2 * u + 1) & 3);
-      o[u] = (ua >> 16) | (ub & 0xFFFF0000u);
-    }
+    for (int u = 0; u < 4; ++u)  // o[u] = bf16(v[2u + 1]) << 16 | bf16(v[2u])
+      asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(o[u]) : "f"(v[2 * u + 1]), "f"(v[2 * u]), "r"(rr[u]));
     *reinterpret_cast<uint4 *>(row) = make_uint4(o[0], o[1], o[2], o[3]);
   }
 };
@@ -86,13 +76,42 @@ __device__ __forceinline__ uint32_t mix3(uint32_t s, uint32_t c, uint32_t i) {
   h = (h ^ (h >> 16)) * 0x7FEB352Du;
   return h ^ (h >> 15);
 }
-__device__ __forceinline__ uint32_t remix(uint32_t h, uint32_t k) {
-  uint32_t w = (h ^ (k * 0x9E3779B9u)) * 0x85EBCA6Bu;
-  return w ^ (w >> 13);
+// Four random words (for 8 BF16 conversions) from one hash value.
+__device__ __forceinline__ uint32_t word_of(uint32_t h, uint32_t u) {
+  const uint32_t w = (h + u * 0x9E3779B9u) * 0x85EBCA6Bu;
+  return w ^ (w >> 15);
+}
+__device__ __forceinline__ uint4 words4(uint32_t h) {
+  return make_uint4(word_of(h, 0u), word_of(h, 1u), word_of(h, 2u), word_of(h, 3u));
+}
+
+// Exact x / d (x + d < 2^32) by a multiply-high and one correction step.
+struct FastDiv {
+  uint32_t d, m;
+  __device__ explicit FastDiv(uint32_t dd) : d(dd), m(0xFFFFFFFFu / (dd ? dd : 1u)) {}
+  __device__ __forceinline__ uint32_t div(uint32_t x) const {
+    const uint32_t t = __umulhi(x, m);
+    return t + ((t + 1u) * d <= x ? 1u : 0u);
+  }
+};
+
+// 8 consecutive shared-memory values (16-byte aligned).
+__device__ __forceinline__ void lds8(const float *p, float v[8]) {
+  const float4 a = reinterpret_cast<const float4 *>(p)[0], b = reinterpret_cast<const float4 *>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void lds8(const double *p, double v[8]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[u];
+    v[2 * u] = a.x;
+    v[2 * u + 1] = a.y;
+  }
 }
 
 constexpr int kBob = 64;        // observations per builder block (8 lanes x 8)
 constexpr int kBs = kBob + 4;   // shared row stride (16-byte aligned rows)
+constexpr int kStage = 16;      // staging loads in flight per thread
 
 struct ZopDims {
   int64_t N, ldn, oY, oW, oZ;
@@ -134,82 +153,87 @@ __device__ __forceinline__ void build_block(const BuildDims &D, const float *__r
   const int64_t i0 = blk * kBob;
   const int nobs = (int)min((int64_t)kBob, D.N - i0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const FastDiv divK((uint32_t)K), divp((uint32_t)p), divq((uint32_t)q), divd((uint32_t)d), divf((uint32_t)f);
 
-  // staging, 8 loads in flight per thread
-  for (int e0 = 0; e0 < kBob * K; e0 += 8 * 256) {
-    PT v[8];
+  // staging, kStage loads in flight per thread
+  for (int e0 = 0; e0 < kBob * K; e0 += kStage * 256) {
+    PT v[kStage];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < kStage; ++u) {
       const int e = e0 + tid + u * 256;
-      v[u] = (e < kBob * K && e / K < nobs) ? P[i0 * K + e] : (PT)0;
+      v[u] = (e < kBob * K && (int)divK.div(e) < nobs) ? P[i0 * K + e] : (PT)0;
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < kStage; ++u) {
       const int e = e0 + tid + u * 256;
       if (e < kBob * K) {
-        const int r = e / K, k = e - r * K;
+        const int r = divK.div(e), k = e - r * K;
         const CT pk = (CT)v[u], w = pk * ((CT)1 - pk);
         PsT[k * kBs + r] = pk;
         WsT[k * kBs + r] = w > (CT)0 ? sqrt(w) : (CT)0;
       }
     }
   }
-  for (int e0 = 0; e0 < kBob * p; e0 += 8 * 256) {
-    float v[8];
+  for (int e0 = 0; e0 < kBob * p; e0 += kStage * 256) {
+    float v[kStage];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < kStage; ++u) {
       const int e = e0 + tid + u * 256;
-      v[u] = (e < kBob * p && e / p < nobs) ? __ldg(X + i0 * p + e) : 0.f;
+      v[u] = (e < kBob * p && (int)divp.div(e) < nobs) ? __ldg(X + i0 * p + e) : 0.f;
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < kStage; ++u) {
       const int e = e0 + tid + u * 256;
       if (e < kBob * p) {
-        const int r = e / p, l = e - r * p;
+        const int r = divp.div(e), l = e - r * p;
         XsT[l * kBs + r] = v[u];
       }
     }
   }
   for (int e = tid; e < kBob * f; e += 256) {
-    const int r = e / f, j = e - r * f;
+    const int r = divf.div(e), j = e - r * f;
     zbT[j * kBs + r] = r < nobs ? (CT)zbar[i0 * f + e] : (CT)0;
   }
 
   const int cl = lane >> 3, oc = (lane & 7) * 8;
   const uint32_t iobs = (uint32_t)(i0 + oc);
+  constexpr bool kRand = OT == OpType::BF16;
   auto put_z = [&](int64_t row, const CT v[8]) {  // one row of the Z-block operand
-    const uint32_t h = mix3(5u, (uint32_t)row, iobs);
-    OpStore<OT>::put8(reinterpret_cast<unsigned char *>(Az) + (row * D.ldn + i0 + oc) * esz, v, h, remix(h, 1u));
+    const uint4 rw = kRand ? words4(mix3(5u, (uint32_t)row, iobs)) : make_uint4(0u, 0u, 0u, 0u);
+    OpStore<OT>::put8(reinterpret_cast<unsigned char *>(Az) + (row * D.ldn + i0 + oc) * esz, v, rw);
   };
   if (Az) {
     __syncthreads();
     for (int cg = warp * 4; cg < p; cg += nw * 4) {  // X rows
       const int l = cg + cl;
       if (l >= p) continue;
+      float m[8];
       CT v[8];
+      lds8(XsT + l * kBs + oc, m);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = (CT)XsT[l * kBs + oc + u];
+      for (int u = 0; u < 8; ++u) v[u] = (CT)m[u];
       put_z(l, v);
     }
   }
   for (int k0 = Az ? 0 : 1; k0 < K; k0 += D.kc) {
     const int k1 = min(K, k0 + D.kc), nk = k1 - k0;
     const int w = nk * d;
+    const FastDiv divw((uint32_t)w), divwz((uint32_t)(nk * f));
     __syncthreads();
     if (d) {
-      for (int e0 = 0; e0 < kBob * w; e0 += 8 * 256) {
-        float v[8];
+      for (int e0 = 0; e0 < kBob * w; e0 += kStage * 256) {
+        float v[kStage];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < kStage; ++u) {
           const int e = e0 + tid + u * 256;
-          const int r = e / w;
+          const int r = divw.div(e);
           v[u] = (e < kBob * w && r < nobs) ? __ldg(Y + ((i0 + r) * K + k0) * d + (e - r * w)) : 0.f;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < kStage; ++u) {
           const int e = e0 + tid + u * 256;
           if (e < kBob * w) {
-            const int r = e / w;
+            const int r = divw.div(e);
             YsT[(e - r * w) * kBs + r] = v[u];
           }
         }
@@ -217,20 +241,20 @@ __device__ __forceinline__ void build_block(const BuildDims &D, const float *__r
     }
     if (f) {
       const int wz = nk * f;
-      for (int e0 = 0; e0 < kBob * wz; e0 += 8 * 256) {
-        float v[8];
+      for (int e0 = 0; e0 < kBob * wz; e0 += kStage * 256) {
+        float v[kStage];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < kStage; ++u) {
           const int e = e0 + tid + u * 256;
-          const int r = e / wz;
+          const int r = divwz.div(e);
           v[u] = (e < kBob * wz && r < nobs) ? __ldg(Z + ((i0 + r) * K + k0) * f + (e - r * wz)) : 0.f;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < kStage; ++u) {
           const int e = e0 + tid + u * 256;
           if (e < kBob * wz) {
-            const int r = e / wz, c = e - r * wz;
-            ZcT[c * kBs + r] = r < nobs ? (CT)v[u] - zbT[(c % f) * kBs + r] : (CT)0;
+            const int r = divwz.div(e), c = e - r * wz;
+            ZcT[c * kBs + r] = r < nobs ? (CT)v[u] - zbT[(c - (int)divf.div(c) * f) * kBs + r] : (CT)0;
           }
         }
       }
@@ -241,26 +265,30 @@ __device__ __forceinline__ void build_block(const BuildDims &D, const float *__r
     for (int cg = warp * 4; cg < ncols; cg += nw * 4) {
       const int cc = cg + cl;
       if (cc >= ncols) continue;
-      const int kq = cc / q, l = cc - kq * q, k = ks + kq, kk = k - k0;
+      const int kq = divq.div(cc), l = cc - kq * q, k = ks + kq, kk = k - k0;
       const int64_t c = (int64_t)(k - 1) * q + l;
       const float *mrow = l < p ? XsT + l * kBs : YsT + (kk * d + (l - p)) * kBs;
       float m[8];
-      CT pv[8], wv[8];
-      {
-        const float4 a = *reinterpret_cast<const float4 *>(mrow + oc);
-        const float4 b = *reinterpret_cast<const float4 *>(mrow + oc + 4);
-        m[0] = a.x; m[1] = a.y; m[2] = a.z; m[3] = a.w; m[4] = b.x; m[5] = b.y; m[6] = b.z; m[7] = b.w;
-      }
+      CT pk[8], wk[8], pv[8], wv[8];
+      lds8(mrow + oc, m);
+      lds8(PsT + k * kBs + oc, pk);
+      lds8(WsT + k * kBs + oc, wk);
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        pv[u] = PsT[k * kBs + oc + u] * (CT)m[u];
-        wv[u] = WsT[k * kBs + oc + u] * (CT)m[u];
+        pv[u] = pk[u] * (CT)m[u];
+        wv[u] = wk[u] * (CT)m[u];
       }
-      const uint32_t h = mix3(1u, (uint32_t)c, iobs);
+      uint4 ra = make_uint4(0u, 0u, 0u, 0u), rd = ra;
+      if (kRand) {
+        ra = words4(mix3(1u, (uint32_t)c, iobs));
+        // Ad takes the other halves of the same words
+        rd = make_uint4(__funnelshift_l(ra.x, ra.x, 16), __funnelshift_l(ra.y, ra.y, 16),
+                        __funnelshift_l(ra.z, ra.z, 16), __funnelshift_l(ra.w, ra.w, 16));
+      }
       unsigned char *rowA = reinterpret_cast<unsigned char *>(At) + (c * D.ldn + i0 + oc) * esz;
       unsigned char *rowD = reinterpret_cast<unsigned char *>(Ad) + (c * D.ldn + i0 + oc) * esz;
-      OpStore<OT>::put8(rowA, pv, h, remix(h, 1u));
-      OpStore<OT>::put8(rowD, wv, remix(h, 2u), remix(h, 3u));
+      OpStore<OT>::put8(rowA, pv, ra);
+      OpStore<OT>::put8(rowD, wv, rd);
     }
     if (Az) {  // Y rows (classes >= 1), W and Zc rows of this chunk's classes
       const int ny = (k1 - ks) * d, nwz = nk * f, rows = ny + 2 * nwz;
@@ -270,19 +298,23 @@ __device__ __forceinline__ void build_block(const BuildDims &D, const float *__r
         CT v[8];
         int64_t row;
         if (c < ny) {
-          const int kq = c / d, l = c - kq * d, kk = ks + kq - k0;
+          const int kq = divd.div(c), l = c - kq * d, kk = ks + kq - k0;
+          float m[8];
+          lds8(YsT + (kk * d + l) * kBs + oc, m);
 #pragma unroll
-          for (int u = 0; u < 8; ++u) v[u] = (CT)YsT[(kk * d + l) * kBs + oc + u];
+          for (int u = 0; u < 8; ++u) v[u] = (CT)m[u];
           row = D.oY + (int64_t)(ks + kq - 1) * d + l;
         } else if (c < ny + nwz) {
-          const int c2 = c - ny, kk = c2 / f;
+          const int c2 = c - ny, kk = divf.div(c2);
+          CT pk[8], zc[8];
+          lds8(PsT + (k0 + kk) * kBs + oc, pk);
+          lds8(ZcT + c2 * kBs + oc, zc);
 #pragma unroll
-          for (int u = 0; u < 8; ++u) v[u] = PsT[(k0 + kk) * kBs + oc + u] * ZcT[c2 * kBs + oc + u];
+          for (int u = 0; u < 8; ++u) v[u] = pk[u] * zc[u];
           row = D.oW + (int64_t)k0 * f + c2;
         } else {
           const int c2 = c - ny - nwz;
-#pragma unroll
-          for (int u = 0; u < 8; ++u) v[u] = ZcT[c2 * kBs + oc + u];
+          lds8(ZcT + c2 * kBs + oc, v);
           row = D.oZ + (int64_t)k0 * f + c2;
         }
         put_z(row, v);
@@ -902,10 +934,16 @@ size_t build_smem_bytes(const Shape &s, OpType t, int ob, int kc, bool with_z) {
          (with_z ? ((size_t)kc * s.f + s.f) * kBs * csz : 0);
 }
 
+// Classes per staging chunk: the most that keep three blocks on an SM (so that
+// one block's staging overlaps the others' stores), else two, else one.
 void build_blocking(const Shape &s, OpType t, int *ob, int *kc, bool with_z) {
   *ob = kBob;
-  *kc = std::max(1, with_z ? s.K : s.K - 1);
-  while (*kc > 1 && build_smem_bytes(s, t, *ob, *kc, with_z) > 100 * 1024) *kc = (*kc + 1) / 2;
+  const int kmax = std::max(1, with_z ? s.K : s.K - 1);
+  for (const size_t cap : {(size_t)74 * 1024, (size_t)112 * 1024, (size_t)200 * 1024}) {
+    *kc = kmax;
+    while (*kc > 1 && build_smem_bytes(s, t, *ob, *kc, with_z) > cap) --*kc;
+    if (build_smem_bytes(s, t, *ob, *kc, with_z) <= cap) return;
+  }
 }
 
 cudaError_t launch_build_operands(const Shape &s, OpType t, const float *X, const float *Y, const void *P, void *At,
