@@ -262,17 +262,26 @@ __device__ __forceinline__ void build_block(const BuildDims &D, const float *__r
     __syncthreads();
     const int ks = k0 == 0 ? 1 : k0;  // the class operands start at class 1
     const int ncols = (k1 - ks) * q;
-    for (int cg = warp * 4; cg < ncols; cg += nw * 4) {
+    // each warp takes a contiguous range of columns, so that a lane keeps the
+    // P and sqrt(P(1-P)) values of its class in registers until the class changes
+    const int per = ((ncols + nw - 1) / nw + 3) & ~3;
+    const int cbeg = warp * per, cend = min(ncols, cbeg + per);
+    int kcur = -1;
+    CT pk[8], wk[8];
+    for (int cg = cbeg; cg < cend; cg += 4) {
       const int cc = cg + cl;
-      if (cc >= ncols) continue;
+      if (cc >= cend) continue;
       const int kq = divq.div(cc), l = cc - kq * q, k = ks + kq, kk = k - k0;
       const int64_t c = (int64_t)(k - 1) * q + l;
       const float *mrow = l < p ? XsT + l * kBs : YsT + (kk * d + (l - p)) * kBs;
       float m[8];
-      CT pk[8], wk[8], pv[8], wv[8];
+      CT pv[8], wv[8];
       lds8(mrow + oc, m);
-      lds8(PsT + k * kBs + oc, pk);
-      lds8(WsT + k * kBs + oc, wk);
+      if (k != kcur) {
+        lds8(PsT + k * kBs + oc, pk);
+        lds8(WsT + k * kBs + oc, wk);
+        kcur = k;
+      }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         pv[u] = pk[u] * (CT)m[u];
@@ -324,7 +333,7 @@ __device__ __forceinline__ void build_block(const BuildDims &D, const float *__r
 }
 
 template <OpType OT, typename PT>
-__global__ void __launch_bounds__(256) build_operands_z_kernel(BuildDims D, const float *__restrict__ X,
+__global__ void __launch_bounds__(256, 3) build_operands_z_kernel(BuildDims D, const float *__restrict__ X,
                                                                const float *__restrict__ Y, const PT *__restrict__ P,
                                                                void *At, void *Ad, const float *__restrict__ Z,
                                                                const PT *__restrict__ zbar, void *Az) {
@@ -332,7 +341,7 @@ __global__ void __launch_bounds__(256) build_operands_z_kernel(BuildDims D, cons
 }
 
 template <OpType OT, typename PT>
-__global__ void __launch_bounds__(256) build_operands_kernel(BuildDims D, const float *__restrict__ X,
+__global__ void __launch_bounds__(256, 3) build_operands_kernel(BuildDims D, const float *__restrict__ X,
                                                              const float *__restrict__ Y,
                                                              const PT *__restrict__ P, void *At, void *Ad) {
   build_block<OT, PT>(D, X, Y, P, At, Ad, blockIdx.x);
@@ -817,9 +826,32 @@ __global__ void __launch_bounds__(kZThreads) grouped_zblocks_kernel(const GroupP
 __device__ __forceinline__ double zop_entry(const ZTileView &zv, int64_t a, int64_t b) {
   const int pair = zv.index[(a / kTile) * zv.nt + (b / kTile)];
   const int64_t within = (b % kTile) * kTile + (a % kTile);  // tiles are stored [b][a]
-  double v = 0.0;
-  for (int s = 0; s < zv.split; ++s) v += (double)zv.part[((int64_t)s * zv.npairs + pair) * kTile * kTile + within];
-  return v;
+  float v = 0.f;
+  for (int s = 0; s < zv.split; ++s) v += zv.part[((int64_t)s * zv.npairs + pair) * kTile * kTile + within];
+  return (double)v;
+}
+
+// Class and local index of a class coefficient (theta index a < mc), 32-bit.
+__device__ __forceinline__ void class_local32(const Shape &S, int a, int &k, int &l) {
+  if (a < (int)S.nb) {
+    k = a / S.p;
+    l = a - k * S.p;
+    ++k;
+  } else {
+    const int r = a - (int)S.nb;
+    k = r / S.d;
+    l = S.p + (r - k * S.d);
+    ++k;
+  }
+}
+
+// Sum over the splits of one partial entry: float32 partials are summed in
+// float32 (a few terms; relative error ~1e-7), float64 ones in float64.
+template <typename CT>
+__device__ __forceinline__ double split_sum(const CT *__restrict__ base, int nsplit, int64_t stride) {
+  CT v = (CT)0;
+  for (int s = 0; s < nsplit; ++s) v += base[(int64_t)s * stride];
+  return (double)v;
 }
 
 template <typename CT, typename ZT>
@@ -833,19 +865,18 @@ __device__ __forceinline__ double assemble_entry(const Shape &S, const CT *__res
   double v = 0.0;
   if (r < S.mc) {
     int kr, lr, kc, lc;
-    theta_class_local(S, r, kr, lr);
-    theta_class_local(S, c, kc, lc);
-    const int64_t ar = (int64_t)(kr - 1) * q + lr, ac = (int64_t)(kc - 1) * q + lc;
-    const int64_t ahi = ar > ac ? ar : ac, alo = ar > ac ? ac : ar;
-    const int ti = (int)(ahi / kTile), tj = (int)(alo / kTile);
-    const int64_t within = (alo % kTile) * kTile + (ahi % kTile);  // tiles are stored [b][a]
+    class_local32(S, (int)r, kr, lr);
+    class_local32(S, (int)c, kc, lc);
+    const int ar = (kr - 1) * q + lr, ac = (kc - 1) * q + lc;
+    const int ahi = ar > ac ? ar : ac, alo = ar > ac ? ac : ar;
+    const int ti = ahi / kTile, tj = alo / kTile;
+    const int within = (alo % kTile) * kTile + (ahi % kTile);  // tiles are stored [b][a]
     if (kr != kc) {
       const int64_t idx = (int64_t)ti * (ti + 1) / 2 + tj;
-      for (int s = 0; s < msplit; ++s) v -= (double)mainp[((int64_t)s * nmain + idx) * kTile * kTile + within];
-    } else {
-      const int b = band_of[ti * nt1d + tj];
-      for (int s = 0; s < bsplit; ++s) v += (double)bandp[((int64_t)s * nband + b) * kTile * kTile + within];
+      return -split_sum<CT>(mainp + idx * kTile * kTile + within, msplit, (int64_t)nmain * kTile * kTile);
     }
+    const int b = band_of[ti * nt1d + tj];
+    return split_sum<CT>(bandp + (int64_t)b * kTile * kTile + within, bsplit, (int64_t)nband * kTile * kTile);
   } else if (c < S.mc) {
     const int j = (int)(r - S.mc);
     int kc, lc;
@@ -869,18 +900,34 @@ __device__ __forceinline__ double assemble_entry(const Shape &S, const CT *__res
   return v;
 }
 
+// Tiled assembly: one CTA per 32 x 32 tile (ti >= tj) of the lower triangle,
+// one entry per thread.  The entries are written column by column (coalesced)
+// and, through a transpose in shared memory, into the mirror tile row by row
+// (coalesced too).
 template <typename CT, typename ZT>
-__global__ void assemble_kernel(Shape S, const CT *__restrict__ mainp, int msplit, int nmain,
-                                const CT *__restrict__ bandp, int bsplit, int nband, const int *__restrict__ band_of,
-                                int nt1d, const ZT *__restrict__ zp, int zsplit, ZTileView zv, double *__restrict__ F) {
+__global__ void __launch_bounds__(1024, 2) assemble_tiles_kernel(Shape S, const CT *__restrict__ mainp, int msplit,
+                                                                 int nmain, const CT *__restrict__ bandp, int bsplit,
+                                                                 int nband, const int *__restrict__ band_of, int nt1d,
+                                                                 const ZT *__restrict__ zp, int zsplit, ZTileView zv,
+                                                                 double *__restrict__ F) {
+  __shared__ double tile[32][33];  // tile[c - c0][r - r0]
   const int64_t n = S.n;
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t c = blockIdx.y + (int64_t)gridDim.y * blockIdx.z;
-  if (r >= n || c >= n || r < c) return;  // (r, c) in the lower triangle; both mirror entries are written
-  const double v = assemble_entry<CT, ZT>(S, mainp, msplit, nmain, bandp, bsplit, nband, band_of, nt1d, zp, zsplit,
-                                          r, c, zv);
-  F[c * n + r] = v;
-  F[r * n + c] = v;
+  const int t = (int)blockIdx.x;
+  int ti = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+  while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+  while (ti * (ti + 1) / 2 > t) --ti;
+  const int tj = t - ti * (ti + 1) / 2;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t r0 = (int64_t)ti * 32, c0 = (int64_t)tj * 32, r = r0 + tx, c = c0 + ty;
+  double v = 0.0;
+  if (r < n && c < n && r >= c) {
+    v = assemble_entry<CT, ZT>(S, mainp, msplit, nmain, bandp, bsplit, nband, band_of, nt1d, zp, zsplit, r, c, zv);
+    F[c * n + r] = v;
+  }
+  tile[ty][tx] = v;
+  __syncthreads();
+  const int64_t rr = r0 + ty, cc = c0 + tx;  // F(c, r) = F(r, c) for r > c: row r0 + ty, columns c0 + tx
+  if (rr < n && cc < n && rr > cc) F[rr * n + cc] = tile[tx][ty];
 }
 
 // Grouped assembly: item = (problem, block of kAssembleCols columns); the
@@ -1122,17 +1169,18 @@ cudaError_t launch_zblocks(const Shape &s, bool fp64, const float *X, const floa
 }
 
 cudaError_t launch_assemble(const Shape &s, const AssembleIO &io, int nmain, double *F, cudaStream_t st) {
-  dim3 grid, block;
-  grid_2d(s.n, s.n, grid, block);
+  const int64_t nt = (s.n + 31) / 32;
+  const unsigned grid = (unsigned)(nt * (nt + 1) / 2);
+  const int block = 1024;
   const TileLists &tl = *io.tl;
   const int nt1d = (int)((s.mc + kTile - 1) / kTile);
   if (io.fp64) {
-    assemble_kernel<double, double><<<grid, block, 0, st>>>(
+    assemble_tiles_kernel<double, double><<<grid, block, 0, st>>>(
         s, reinterpret_cast<const double *>(io.main_part), io.main_split, nmain,
         reinterpret_cast<const double *>(io.band_part), io.band_split, tl.nband, tl.band_of, nt1d,
         reinterpret_cast<const double *>(io.z_part), io.z_split, io.zt, F);
   } else {
-    assemble_kernel<float, float><<<grid, block, 0, st>>>(
+    assemble_tiles_kernel<float, float><<<grid, block, 0, st>>>(
         s, reinterpret_cast<const float *>(io.main_part), io.main_split, nmain,
         reinterpret_cast<const float *>(io.band_part), io.band_split, tl.nband, tl.band_of, nt1d,
         reinterpret_cast<const float *>(io.z_part), io.z_split, io.zt, F);

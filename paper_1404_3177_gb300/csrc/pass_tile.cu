@@ -10,7 +10,9 @@
 //     mbarrier) into a ring of 2-3 shared-memory stages, so the next tiles
 //     load while the current one is used (the last, partial tile is loaded
 //     with plain loads);
-//   * X is transposed in shared memory (Xt[l][r]) so that a warp reads RPW
+//   * X is transposed in shared memory (column l at Xt + xcol(l), rows
+//     contiguous; groups of 4 columns padded so that the gradient's 16-byte
+//     reads of 8 column groups hit distinct banks) so that a warp reads RPW
 //     rows of one column in one broadcast load; warp w forms the utilities of
 //     rows RPW w .. RPW w + RPW - 1 with lanes over alternatives;
 //   * the residuals r_ik = I(y_i = k) - P_ik are kept transposed (Rt[k][r]) and
@@ -37,6 +39,7 @@ constexpr uint64_t kTileWaitNs = 2000000000ull;
 struct TileDims {
   int64_t N, ntiles;
   int K, p, d, f, Kpad, R, R4, S, pp;
+  int xq;  // Xt: columns in groups of 4 rows of R4, groups xq = 4 R4 + 4 apart (conflict-free 16-byte reads)
   int nb, mc, n;
   int stage_bytes, off_x, off_y, off_z, off_c;                       // within a stage
   int off_bt, off_gt, off_al, off_xt, off_rt, off_red, off_bar, off_stage;
@@ -118,7 +121,7 @@ __global__ void __launch_bounds__(kPT, 2) pass_tile_kernel(TileDims D, PassIO io
   float *Bt = reinterpret_cast<float *>(sm + D.off_bt);  // [p][Kpad]
   float *Gt = reinterpret_cast<float *>(sm + D.off_gt);  // [d][Kpad]
   float *al = reinterpret_cast<float *>(sm + D.off_al);  // [f]
-  float *Xt = reinterpret_cast<float *>(sm + D.off_xt);  // [pp][R4]
+  float *Xt = reinterpret_cast<float *>(sm + D.off_xt);  // column l at xcol(l)
   float *Rt = reinterpret_cast<float *>(sm + D.off_rt);  // [Kpad][R4] (FULL)
   double *red = reinterpret_cast<double *>(sm + D.off_red);
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm + D.off_bar);
@@ -126,6 +129,8 @@ __global__ void __launch_bounds__(kPT, 2) pass_tile_kernel(TileDims D, PassIO io
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int K = D.K, p = D.p, d = D.d, f = D.f, Kpad = D.Kpad, R = D.R, R4 = D.R4;
   const int64_t N = D.N;
+  auto xcol = [&](int l) { return (l >> 2) * D.xq + (l & 3) * R4; };
+  constexpr int kR = 8 * RPW, kRsh = RPW == 4 ? 5 : RPW == 2 ? 4 : 3;  // rows per tile, log2
 
   // coefficients theta (+ t delta), zero for the base alternative and the padding
   const double tsc = io.delta ? *io.tscale : 0.0;
@@ -139,7 +144,7 @@ __global__ void __launch_bounds__(kPT, 2) pass_tile_kernel(TileDims D, PassIO io
     Gt[e] = (k >= 1 && k < K) ? (float)coef(D.nb + (int64_t)(k - 1) * d + j) : 0.f;
   }
   for (int j = tid; j < f; j += kPT) al[j] = (float)coef(D.mc + j);
-  for (int e = p * R4 + tid; e < D.pp * R4; e += kPT) Xt[e] = 0.f;  // padding columns of Xt
+  for (int e = p * R4 + tid; e < D.pp * R4; e += kPT) Xt[xcol(e / R4) + e % R4] = 0.f;  // padding columns
   if (FULL)
     for (int e = tid; e < R4; e += kPT) Rt[Kpad * R4 + e] = 0.f;       // row read by the last class pair
   if (tid == 0) {
@@ -206,9 +211,9 @@ __global__ void __launch_bounds__(kPT, 2) pass_tile_kernel(TileDims D, PassIO io
     }
     __syncthreads();
     if (s_abort) break;
-    for (int e = tid; e < R * p; e += kPT) {
-      const int r = e / p, l = e - r * p;
-      Xt[l * R4 + r] = Xs[e];
+    for (int e = tid; e < kR * p; e += kPT) {  // lanes over rows: no division, conflict-free
+      const int r = e & (kR - 1), l = e >> kRsh;
+      Xt[xcol(l) + r] = Xs[r * p + l];
     }
     __syncthreads();
 
@@ -223,7 +228,7 @@ __global__ void __launch_bounds__(kPT, 2) pass_tile_kernel(TileDims D, PassIO io
 #pragma unroll 2
       for (int j = 0; j < p; ++j) {
         float xv[RPW];
-        load_rows<RPW>(Xt + j * R4 + r0, xv);
+        load_rows<RPW>(Xt + xcol(j) + r0, xv);
 #pragma unroll
         for (int c = 0; c < CS; ++c) {
           const float b = Bt[j * Kpad + lane + 32 * c];
@@ -326,7 +331,7 @@ __global__ void __launch_bounds__(kPT, 2) pass_tile_kernel(TileDims D, PassIO io
           const float4 rb = *reinterpret_cast<const float4 *>(Rt + (k1 + 1) * R4 + r);
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const float4 x = *reinterpret_cast<const float4 *>(Xt + (l0 + q) * R4 + r);
+            const float4 x = *reinterpret_cast<const float4 *>(Xt + xcol(l0 + q) + r);
             a[q] = fmaf(ra.x, x.x, fmaf(ra.y, x.y, fmaf(ra.z, x.z, fmaf(ra.w, x.w, a[q]))));
             a[4 + q] = fmaf(rb.x, x.x, fmaf(rb.y, x.y, fmaf(rb.z, x.z, fmaf(rb.w, x.w, a[4 + q]))));
           }
@@ -427,6 +432,7 @@ bool make_tile_dims(const Shape &s, bool full, int rpw, TileDims &D, size_t &sme
   D.R = 8 * rpw;
   D.R4 = D.R + 4;
   D.pp = round_up_int(std::max(s.p, 1), 4);
+  D.xq = 4 * D.R4 + 4;
   D.nb = (int)s.nb; D.mc = (int)s.mc; D.n = (int)s.n;
   D.ntiles = (s.N + D.R - 1) / D.R;
   int o = 0;
@@ -439,7 +445,7 @@ bool make_tile_dims(const Shape &s, bool full, int rpw, TileDims &D, size_t &sme
   D.off_bt = o; o += round_up_int(s.p * D.Kpad * 4, 128);
   D.off_gt = o; o += round_up_int(s.d * D.Kpad * 4, 128);
   D.off_al = o; o += round_up_int(std::max(s.f, 1) * 4, 128);
-  D.off_xt = o; o += round_up_int(D.pp * D.R4 * 4, 128);
+  D.off_xt = o; o += round_up_int(D.pp / 4 * D.xq * 4, 128);
   D.off_rt = o; o += full ? round_up_int((D.Kpad + 1) * D.R4 * 4, 128) : 0;
   D.off_red = o; o += round_up_int(std::max(2 * kPT / 32, s.K * s.f) * 8, 128);
   D.off_bar = o; o += 128;
