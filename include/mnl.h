@@ -175,8 +175,11 @@ MNL_API int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision
 
 /* Copy HOST arrays into the handle's own device buffers (handles created with
  * data = NULL only; otherwise MNL_ERR_INVALID_ARG), then validate them as
- * mnl_create does.  Pinned host memory makes the copy asynchronous and fast;
- * pageable memory works too.  Synchronises the stream. */
+ * mnl_create does.  The copy is split into 32 MiB pieces over four internal
+ * copy streams (several copy engines); it starts after the work already on
+ * the handle's stream and completes before anything enqueued there later.
+ * Pinned host memory makes the copy asynchronous and fast; pageable memory
+ * works too.  Synchronises the stream. */
 MNL_API int mnl_upload(mnl_handle *h, const mnl_data *host_data);
 
 /* Log-likelihood and gradient at theta (eq. "log-lik function", eq. "loglik gradient").

@@ -62,6 +62,12 @@ struct mnl_handle {
   double *h_scal;
   int *h_flags;
   cudaEvent_t ev[12];
+  // host uploads (handles that own their data): chunks spread over several
+  // copy streams, joined to st by events
+  static constexpr int kUp = 4;
+  cudaStream_t ust[kUp];
+  cudaEvent_t uev[kUp + 1];
+  bool up_ready;
   int launches;
   std::vector<void *> allocs;
 };
@@ -208,6 +214,11 @@ void free_all(mnl_handle *h) {
   if (h->h_scal) cudaFreeHost(h->h_scal);
   if (h->h_flags) cudaFreeHost(h->h_flags);
   for (auto &e : h->ev) if (e) cudaEventDestroy(e);
+  if (h->up_ready) {
+    for (auto &s2 : h->ust) cudaStreamDestroy(s2);
+    for (auto &e : h->uev) cudaEventDestroy(e);
+    h->up_ready = false;
+  }
   h->h_scal = nullptr;
   h->h_flags = nullptr;
 }
@@ -710,12 +721,36 @@ int mnl_upload(mnl_handle *h, const mnl_data *hd) {
   if (!hd->choice || (S.p > 0 && !hd->X) || (S.d > 0 && !hd->Y) || (S.f > 0 && !hd->Z)) return MNL_ERR_INVALID_ARG;
   int rc = set_device(h);
   if (rc) return rc;
-  if (S.p) CK(cudaMemcpyAsync(const_cast<float *>(h->X), hd->X, (size_t)S.N * S.p * 4, cudaMemcpyHostToDevice, h->st));
-  if (S.d)
-    CK(cudaMemcpyAsync(const_cast<float *>(h->Y), hd->Y, (size_t)S.N * S.K * S.d * 4, cudaMemcpyHostToDevice, h->st));
-  if (S.f)
-    CK(cudaMemcpyAsync(const_cast<float *>(h->Z), hd->Z, (size_t)S.N * S.K * S.f * 4, cudaMemcpyHostToDevice, h->st));
-  CK(cudaMemcpyAsync(const_cast<int32_t *>(h->choice), hd->choice, (size_t)S.N * 4, cudaMemcpyHostToDevice, h->st));
+  if (!h->up_ready) {
+    for (auto &s2 : h->ust) CK(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+    for (auto &e : h->uev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    h->up_ready = true;
+  }
+  // The copies start after the work already queued on st (which may still
+  // read the previous data) and st waits for all of them.  Chunks of 32 MiB
+  // are dealt to the copy streams in turn, so several copy engines run.
+  CK(cudaEventRecord(h->uev[mnl_handle::kUp], h->st));
+  for (auto &s2 : h->ust) CK(cudaStreamWaitEvent(s2, h->uev[mnl_handle::kUp], 0));
+  constexpr size_t kChunk = (size_t)32 << 20;
+  int next = 0;
+  auto copy = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
+    for (size_t o = 0; o < bytes; o += kChunk) {
+      const size_t b = bytes - o < kChunk ? bytes - o : kChunk;
+      const cudaError_t e = cudaMemcpyAsync(static_cast<char *>(dst) + o, static_cast<const char *>(src) + o, b,
+                                            cudaMemcpyHostToDevice, h->ust[next]);
+      if (e != cudaSuccess) return e;
+      next = (next + 1) % mnl_handle::kUp;
+    }
+    return cudaSuccess;
+  };
+  if (S.p) CK(copy(const_cast<float *>(h->X), hd->X, (size_t)S.N * S.p * 4));
+  if (S.d) CK(copy(const_cast<float *>(h->Y), hd->Y, (size_t)S.N * S.K * S.d * 4));
+  if (S.f) CK(copy(const_cast<float *>(h->Z), hd->Z, (size_t)S.N * S.K * S.f * 4));
+  CK(copy(const_cast<int32_t *>(h->choice), hd->choice, (size_t)S.N * 4));
+  for (int i = 0; i < mnl_handle::kUp; ++i) {
+    CK(cudaEventRecord(h->uev[i], h->ust[i]));
+    CK(cudaStreamWaitEvent(h->st, h->uev[i], 0));
+  }
   return validate(h);
 }
 

@@ -34,6 +34,7 @@ namespace {
 constexpr int kPT = 256;          // threads per CTA
 constexpr int kBetaItems = 2;     // beta-gradient register tiles per warp
 constexpr int kYZSlots = 2;       // gamma / alpha outputs per thread
+constexpr int kRegYZ = 8;         // d, f up to this: gamma and alpha coefficients in registers
 constexpr uint64_t kTileWaitNs = 2000000000ull;
 
 struct TileDims {
@@ -189,6 +190,17 @@ __global__ void __launch_bounds__(kPT, 2) pass_tile_kernel(TileDims D, PassIO io
     }
   }
 
+  // this lane's gamma coefficients (classes lane + 32 c) and alpha, in
+  // registers when d, f <= kRegYZ (they do not change during the pass)
+  const bool yz_reg = d <= kRegYZ && f <= kRegYZ;
+  float gr[CS][kRegYZ], ar[kRegYZ];
+#pragma unroll
+  for (int j = 0; j < kRegYZ; ++j) {
+    ar[j] = (yz_reg && j < f) ? al[j] : 0.f;
+#pragma unroll
+    for (int c = 0; c < CS; ++c) gr[c][j] = (yz_reg && j < d) ? Gt[j * Kpad + lane + 32 * c] : 0.f;
+  }
+
   int it = 0;
   for (int64_t tl = blockIdx.x; tl < D.ntiles; tl += gridDim.x, ++it) {
     const int s = it % D.S;
@@ -243,9 +255,17 @@ __global__ void __launch_bounds__(kPT, 2) pass_tile_kernel(TileDims D, PassIO io
 #pragma unroll
         for (int r = 0; r < RPW; ++r) {
           const float *y = Ys + ((size_t)(r0 + r) * K + k) * d;
-          for (int j = 0; j < d; ++j) u[r][c] = fmaf(y[j], Gt[j * Kpad + k], u[r][c]);
           const float *z = Zs + ((size_t)(r0 + r) * K + k) * f;
-          for (int j = 0; j < f; ++j) u[r][c] = fmaf(z[j], al[j], u[r][c]);
+          if (yz_reg) {
+#pragma unroll
+            for (int j = 0; j < kRegYZ; ++j) {
+              if (j < d) u[r][c] = fmaf(y[j], gr[c][j], u[r][c]);
+              if (j < f) u[r][c] = fmaf(z[j], ar[j], u[r][c]);
+            }
+          } else {
+            for (int j = 0; j < d; ++j) u[r][c] = fmaf(y[j], Gt[j * Kpad + k], u[r][c]);
+            for (int j = 0; j < f; ++j) u[r][c] = fmaf(z[j], al[j], u[r][c]);
+          }
         }
       }
       float res[CS][RPW];  // residuals of this lane's classes for the warp's rows
