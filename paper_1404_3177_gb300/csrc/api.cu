@@ -327,6 +327,23 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
   return ms;
 }
 
+// Per-phase device times of a step from its events.
+void fill_times(mnl_handle *h, mnl_step_info &loc, float t_fallback) {
+  loc.t_pass_ms = elapsed(h->ev[0], h->ev[1]);
+  loc.t_hess_ms = elapsed(h->ev[1], h->ev[2]);
+  loc.t_chol_ms = elapsed(h->ev[2], h->ev[3]) + t_fallback;
+  loc.t_ls_ms = elapsed(h->ev[3], h->ev[4]);
+  loc.t_build_ms = elapsed(h->ev[1], h->ev[5]);
+  loc.t_syrk_ms = elapsed(h->ev[5], h->ev[6]);
+  loc.t_band_ms = elapsed(h->ev[6], h->ev[7]);
+  loc.t_zblk_ms = elapsed(h->ev[7], h->ev[8]);
+  loc.t_asm_ms = elapsed(h->ev[8], h->ev[2]);
+  loc.t_factor_ms = elapsed(h->ev[2], h->ev[9]);
+  loc.t_solve_ms = elapsed(h->ev[9], h->ev[3]);
+  loc.t_fallback_ms = t_fallback;
+  loc.launches = h->launches;
+}
+
 // One Newton iteration.  With gtol > 0 the gradient is checked before the
 // Hessian is formed; *converged is set and theta left unchanged if it is met.
 int step_impl(mnl_handle *h, double *theta, mnl_step_info *info, double gtol, bool *converged, int max_halvings) {
@@ -375,7 +392,19 @@ int step_impl(mnl_handle *h, double *theta, mnl_step_info *info, double gtol, bo
     h->launches += nl;
   }
   CK(cudaEventRecord(h->ev[3], h->st));
-  CK(cudaMemcpyAsync(h->h_scal, h->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  // The first trial of the step halving (t = 1) and, when it is acceptable, the
+  // update of theta are enqueued behind the solve, so that the common case needs
+  // one host round trip; otherwise theta is unchanged and the steps below decide.
+  const double u8 = 8.0 * (h->fp64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24));
+  h->h_scal[8] = 1.0;
+  CK(cudaMemcpyAsync(h->tscale, h->h_scal + 8, sizeof(double), cudaMemcpyHostToDevice, h->st));
+  rc = run_pass(h, theta, false, h->delta, kLt);
+  if (rc) return rc;
+  CK(cudaEventRecord(h->ev[4], h->st));
+  CK(launch_try_full_step(n, theta, h->delta, h->scal + kL, h->scal + kLabs, h->scal + kLt, h->status, h->err, u8,
+                          h->scal + kStepInf, h->st));
+  h->launches += 1;
+  CK(cudaMemcpyAsync(h->h_scal, h->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   CK(cudaMemcpyAsync(h->h_flags, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   CK(cudaMemcpyAsync(h->h_flags + 1, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   if (mixed) CK(cudaMemcpyAsync(h->h_scal + 12, h->ref, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
@@ -384,6 +413,21 @@ int step_impl(mnl_handle *h, double *theta, mnl_step_info *info, double gtol, bo
   const double l0 = h->h_scal[kL], labs = h->h_scal[kLabs], ginf = h->h_scal[kGinf];
   if (!std::isfinite(l0) || !std::isfinite(ginf)) return MNL_ERR_NONFINITE;
   loc.solve_mode = h->solve_mode;
+  if (mixed) loc.refine_steps = (int)h->h_scal[14];
+  if (h->h_flags[0] & 32) {  // the full step was taken
+    loc.loglik_old = l0;
+    loc.loglik_new = h->h_scal[kLt];
+    loc.grad_inf = ginf;
+    loc.step_inf = h->h_scal[kStepInf];
+    loc.theta_inf = h->h_scal[kThetaInf];
+    loc.step_scale = 1.0;
+    loc.ls_noise = noise_tol(h, labs);
+    loc.halvings = 0;
+    loc.ls_evals = 1;
+    fill_times(h, loc, 0.f);
+    if (info) *info = loc;
+    return MNL_OK;
+  }
   // A refinement that is still converging (ref[1] == 0) continues, 5 steps at a time, up to kRefineMax.
   for (int done = kRefineIters; mixed && (h->h_flags[0] & 16) && !(h->h_flags[0] & 8) && h->h_scal[13] == 0.0 &&
                                 done < kRefineMax;
@@ -445,19 +489,7 @@ int step_impl(mnl_handle *h, double *theta, mnl_step_info *info, double gtol, bo
   loc.ls_noise = tau;
   loc.halvings = j;
   loc.ls_evals = evals;
-  loc.t_pass_ms = elapsed(h->ev[0], h->ev[1]);
-  loc.t_hess_ms = elapsed(h->ev[1], h->ev[2]);
-  loc.t_chol_ms = elapsed(h->ev[2], h->ev[3]) + t_fallback;
-  loc.t_ls_ms = elapsed(h->ev[3], h->ev[4]);
-  loc.t_build_ms = elapsed(h->ev[1], h->ev[5]);
-  loc.t_syrk_ms = elapsed(h->ev[5], h->ev[6]);
-  loc.t_band_ms = elapsed(h->ev[6], h->ev[7]);
-  loc.t_zblk_ms = elapsed(h->ev[7], h->ev[8]);
-  loc.t_asm_ms = elapsed(h->ev[8], h->ev[2]);
-  loc.t_factor_ms = elapsed(h->ev[2], h->ev[9]);
-  loc.t_solve_ms = elapsed(h->ev[9], h->ev[3]);
-  loc.t_fallback_ms = t_fallback;
-  loc.launches = h->launches;
+  fill_times(h, loc, t_fallback);
   if (info) *info = loc;
   return MNL_OK;
 }

@@ -128,6 +128,36 @@ __global__ void axpy_theta_kernel(int64_t n, double *theta, const double *delta,
   }
 }
 
+// The full Newton step theta += delta, applied when it is acceptable as the
+// first trial of the step halving (Sec. 3.1): l(theta + delta) >= l0 - u8 * labs
+// (u8 * labs: the noise level of the float sums), the factorisation and solve
+// succeeded (status bits 4, 8, 16 clear) and no wait timed out.  Sets status
+// bit 32 when applied; scal_out as axpy_theta_kernel.
+__global__ void try_full_step_kernel(int64_t n, double *theta, const double *delta, const double *l0,
+                                     const double *labs, const double *lt, int *status, const int *err, double u8,
+                                     double *scal_out) {
+  const double a = *l0, b = *lt;
+  const bool ok = (*status & (4 | 8 | 16)) == 0 && *err == 0 && isfinite(a) && isfinite(b) && b >= a - u8 * *labs;
+  if (!ok) return;
+  double m1 = 0.0, m2 = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double st = delta[i];
+    const double th = theta[i] + st;
+    theta[i] = th;
+    m1 = fmax(m1, fabs(st));
+    m2 = fmax(m2, fabs(th));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+    m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_nonneg(scal_out, m1);
+    atomic_max_nonneg(scal_out + 1, m2);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, 32);
+}
+
 __global__ void vec_absmax_kernel(int64_t n, const double *v, double *out) {
   double m = 0.0;
   bool nonfinite = false;
@@ -446,6 +476,15 @@ cudaError_t launch_axpy_theta(int64_t n, double *theta, const double *delta, con
                               cudaStream_t st) {
   const int blocks = (int)std::min<int64_t>(64, (n + 255) / 256);
   axpy_theta_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, st>>>(n, theta, delta, tscale, scal_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_try_full_step(int64_t n, double *theta, const double *delta, const double *l0, const double *labs,
+                                 const double *lt, int *status, const int *err, double u8, double *scal_out,
+                                 cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>(64, (n + 255) / 256);
+  try_full_step_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, st>>>(n, theta, delta, l0, labs, lt, status, err, u8,
+                                                                 scal_out);
   return cudaGetLastError();
 }
 

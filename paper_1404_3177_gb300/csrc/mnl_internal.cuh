@@ -314,5 +314,9 @@ cudaError_t launch_mixed_refine(int64_t n, const double *F, const double *g, dou
 cudaError_t launch_axpy_theta(int64_t n, double *theta, const double *delta, const double *tscale, double *scal_out,
                               cudaStream_t st);
 cudaError_t launch_vec_absmax(int64_t n, const double *v, double *out, cudaStream_t st);
+// theta += delta when l(theta + delta) = *lt >= *l0 - u8 * *labs and status / err show no failure; then status |= 32.
+cudaError_t launch_try_full_step(int64_t n, double *theta, const double *delta, const double *l0, const double *labs,
+                                 const double *lt, int *status, const int *err, double u8, double *scal_out,
+                                 cudaStream_t st);
 
 }  // namespace mnl
