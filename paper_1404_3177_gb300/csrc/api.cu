@@ -301,6 +301,7 @@ int run_hessian(mnl_handle *h, cudaEvent_t *ev = nullptr) {
   io.z_part = h->z_part; io.z_split = h->z_split;
   io.tl = &h->tl;
   io.fp64 = h->fp64;
+  io.f32 = h->solve_mode == MNL_SOLVE_MIXED ? h->F32 : nullptr;  // the mixed solve's input, written on the way
   if (h->tcz) {
     io.zt.part = h->zt_part;
     io.zt.split = h->zt_split;
@@ -381,7 +382,7 @@ int step_impl(mnl_handle *h, double *theta, mnl_step_info *info, double gtol, bo
   const bool mixed = h->solve_mode == MNL_SOLVE_MIXED;
   if (mixed) {
     CK(launch_mixed_solve(n, h->F, h->F32, h->grad, h->delta, h->mwork, h->status, h->err, kRefineIters, h->st,
-                          &nl));
+                          &nl, true));
     h->launches += nl;
     CK(cudaEventRecord(h->ev[9], h->st));
   } else {

@@ -909,7 +909,7 @@ __global__ void __launch_bounds__(1024, 2) assemble_tiles_kernel(Shape S, const 
                                                                  int nmain, const CT *__restrict__ bandp, int bsplit,
                                                                  int nband, const int *__restrict__ band_of, int nt1d,
                                                                  const ZT *__restrict__ zp, int zsplit, ZTileView zv,
-                                                                 double *__restrict__ F) {
+                                                                 double *__restrict__ F, float *__restrict__ F32) {
   __shared__ double tile[32][33];  // tile[c - c0][r - r0]
   const int64_t n = S.n;
   const int t = (int)blockIdx.x;
@@ -923,6 +923,7 @@ __global__ void __launch_bounds__(1024, 2) assemble_tiles_kernel(Shape S, const 
   if (r < n && c < n && r >= c) {
     v = assemble_entry<CT, ZT>(S, mainp, msplit, nmain, bandp, bsplit, nband, band_of, nt1d, zp, zsplit, r, c, zv);
     F[c * n + r] = v;
+    if (F32) F32[c * n + r] = (float)v;
   }
   tile[ty][tx] = v;
   __syncthreads();
@@ -1178,12 +1179,12 @@ cudaError_t launch_assemble(const Shape &s, const AssembleIO &io, int nmain, dou
     assemble_tiles_kernel<double, double><<<grid, block, 0, st>>>(
         s, reinterpret_cast<const double *>(io.main_part), io.main_split, nmain,
         reinterpret_cast<const double *>(io.band_part), io.band_split, tl.nband, tl.band_of, nt1d,
-        reinterpret_cast<const double *>(io.z_part), io.z_split, io.zt, F);
+        reinterpret_cast<const double *>(io.z_part), io.z_split, io.zt, F, io.f32);
   } else {
     assemble_tiles_kernel<float, float><<<grid, block, 0, st>>>(
         s, reinterpret_cast<const float *>(io.main_part), io.main_split, nmain,
         reinterpret_cast<const float *>(io.band_part), io.band_split, tl.nband, tl.band_of, nt1d,
-        reinterpret_cast<const float *>(io.z_part), io.z_split, io.zt, F);
+        reinterpret_cast<const float *>(io.z_part), io.z_split, io.zt, F, io.f32);
   }
   return cudaGetLastError();
 }

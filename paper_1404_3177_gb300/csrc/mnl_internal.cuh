@@ -278,6 +278,7 @@ struct AssembleIO {
   const TileLists *tl;   // device pointers inside
   bool fp64;
   ZTileView zt;
+  float *f32 = nullptr;  // when given, the lower triangle of F in float32 too (the mixed solve's input)
 };
 cudaError_t launch_assemble(const Shape &s, const AssembleIO &io, int nmain, double *F, cudaStream_t st);
 
@@ -302,8 +303,10 @@ cudaError_t launch_cholesky_solve(int64_t n, const double *L, const double *dinv
 // refinement state ([2] = refinement steps taken), zeroed by the caller.
 size_t mixed_solve_bytes(int64_t n);
 double *mixed_solve_ref(void *work, int64_t n);
+// f32_ready: F32 already holds the float32 lower triangle of F (written by the assembly).
 cudaError_t launch_mixed_solve(int64_t n, const double *F, float *F32, const double *g, double *delta, void *work,
-                               int *status, int *err, int iters, cudaStream_t st, int *launches);
+                               int *status, int *err, int iters, cudaStream_t st, int *launches,
+                               bool f32_ready = false);
 // status &= mask (device word).
 cudaError_t launch_status_and(int *status, int mask, cudaStream_t st);
 // `iters` more refinement steps after launch_mixed_solve (the caller first clears status bit 16).

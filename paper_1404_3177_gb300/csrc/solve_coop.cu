@@ -690,6 +690,17 @@ __global__ void __launch_bounds__(256) gemv_col_kernel(int64_t n, const TM *__re
   const TM *col = M + o * n;
   TM s[4] = {(TM)0, (TM)0, (TM)0, (TM)0};
   int64_t i = i0 + lane;
+  for (; i + 480 < i1; i += 512) {  // 16 loads of M and x in flight per lane (L2 latency)
+    TM m[16];
+    TX xv[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      m[u] = col[i + 32 * u];
+      xv[u] = x[i + 32 * u];
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) s[u & 3] = fma(m[u], (TM)xv[u], s[u & 3]);
+  }
   for (; i + 96 < i1; i += 128) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) s[u] = fma(col[i + 32 * u], (TM)x[i + 32 * u], s[u]);
@@ -824,7 +835,7 @@ double *mixed_solve_ref(void *work, int64_t n) {
 }
 
 cudaError_t launch_mixed_solve(int64_t n, const double *F, float *F32, const double *g, double *delta, void *work,
-                               int *status, int *err, int iters, cudaStream_t st, int *launches) {
+                               int *status, int *err, int iters, cudaStream_t st, int *launches, bool f32_ready) {
   const MixedLayout L = mixed_layout(n);
   unsigned char *w = static_cast<unsigned char *>(work);
   float *Li = reinterpret_cast<float *>(w + L.li), *Dblk = reinterpret_cast<float *>(w + L.dblk);
@@ -834,7 +845,7 @@ cudaError_t launch_mixed_solve(int64_t n, const double *F, float *F32, const dou
   GridBarrier *bar = reinterpret_cast<GridBarrier *>(w + L.bar);
   cudaError_t e;
   dim3 grid((unsigned)((n + 255) / 256), (unsigned)std::min<int64_t>(n, 65535), (unsigned)((n + 65534) / 65535));
-  f64_to_f32_lower_kernel<<<grid, 256, 0, st>>>(n, F, F32);
+  if (!f32_ready) f64_to_f32_lower_kernel<<<grid, 256, 0, st>>>(n, F, F32);
   if ((e = cudaMemsetAsync(Li, 0, (size_t)n * n * 4, st)) != cudaSuccess) return e;
   if ((e = launch_coop<float, true>(n, F32, Li, Dblk, dinv, bar, status, 8, err, st)) != cudaSuccess) return e;
   const unsigned nt = (unsigned)((n + 31) / 32);
@@ -844,7 +855,7 @@ cudaError_t launch_mixed_solve(int64_t n, const double *F, float *F32, const dou
   gemv_col_kernel<float, double, float, 0><<<gb, 256, 0, st>>>(n, Li, g, y, nullptr, nullptr);
   gemv_col_kernel<float, float, float, 1><<<gb, 256, 0, st>>>(n, Li, y, z, nullptr, nullptr);
   refine_update_kernel<<<1, 1024, 0, st>>>(n, z, delta, ref, status, 1);
-  int cnt = 7;
+  int cnt = f32_ready ? 6 : 7;
   for (int it = 0; it < iters; ++it) {
     gemv_col_kernel<double, double, double, 2><<<gb, 256, 0, st>>>(n, F, delta, r, g, ref);  // r = g - F delta
     gemv_col_kernel<float, double, float, 0><<<gb, 256, 0, st>>>(n, Li, r, y, nullptr, ref);
