@@ -62,7 +62,7 @@ enum {
   MNL_ERR_LINESEARCH = 6,  /* no step size 2^-j, j <= max_halvings, kept l from decreasing    */
   MNL_MAXITER = 7,         /* mnl_fit: maxiter reached without meeting a tolerance (non-fatal) */
   MNL_ERR_TIMEOUT = 8,     /* a bounded device-side wait gave up; the result is invalid      */
-  MNL_ERR_UNSUPPORTED = 9, /* valid request this build does not implement                    */
+  MNL_ERR_UNSUPPORTED = 9, /* valid request that the library does not implement             */
   MNL_PENDING = 10         /* mnl_server_poll: the request has not finished yet (non-fatal)  */
 };
 
