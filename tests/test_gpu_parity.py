@@ -327,3 +327,23 @@ def test_float32_gradient_modes_stop_at_the_noise_floor(MNL, prec):
         th, info = m.fit()
     assert info["status"] == 0 and info["stop_reason"] in (3, 5), info
     assert np.abs(th.cpu().numpy() - ref).max() / np.abs(ref).max() <= THETA_TOL
+
+
+# ---------------------------------------------------------------------------
+# Step halving (Sec. 3.1): a start where the full Newton step lowers l
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16"])
+def test_step_halving_from_a_distant_start(MNL, prec):
+    prob = datagen.make_problem(4000, 4, 3, 1, 2, 11, theta_sd=0.5)
+    th0 = 2.0 * np.random.default_rng(7).standard_normal(prob.n_theta)
+    ref, st = oracle.fit(prob, th0, maxiter=1, gtol=0.0)
+    assert st["ls_evals"] == 3  # the oracle rejects t = 1 and t = 1/2 (l drops by thousands) and takes t = 1/4
+    with MNL(**dev(prob), precision=prec, solve="fp64" if prec == "fp64" else "auto") as m:
+        th = torch.from_numpy(th0.copy()).cuda()
+        info = m.newton_step(th)
+        th = th.cpu().numpy()
+    assert info["halvings"] == 2 and info["ls_evals"] == 3 and info["step_scale"] == 0.25, info
+    assert oracle.loglik_grad(prob, th)[0] > oracle.loglik_grad(prob, th0)[0]
+    tol = 1e-9 if prec == "fp64" else 5e-2  # relative to the step; BF16: the Hessian's 2e-3 error
+    assert np.abs(th - ref).max() <= tol * np.abs(ref - th0).max()
