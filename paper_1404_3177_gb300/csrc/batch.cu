@@ -498,15 +498,12 @@ int ws_build(Engine &E, WorkSet &W, const std::vector<const ProbLayout *> &L, in
     static const int64_t bounds[] = {128, 256, 512, kCtaSolveMaxN};
     W.chol_buckets.clear();
     size_t at = order.size();  // walk from the smallest
-    int64_t lo = 0;
     for (int64_t hi : bounds) {
       size_t from = at;
       while (from > 0 && L[order[from - 1]]->s.n <= hi) --from;
       if (from < at) W.chol_buckets.push_back({(int)from, (int)(at - from), grouped_chol_smem(L[order[from]]->s.n)});
       at = from;
-      lo = hi;
     }
-    (void)lo;
     if ((rc = upload(W.chol_list, order, E.st))) return rc;
   }
   if ((rc = upload(W.build_items, bi, E.st)) || (rc = upload(W.z_items, zi, E.st)) ||
@@ -527,9 +524,9 @@ int ws_build(Engine &E, WorkSet &W, const std::vector<const ProbLayout *> &L, in
     int t = 0;
     for (int ti = 0; ti < l.nt1d; ++ti)
       for (int tj = 0; tj <= ti; ++tj, ++t)
-        um.push_back({mA, i, ti, tj, 0, kb, g.main_off + (int64_t)t * kTile * kTile});
+        um.push_back({mA, i, ti, tj, 0, kb, g.main_off + (int64_t)t * kTile * kTile, 0, -1});
     for (size_t k = 0; k < l.bands.size(); ++k)
-      ub.push_back({mD, i, l.bands[k].x, l.bands[k].y, 0, kb, g.band_off + (int64_t)k * kTile * kTile});
+      ub.push_back({mD, i, l.bands[k].x, l.bands[k].y, 0, kb, g.band_off + (int64_t)k * kTile * kTile, 0, -1});
   }
   if (E.fp64) {
     auto by_len = [](const SyrkUnit &a, const SyrkUnit &c) { return (a.kb1 - a.kb0) > (c.kb1 - c.kb0); };
