@@ -42,6 +42,7 @@ def _rank_main(rank, world, port, out_dir):
     dist.destroy_process_group()
 
 
+@pytest.mark.skipif(torch.cuda.is_available(), reason="with CUDA the bench's ranks use NCCL, one GPU each")
 def test_allmax_and_barrier_over_two_gloo_ranks(tmp_path):
     mp.spawn(_rank_main, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
     vals = [float((tmp_path / f"rank{r}.txt").read_text()) for r in range(2)]
