@@ -188,6 +188,22 @@ def cholesky_solve(L: np.ndarray, b: np.ndarray) -> np.ndarray:
 STOP_NAMES = {1: "gtol", 2: "ftol", 3: "steptol", 4: "maxiter", -2: "not_pd", -4: "linesearch"}
 
 
+def std_errors(prob, theta) -> np.ndarray:
+    """Asymptotic standard errors at theta (normally the estimate): the square roots of the diagonal of the
+    inverse of the observed information F = -H (the coefficient table of the package's ``summary`` method,
+    Sec. 2.3).  Each diagonal entry of F^-1 comes from one solve with the oracle's Cholesky factor."""
+    F = neg_hessian(prob, theta)
+    L = cholesky(F)
+    if L is None:
+        raise ValueError("-H is not positive definite at theta")
+    n = F.shape[0]
+    var = np.empty(n)
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        var[i] = cholesky_solve(L, e)[i]
+    return np.sqrt(var)
+
 # Rounding-noise allowance of the line search: 8 units of FP64 roundoff times |l|.
 LS_REL_TOL = 8 * 2.0 ** -53
 

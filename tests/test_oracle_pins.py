@@ -377,3 +377,39 @@ def test_singular_design_reports_not_positive_definite():
     prob.X[:, 2] = prob.X[:, 1]
     F = oracle.neg_hessian(prob, rand_theta(prob))
     assert oracle.cholesky(F) is None or np.linalg.eigvalsh(F).min() < 1e-8 * np.abs(F).max()
+
+
+# ---------------------------------------------------------------------------
+# Standard errors (the package's summary table): sqrt(diag((-H)^-1)) at the estimate
+# ---------------------------------------------------------------------------
+
+def test_std_errors_intercept_only_closed_form():
+    """Intercept only: Var(ln(n_k / n_0)) = 1/n_k + 1/n_0 (multinomial log-odds)."""
+    prob = datagen.make_problem(3000, 5, 1, 0, 0, 31, intercept=True, theta_sd=0.7)
+    th_hat, _ = oracle.fit(prob)
+    n = np.bincount(prob.choice, minlength=5).astype(np.float64)
+    np.testing.assert_allclose(oracle.std_errors(prob, th_hat), np.sqrt(1.0 / n[1:] + 1.0 / n[0]), rtol=1e-9)
+
+
+def test_std_errors_saturated_groups_closed_form():
+    """One-hot groups: Var(beta_k[g]) = 1/n_gk + 1/n_g0, independently per group."""
+    G, K, N = 3, 4, 2400
+    prob = datagen.make_problem(N, K, G, 0, 0, 41, intercept=False)
+    grp = np.arange(N) % G
+    prob.X = np.eye(G, dtype=np.float32)[grp]
+    prob.choice = np.random.default_rng(2).integers(0, K, N).astype(np.int32)
+    th_hat, _ = oracle.fit(prob)
+    se = oracle.std_errors(prob, th_hat).reshape(K - 1, G)
+    for g in range(G):
+        n = np.bincount(prob.choice[grp == g], minlength=K).astype(np.float64)
+        np.testing.assert_allclose(se[:, g], np.sqrt(1.0 / n[1:] + 1.0 / n[0]), rtol=1e-9)
+
+
+def test_std_errors_binary_logit_textbook():
+    """K = 2: sqrt(diag((X^T W X)^-1)) with W = p(1 - p) at the estimate, formed here with NumPy."""
+    prob = datagen.make_problem(400, 2, 3, 0, 0, 21, intercept=True, theta_sd=0.8)
+    th_hat, _ = oracle.fit(prob)
+    X = prob.X.astype(np.float64)
+    pr = 1.0 / (1.0 + np.exp(-(X @ th_hat)))
+    info = X.T @ (X * (pr * (1.0 - pr))[:, None])
+    np.testing.assert_allclose(oracle.std_errors(prob, th_hat), np.sqrt(np.diag(np.linalg.inv(info))), rtol=1e-9)
