@@ -116,7 +116,15 @@ typedef struct mnl_step_info {
   int32_t solve_mode;  /* MNL_SOLVE_FP64 or MNL_SOLVE_MIXED, as used          */
   int32_t refine_steps;/* refinement steps of a mixed solve                 */
   int32_t fallback;    /* 1 when a mixed solve fell back to float64          */
+  int32_t factor_kind; /* factorisation of the (first) solve: MNL_FACTOR_*   */
 } mnl_step_info;
+
+/* mnl_step_info.factor_kind: the cooperative blocked Cholesky on the CUDA
+ * cores (float32 in a mixed solve, float64 otherwise), or the panel
+ * factorisation whose trailing updates run on the tensor cores (mixed solves
+ * with n_theta >= 1024; environment variable MNL_TC_CHOL_MIN_N, read by
+ * mnl_create, moves that threshold). */
+enum { MNL_FACTOR_NONE = 0, MNL_FACTOR_COOP = 1, MNL_FACTOR_TENSOR = 2 };
 
 typedef struct mnl_fit_opts {
   int32_t maxiter;      /* Newton iterations at most (paper default 50)              */

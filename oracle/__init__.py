@@ -5,8 +5,8 @@ baseline leg of ``bench.py`` use this module.  The library's product path never
 imports it.
 
 Every function takes a ``datagen.Problem``-like object (attributes N, K, p, d,
-f, gamma_base, X, Y, Z, choice) and float64 coefficient vectors in the order of
-eq. "theta vec".
+f, gamma_base, X, Y, Z, choice and, optionally, w: float32 observation weights)
+and float64 coefficient vectors in the order of eq. "theta vec".
 """
 from __future__ import annotations
 
@@ -39,7 +39,7 @@ def build(force: bool = False) -> str:
 class _Problem(C.Structure):
     _fields_ = [("N", C.c_int64), ("K", C.c_int32), ("p", C.c_int32), ("d", C.c_int32), ("f", C.c_int32),
                 ("gamma_base", C.c_int32), ("X", C.c_void_p), ("Y", C.c_void_p), ("Z", C.c_void_p),
-                ("choice", C.c_void_p)]
+                ("choice", C.c_void_p), ("w", C.c_void_p)]
 
 
 class FitOpts(C.Structure):
@@ -86,8 +86,11 @@ class _Keep:
         self.Y = np.ascontiguousarray(prob.Y, dtype=np.float32)
         self.Z = np.ascontiguousarray(prob.Z, dtype=np.float32)
         self.c = np.ascontiguousarray(prob.choice, dtype=np.int32)
+        w = getattr(prob, "w", None)
+        self.w = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
         self.s = _Problem(prob.N, prob.K, prob.p, prob.d, prob.f, prob.gamma_base, self.X.ctypes.data,
-                          self.Y.ctypes.data, self.Z.ctypes.data, self.c.ctypes.data)
+                          self.Y.ctypes.data, self.Z.ctypes.data, self.c.ctypes.data,
+                          None if self.w is None else self.w.ctypes.data)
         self.n = num_params(prob.K, prob.p, prob.d, prob.f, prob.gamma_base)
 
 

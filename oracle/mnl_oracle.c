@@ -29,6 +29,11 @@
  * Coefficient order (eq. "theta vec"): beta_1..beta_{K-1} (p each),
  * gamma_0..gamma_{K-1} (d each; gamma_0 only when gamma_base = 1), alpha (f).
  *
+ * Observation weights (the `weights` argument of the package's mnlogit call,
+ * Sec. 2.3; the paper does not define them further) are read as case weights:
+ * observation i counts w_i times, so l, dl/dtheta and d2l/dtheta2 are the sums
+ * above with each term multiplied by w_i (NULL weights: all ones).
+ *
  * Readings of points the paper leaves open: exp/log use a max shift (equal in
  * exact arithmetic to eq. "base probability"); the line search accepts the
  * first halved step whose log-likelihood is not lower (Sec. 3.1), "not lower"
@@ -52,6 +57,7 @@ typedef struct {
   const float *Y;        /* [N][K][d] */
   const float *Z;        /* [N][K][f] */
   const int32_t *choice; /* [N], 0..K-1, 0 = base */
+  const float *w;        /* [N] observation weights (>= 0), or NULL for all ones */
 } oracle_problem;
 
 typedef struct {
@@ -113,6 +119,9 @@ static void design_row(const oracle_problem *P, int64_t i, int k, srow *r) {
 
 static int row_capacity(const oracle_problem *P) { return P->p + 2 * P->d + P->f + 1; }
 
+/* Weight of observation i (1 when no weights are given). */
+static double weight(const oracle_problem *P, int64_t i) { return P->w ? (double)P->w[i] : 1.0; }
+
 typedef struct {
   srow *rows; /* K rows */
   double *V;  /* K */
@@ -163,6 +172,9 @@ int oracle_check(const oracle_problem *P) {
   if (P->N < 0 || P->K < 2 || P->p < 0 || P->d < 0 || P->f < 0) return -1;
   for (int64_t i = 0; i < P->N; ++i)
     if (P->choice[i] < 0 || P->choice[i] >= P->K) return -2;
+  if (P->w)
+    for (int64_t i = 0; i < P->N; ++i)
+      if (!(P->w[i] >= 0.0f) || !isfinite(P->w[i])) return -4;
   return 0;
 }
 
@@ -173,7 +185,7 @@ int oracle_probs(const oracle_problem *P, const double *theta, double *prob, dou
   if (work_init(P, &w)) return -3;
   double l = 0.0;
   for (int64_t i = 0; i < P->N; ++i) {
-    l += observation(P, theta, i, &w);
+    l += weight(P, i) * observation(P, theta, i, &w);
     for (int k = 0; k < P->K; ++k) prob[i * P->K + k] = w.pr[k];
   }
   work_free(&w);
@@ -190,12 +202,13 @@ int oracle_loglik_grad(const oracle_problem *P, const double *theta, double *log
   if (grad) memset(grad, 0, sizeof(double) * n);
   double l = 0.0;
   for (int64_t i = 0; i < P->N; ++i) {
-    l += observation(P, theta, i, &w);
+    const double wi = weight(P, i);
+    l += wi * observation(P, theta, i, &w);
     if (!grad) continue;
     const srow *ry = &w.rows[P->choice[i]];
-    for (int e = 0; e < ry->n; ++e) grad[ry->idx[e]] += ry->val[e];
+    for (int e = 0; e < ry->n; ++e) grad[ry->idx[e]] += wi * ry->val[e];
     for (int k = 0; k < P->K; ++k)
-      for (int e = 0; e < w.rows[k].n; ++e) grad[w.rows[k].idx[e]] -= w.pr[k] * w.rows[k].val[e];
+      for (int e = 0; e < w.rows[k].n; ++e) grad[w.rows[k].idx[e]] -= wi * w.pr[k] * w.rows[k].val[e];
   }
   work_free(&w);
   if (loglik) *loglik = l;
@@ -229,6 +242,7 @@ int oracle_neg_hessian(const oracle_problem *P, const double *theta, double *F, 
     if (work_init(P, &w) || !jbar) { err = 1; continue; }
     for (int64_t i = 0; i < N; ++i) {
       const double *pr = prob + i * K;
+      const double wi = weight(P, i);
       for (int k = 0; k < K; ++k) design_row(P, i, k, &w.rows[k]);
       /* jbar_i = sum_k P_ik j_ik (only entries below a1 are needed) */
       for (int64_t a = 0; a < a1; ++a) jbar[a] = 0.0;
@@ -241,14 +255,14 @@ int oracle_neg_hessian(const oracle_problem *P, const double *theta, double *F, 
         for (int e = 0; e < r->n; ++e) {
           const int64_t a = r->idx[e];
           if (a < a0 || a >= a1) continue;
-          const double wa = pr[k] * r->val[e];
+          const double wa = wi * pr[k] * r->val[e];
           for (int e2 = 0; e2 < r->n; ++e2)
             if (r->idx[e2] <= a) F[a * n + r->idx[e2]] += wa * r->val[e2];
         }
       }
       /* - jbar_i jbar_i^T */
       for (int64_t a = a0; a < a1; ++a) {
-        const double ja = jbar[a];
+        const double ja = wi * jbar[a];
         if (ja == 0.0) continue;
         double *Fa = F + a * n;
         for (int64_t b = 0; b <= a; ++b) Fa[b] -= ja * jbar[b];
@@ -309,7 +323,7 @@ int oracle_neg_hessian_entries(const oracle_problem *P, const double *theta, int
         ja += pr[k] * va;
         jb += pr[k] * vb;
       }
-      acc += s - ja * jb;
+      acc += weight(P, i) * (s - ja * jb);
     }
     out[e] = acc;
   }

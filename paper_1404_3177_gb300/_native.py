@@ -60,7 +60,7 @@ class mnl_step_info(C.Structure):
                 ("t_band_ms", C.c_float), ("t_zblk_ms", C.c_float), ("t_asm_ms", C.c_float),
                 ("t_factor_ms", C.c_float), ("t_solve_ms", C.c_float), ("t_fallback_ms", C.c_float),
                 ("launches", C.c_int32), ("solve_mode", C.c_int32), ("refine_steps", C.c_int32),
-                ("fallback", C.c_int32)]
+                ("fallback", C.c_int32), ("factor_kind", C.c_int32)]
 
 
 class mnl_fit_opts(C.Structure):

@@ -1,9 +1,11 @@
 // C ABI of libmnl: handle lifetime, workspaces and the Newton-Raphson driver
 // (Sec. 3.1 eq. "NR update" with step halving; stopping rules of Sec. 2.3).
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <new>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -58,6 +60,9 @@ struct mnl_handle {
   double *dinv, *ref;  // ref points into mwork
   float *F32;
   void *mwork, *cwork;  // mixed-solve and float64-factor workspaces
+  void *tcwork;         // tensor-core factorisation (n_theta >= the threshold)
+  TcCholPlan tcp;
+  uint64_t wait_ns;     // bound of the kernels' device waits (0: their defaults)
   // host mirrors (pinned)
   double *h_scal;
   int *h_flags;
@@ -89,6 +94,19 @@ int cuda_fail(cudaError_t e) {
 }
 
 int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// n_theta from which the mixed solve factors on the tensor cores; the
+// environment variable MNL_TC_CHOL_MIN_N (read when a handle is created)
+// overrides it.
+int64_t tc_chol_min_n() {
+  const char *v = std::getenv("MNL_TC_CHOL_MIN_N");
+  if (v && *v) {
+    char *end = nullptr;
+    const long long x = std::strtoll(v, &end, 10);
+    if (end && *end == 0 && x > 0) return (int64_t)x;
+  }
+  return kTcCholMinN;
+}
 
 // Below this many observations MNL_BF16 forms the Hessian operands in TF32.
 constexpr int64_t kBf16MinRows = 1024;
@@ -191,7 +209,8 @@ Sizes plan_sizes(const mnl_dims &d, int prec_in, bool owned, int nsm, int *main_
   }
   z.F = (size_t)S.n * S.n * 8;
   // dinv (float64), F32 (float32), the mixed-solve and float64-factor workspaces
-  z.solve = (size_t)S.n * 8 + (size_t)S.n * S.n * 4 + mixed_solve_bytes(S.n) + chol_work_bytes(S.n);
+  z.solve = (size_t)S.n * 8 + (size_t)S.n * S.n * 4 + mixed_solve_bytes(S.n) + chol_work_bytes(S.n) +
+            (S.n >= tc_chol_min_n() ? tc_chol_bytes(S.n) : 0);
   z.owned = owned ? ((size_t)S.N * S.p + (size_t)S.N * S.K * (S.d + S.f)) * 4 + (size_t)S.N * 4 : 0;
   return z;
 }
@@ -380,7 +399,12 @@ int step_impl(mnl_handle *h, double *theta, mnl_step_info *info, double gtol, bo
   CK(cudaEventRecord(h->ev[2], h->st));
   int nl = 0;
   const bool mixed = h->solve_mode == MNL_SOLVE_MIXED;
-  if (mixed) {
+  if (mixed && h->tcp.ready) {
+    CK(launch_mixed_solve_tc(h->tcp, h->F, h->F32, h->grad, h->delta, h->mwork, h->status, h->err, kRefineIters,
+                             h->wait_ns, h->st, &nl));
+    h->launches += nl;
+    CK(cudaEventRecord(h->ev[9], h->st));
+  } else if (mixed) {
     CK(launch_mixed_solve(n, h->F, h->F32, h->grad, h->delta, h->mwork, h->status, h->err, kRefineIters, h->st,
                           &nl, true));
     h->launches += nl;
@@ -414,6 +438,7 @@ int step_impl(mnl_handle *h, double *theta, mnl_step_info *info, double gtol, bo
   const double l0 = h->h_scal[kL], labs = h->h_scal[kLabs], ginf = h->h_scal[kGinf];
   if (!std::isfinite(l0) || !std::isfinite(ginf)) return MNL_ERR_NONFINITE;
   loc.solve_mode = h->solve_mode;
+  loc.factor_kind = (mixed && h->tcp.ready) ? MNL_FACTOR_TENSOR : MNL_FACTOR_COOP;
   if (mixed) loc.refine_steps = (int)h->h_scal[14];
   if (h->h_flags[0] & 32) {  // the full step was taken
     loc.loglik_old = l0;
@@ -609,6 +634,11 @@ int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *
       (rc = dalloc(h, &h->cwork, chol_work_bytes(S.n))))
     return fail(rc);
   h->ref = mixed_solve_ref(h->mwork, S.n);
+  if (S.n >= tc_chol_min_n()) {
+    if ((rc = dalloc(h, &h->tcwork, tc_chol_bytes(S.n)))) return fail(rc);
+    const cudaError_t e = tc_chol_prepare(S.n, h->tcwork, h->nsm, &h->tcp);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(cuda_fail(e)); }
+  }
   h->solve_mode = h->fp64 ? MNL_SOLVE_FP64 : MNL_SOLVE_MIXED;
   (void)tsz;
   h->op_bytes = z.ops;
@@ -689,18 +719,26 @@ int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *
       std::vector<SyrkUnit> u;
       const int64_t nmain = (int64_t)h->h_main.size();
       auto slot = [](int ti, int tj) { return (int64_t)ti * (ti + 1) / 2 + tj; };
+      // Tiles in square blocks of kSuper x kSuper (block rows I >= block columns J, J fastest): the
+      // persistent CTAs take consecutive jobs at the same time and walk the observations in step, so
+      // a block keeps the operand rows read at once to 2 kSuper tile rows instead of a whole band of
+      // the triangle (which does not fit in L2 when there are many tile rows).
+      constexpr int kSuper = 16;
+      const int nsb = (h->nt1d + kSuper - 1) / kSuper;
       for (int sp = 0; sp < nsplit; ++sp)
-        for (int ti = 0; ti < h->nt1d; ++ti)
-          for (int tj = 0; tj <= ti; tj += 2) {
-            SyrkUnit w;
-            w.map = 0; w.problem = 0; w.ti = ti; w.tj = tj;
-            w.kb0 = (int)((int64_t)kb * sp / nsplit);
-            w.kb1 = (int)((int64_t)kb * (sp + 1) / nsplit);
-            w.out_off = ((int64_t)sp * nmain + slot(ti, tj)) * kTile * kTile;
-            w.out_off2 = tj + 1 <= ti ? ((int64_t)sp * nmain + slot(ti, tj + 1)) * kTile * kTile : -1;
-            w.flags = 0;
-            u.push_back(w);
-          }
+        for (int I = 0; I < nsb; ++I)
+          for (int J = 0; J <= I; ++J)
+            for (int ti = I * kSuper; ti < std::min(h->nt1d, (I + 1) * kSuper); ++ti)
+              for (int tj = J * kSuper; tj <= std::min(ti, (J + 1) * kSuper - 1); tj += 2) {
+                SyrkUnit w;
+                w.map = 0; w.problem = 0; w.ti = ti; w.tj = tj;
+                w.kb0 = (int)((int64_t)kb * sp / nsplit);
+                w.kb1 = (int)((int64_t)kb * (sp + 1) / nsplit);
+                w.out_off = ((int64_t)sp * nmain + slot(ti, tj)) * kTile * kTile;
+                w.out_off2 = tj + 1 <= ti ? ((int64_t)sp * nmain + slot(ti, tj + 1)) * kTile * kTile : -1;
+                w.flags = 0;
+                u.push_back(w);
+              }
       return u;
     };
     const std::vector<SyrkUnit> jm = S.mc > 0 ? make_main_units(h->main_split) : std::vector<SyrkUnit>();

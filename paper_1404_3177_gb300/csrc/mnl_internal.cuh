@@ -313,6 +313,50 @@ cudaError_t launch_status_and(int *status, int mask, cudaStream_t st);
 cudaError_t launch_mixed_refine(int64_t n, const double *F, const double *g, double *delta, void *work, int *status,
                                 int iters, cudaStream_t st, int *launches);
 
+// ---------------------------------------------------------------------------
+// Mixed solve with a tensor-core factorisation (large n): blocked right-looking
+// float32 Cholesky of F and the inverse of the factor, panels of kCholPanel
+// columns; per panel one CTA factors and inverts the diagonal block, a panel
+// kernel forms the panel rows of L (and of L^{-1}) and their TF32 hi/lo
+// copies, and the trailing updates run as 3xTF32 tcgen05 tiles.
+// ---------------------------------------------------------------------------
+constexpr int kCholPanel = 128;
+// One 128 x 128 tile of a trailing update: C(ti, tj) -= A(ti) B(tj)^T, with
+// A = panel rows (maps 0, 1), B = rows of maps (2 bmap, 2 bmap + 1), C the
+// factor (cbuf 0) or the inverse (cbuf 1); tri: only the lower triangle of
+// the tile.
+struct CholUnit {
+  int ti, tj, bmap, cbuf, tri, pad;
+};
+size_t chol_update_smem_bytes();
+// Sets the kernel's shared-memory attribute on the current device.
+cudaError_t chol_update_tc_setup();
+cudaError_t launch_chol_update_tc(const CUtensorMap *maps, const CholUnit *units, int nunits, int grid, float *C0,
+                                  float *C1, int64_t ld, int64_t n, int *err, uint64_t wait_ns, cudaStream_t st);
+
+// Host-side plan (built once per handle; holds device pointers into `ws`).
+struct TcCholPlan {
+  int64_t n = 0, n_pad = 0;
+  int np = 0, grid = 0;
+  void *ws = nullptr;                 // tc_chol_bytes(n) bytes of device memory
+  CUtensorMap *maps = nullptr;        // device: Ph, Pl, Rh, Rl
+  CholUnit *units = nullptr;          // device: all panels' units
+  std::vector<int> unit_off;          // host: panel k's units are [unit_off[k], unit_off[k + 1])
+  float *Ph = nullptr, *Pl = nullptr, *Rh = nullptr, *Rl = nullptr;  // [n_pad][128] hi / lo
+  float *InvT = nullptr;             // [np][128][128]: inverse of each diagonal block, transposed
+  bool ready = false;
+};
+// Use the tensor-core factorisation for n_theta at or above this.
+constexpr int64_t kTcCholMinN = 1024;
+size_t tc_chol_bytes(int64_t n);
+// Encodes the tensor maps and uploads the unit lists (synchronous; call at set-up).
+cudaError_t tc_chol_prepare(int64_t n, void *ws, int num_sms, TcCholPlan *plan);
+// As launch_mixed_solve (F32 holds the float32 lower triangle of F), with the
+// tensor-core factorisation and inverse.
+cudaError_t launch_mixed_solve_tc(const TcCholPlan &plan, const double *F, float *F32, const double *g, double *delta,
+                                  void *work, int *status, int *err, int iters, uint64_t wait_ns, cudaStream_t st,
+                                  int *launches);
+
 // Small FP64 vector kernels.
 cudaError_t launch_axpy_theta(int64_t n, double *theta, const double *delta, const double *tscale, double *scal_out,
                               cudaStream_t st);

@@ -313,14 +313,14 @@ __device__ __forceinline__ void pivot(double d, double &lc, double &ri) {
 // finite beyond their written part (they are zeroed once).  Returns false when
 // a pivot is not positive or not finite (the factor then continues with 1).
 constexpr int kCholUnroll = 8;
-template <typename T>
+template <typename T, int DS = kDs>
 __device__ __forceinline__ bool warp_chol_inv32(T *Bc, T *Xb, T *Lt, T *rinv) {
   constexpr int kUnroll = sizeof(T) == 4 ? kCholUnroll : 1;  // float64: registers are short
   const int lane = threadIdx.x & 31;
   T a[32], x[32];
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
-    a[j] = j <= lane ? Bc[j * kDs + lane] : (T)0;
+    a[j] = j <= lane ? Bc[j * DS + lane] : (T)0;
     x[j] = j == lane ? (T)1 : (T)0;
   }
   bool ok = true;
@@ -334,9 +334,9 @@ __device__ __forceinline__ bool warp_chol_inv32(T *Bc, T *Xb, T *Lt, T *rinv) {
     const T v = lane == c ? lc : a[0] * ri;  // L_lane,c for lane >= c
     dg = __shfl_sync(0xffffffffu, fma(-v, v, a[1]), (c + 1) & 31);
     if (lane > c) Lt[c * kLts + lane - c - 1] = v;
-    Bc[c * kDs + lane] = lane >= c ? v : (T)0;
+    Bc[c * DS + lane] = lane >= c ? v : (T)0;
     const T xc = x[0] * ri;
-    Xb[lane * kDs + c] = xc;
+    Xb[lane * DS + c] = xc;
     if (lane == 0) rinv[c] = ri;
     __syncwarp();
     const T ac = lane > c ? v : (T)0;
@@ -768,6 +768,282 @@ __global__ void refine_check_kernel(const double *ref, int *status) {
 
 __global__ void status_and_kernel(int *status, int mask) { atomicAnd(status, mask); }
 
+// ---------------------------------------------------------------------------
+// Tensor-core factorisation for large n (launch_mixed_solve_tc).  Panels of
+// kDp = 128 columns; per panel k (columns j0 = 128 k ...):
+//   diagonal step (one CTA): factor and invert the diagonal block;
+//   panel step (many CTAs):  the panel rows L(i, j0 + kk) for i >= j0 + 128,
+//     stored only as the TF32 hi/lo operands Ph/Pl of the trailing update, and
+//     the row block of the inverse B = L^{-1}: B_kj <- Inv_kk B_kj (j < k),
+//     with its hi/lo copies Rh/Rl;
+//   trailing update (tcgen05, syrk_tc.cu): F_ij -= L_ik L_jk^T (j > k) and
+//     B_ij -= L_ik B_kj (i > k, j <= k).
+// B is the block forward substitution L B = I carried along with the
+// factorisation, as in the cooperative kernel above.
+// ---------------------------------------------------------------------------
+constexpr int kDp = kCholPanel;  // panel width = diagonal block edge
+constexpr int kDd = kDp + 4;     // shared stride of the diagonal step's arrays
+constexpr size_t kDiag128Smem = (size_t)(2 * kDp * kDd + 32 * kLts + kDp) * sizeof(float);
+constexpr int kPr = 64;          // panel step: rows (or inverse columns) per item
+constexpr int kPs = kPr + 4;     // shared stride of the operand chunk
+constexpr size_t kPanelSmem = (size_t)(kDp * kDd + kDp * kPs) * sizeof(float);
+
+// x = hi + lo with hi, lo rounded to TF32 (lo carries the bits hi drops).
+__device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
+  uint32_t h, l;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+  hi = __uint_as_float(h);
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - hi));
+  lo = __uint_as_float(l);
+}
+
+// Diagonal step of panel k: D = F(j0.., j0..) (already updated by the earlier
+// panels; identity past n) is factored D = L L^T and L inverted in four
+// 32-column steps.  Step b (j = 32 b): one warp factors and inverts the 32 x 32
+// diagonal block (warp_chol_inv32); then the rows below, L_ib = D_ib Inv_bb^T,
+// and the inverse's row block X_b,: = Inv_bb W_b,: (W: the accumulated
+// right-hand side, zero at first); then the trailing part of the block,
+// D_ij -= L_ib L_jb^T, and W_i,: -= L_ib X_b,: for the rows below.
+// Writes InvT[m][r] = Inv(r, m), the diagonal block of L^{-1} into Li, and its
+// hi/lo rows Rh/Rl[j0 + c][r] = Inv(r, c).  status |= bad_bit on a pivot that
+// is not positive.
+__global__ void __launch_bounds__(256, 1) chol_diag128_kernel(const float *__restrict__ F32, int64_t ld, int64_t n,
+                                                              int k, float *__restrict__ Li, float *__restrict__ InvT,
+                                                              float *__restrict__ Rh, float *__restrict__ Rl,
+                                                              int *status, int bad_bit) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float *D = reinterpret_cast<float *>(smem_raw);  // D[c * kDd + r] = element (r, c)
+  float *X = D + kDp * kDd;                        // the inverse, same layout
+  float *Lt = X + kDp * kDd;                       // [32][kLts], warp-step scratch
+  float *rinv = Lt + 32 * kLts;                    // [128]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t j0 = (int64_t)k * kDp;
+  const int nb = (int)(n - j0 < kDp ? n - j0 : kDp);
+  for (int e = tid; e < kDp * kDp; e += 256) {
+    const int c = e >> 7, r = e & 127;
+    D[c * kDd + r] = (r < nb && c < nb) ? (r >= c ? F32[(j0 + c) * ld + j0 + r] : 0.f) : (r == c ? 1.f : 0.f);
+    X[c * kDd + r] = 0.f;
+  }
+  for (int e = tid; e < 32 * kLts; e += 256) Lt[e] = 0.f;
+  __syncthreads();
+  for (int b = 0; b < 4; ++b) {
+    const int j = 32 * b, nr = kDp - j - 32;  // rows below the step
+    if (warp == kDiagWarp) {
+      const bool ok = warp_chol_inv32<float, kDd>(D + j * kDd + j, X + j * kDd + j, Lt, rinv + j);
+      if (!ok && lane == 0) atomicOr(status, bad_bit);
+    }
+    __syncthreads();
+    // Rows below: strips of 4 rows (r) with column j + lane.  Inverse row
+    // block: strips of 4 rows j + r' with columns c' < j (lanes, groups of 32).
+    const int nsa = nr / 4, nsb = j / 32 * 8;
+    float oa[3][4], ob[3][4];
+    int na = 0, nbk = 0;
+    for (int t = warp; t < nsa; t += 8, ++na) {
+      const int r = j + 32 + 4 * t;
+      float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+      for (int m = 0; m < 32; ++m) {
+        const float iv = X[(j + m) * kDd + j + lane];  // Inv_bb(lane, m)
+        const float4 d4 = *reinterpret_cast<const float4 *>(D + (j + m) * kDd + r);
+        o[0] = fmaf(d4.x, iv, o[0]); o[1] = fmaf(d4.y, iv, o[1]);
+        o[2] = fmaf(d4.z, iv, o[2]); o[3] = fmaf(d4.w, iv, o[3]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) oa[na][u] = o[u];
+    }
+    for (int t = warp; t < nsb; t += 8, ++nbk) {
+      const int rp = 4 * (t & 7), cp = 32 * (t >> 3) + lane;
+      float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+      for (int m = 0; m < 32; ++m) {
+        const float w = X[cp * kDd + j + m];  // W(j + m, cp)
+        const float4 i4 = *reinterpret_cast<const float4 *>(X + (j + m) * kDd + j + rp);  // Inv_bb(rp.., m)
+        o[0] = fmaf(i4.x, w, o[0]); o[1] = fmaf(i4.y, w, o[1]);
+        o[2] = fmaf(i4.z, w, o[2]); o[3] = fmaf(i4.w, w, o[3]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) ob[nbk][u] = o[u];
+    }
+    __syncthreads();
+    na = 0;
+    for (int t = warp; t < nsa; t += 8, ++na) {
+      const int r = j + 32 + 4 * t;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) D[(j + lane) * kDd + r + u] = oa[na][u];
+    }
+    nbk = 0;
+    for (int t = warp; t < nsb; t += 8, ++nbk) {
+      const int rp = 4 * (t & 7), cp = 32 * (t >> 3) + lane;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) X[cp * kDd + j + rp + u] = ob[nbk][u];
+    }
+    __syncthreads();
+    if (nr > 0) {
+      // Trailing part: 32 x 32 blocks (RB >= CB) of the nr x nr lower part, in strips of 8 rows;
+      // inverse: strips of 8 rows below with 32-column groups of the first j + 32 columns.
+      const int nrb = nr / 32;
+      const int nc = nrb * (nrb + 1) / 2 * 4, nd = (nr / 8) * (j / 32 + 1);
+      for (int t = warp; t < nc + nd; t += 8) {
+        float o[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (t < nc) {
+          const int pr = t >> 2, strip = t & 3;
+          int RB = 0;
+          while ((RB + 1) * (RB + 2) / 2 <= pr) ++RB;
+          const int CB = pr - RB * (RB + 1) / 2;
+          const int r = j + 32 + 32 * RB + 8 * strip, c = j + 32 + 32 * CB + lane;
+#pragma unroll 8
+          for (int m = 0; m < 32; ++m) {
+            const float lc = D[(j + m) * kDd + c];
+            const float4 a = *reinterpret_cast<const float4 *>(D + (j + m) * kDd + r);
+            const float4 b4 = *reinterpret_cast<const float4 *>(D + (j + m) * kDd + r + 4);
+            o[0] = fmaf(a.x, lc, o[0]); o[1] = fmaf(a.y, lc, o[1]); o[2] = fmaf(a.z, lc, o[2]);
+            o[3] = fmaf(a.w, lc, o[3]); o[4] = fmaf(b4.x, lc, o[4]); o[5] = fmaf(b4.y, lc, o[5]);
+            o[6] = fmaf(b4.z, lc, o[6]); o[7] = fmaf(b4.w, lc, o[7]);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (c <= r + u) D[c * kDd + r + u] -= o[u];
+        } else {
+          const int e = t - nc, strip = e % (nr / 8), cg = e / (nr / 8);
+          const int r = j + 32 + 8 * strip, c = 32 * cg + lane;
+#pragma unroll 8
+          for (int m = 0; m < 32; ++m) {
+            const float xv = X[c * kDd + j + m];
+            const float4 a = *reinterpret_cast<const float4 *>(D + (j + m) * kDd + r);
+            const float4 b4 = *reinterpret_cast<const float4 *>(D + (j + m) * kDd + r + 4);
+            o[0] = fmaf(a.x, xv, o[0]); o[1] = fmaf(a.y, xv, o[1]); o[2] = fmaf(a.z, xv, o[2]);
+            o[3] = fmaf(a.w, xv, o[3]); o[4] = fmaf(b4.x, xv, o[4]); o[5] = fmaf(b4.y, xv, o[5]);
+            o[6] = fmaf(b4.z, xv, o[6]); o[7] = fmaf(b4.w, xv, o[7]);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) X[c * kDd + r + u] -= o[u];
+        }
+      }
+      __syncthreads();
+    }
+  }
+  float *Ik = InvT + (int64_t)k * kDp * kDp;
+  for (int e = tid; e < kDp * kDp; e += 256) {
+    const int c = e >> 7, r = e & 127;
+    const float v = X[c * kDd + r];  // zero above the diagonal
+    Ik[e] = v;                       // InvT[c][r] = Inv(r, c)
+    if (r >= c && r < nb && c < nb) Li[(j0 + c) * ld + j0 + r] = v;
+    float hi, lo;
+    tf32_split(v, hi, lo);
+    Rh[(j0 + c) * kDp + r] = hi;
+    Rl[(j0 + c) * kDp + r] = lo;
+  }
+}
+
+// Panel step of panel k, items of 64 rows ((a), i >= j0 + 128, up to n_pad)
+// or 64 columns ((b), c < j0), each a 64 x 128 product with the inverse of
+// the diagonal block (lower triangular: Inv(kk, m) = 0 for m > kk):
+//   (a) L(i, j0 + kk) = sum_m F(i, j0 + m) Inv(kk, m) -> Ph/Pl[i][kk] (zero rows past n);
+//   (b) B(j0 + kk, c) <- sum_m Inv(kk, m) B(j0 + m, c) in Li, and Rh/Rl[c][kk].
+__global__ void __launch_bounds__(256, 2) chol_panel_kernel(const float *__restrict__ F32, int64_t ld, int64_t n,
+                                                            int64_t n_pad, int k, float *__restrict__ Li,
+                                                            const float *__restrict__ InvT, float *__restrict__ Ph,
+                                                            float *__restrict__ Pl, float *__restrict__ Rh,
+                                                            float *__restrict__ Rl) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float *Is = reinterpret_cast<float *>(smem_raw);  // Is[m * kDd + kk] = Inv(kk, m)
+  float *Os = Is + kDp * kDd;                        // Os[m * kPs + x]: operand chunk
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t j0 = (int64_t)k * kDp, r_begin = j0 + kDp;
+  const int na = (int)((n_pad - r_begin) / kPr), nbi = (int)(j0 / kPr);
+  const float *Ik = InvT + (int64_t)k * kDp * kDp;
+  for (int e = tid; e < kDp * kDp; e += 256) Is[(e >> 7) * kDd + (e & 127)] = Ik[e];
+  const int mend = 8 * ty + 8;  // Inv(kk, m) = 0 for m > kk >= 8 ty + 7
+  for (int item = blockIdx.x; item < na + nbi; item += gridDim.x) {
+    const bool rows = item < na;
+    const int64_t x0 = rows ? r_begin + (int64_t)item * kPr : (int64_t)(item - na) * kPr;
+    __syncthreads();  // Is is loaded; the previous item is done with Os
+    if (rows) {
+      for (int e = tid; e < kDp * kPr; e += 256) {
+        const int m = e >> 6, x = e & 63;
+        Os[m * kPs + x] = (x0 + x < n && j0 + m < n) ? F32[(j0 + m) * ld + x0 + x] : 0.f;
+      }
+    } else {
+      for (int e = tid; e < kDp * kPr; e += 256) {
+        const int x = e >> 7, m = e & 127;
+        Os[m * kPs + x] = j0 + m < n ? Li[(x0 + x) * ld + j0 + m] : 0.f;
+      }
+    }
+    __syncthreads();
+    float acc[4][8];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+#pragma unroll 4
+    for (int m = 0; m < mend; ++m) {
+      const float4 a = *reinterpret_cast<const float4 *>(Os + m * kPs + 4 * tx);
+      const float4 b0 = *reinterpret_cast<const float4 *>(Is + m * kDd + 8 * ty);
+      const float4 b1 = *reinterpret_cast<const float4 *>(Is + m * kDd + 8 * ty + 4);
+      const float av[4] = {a.x, a.y, a.z, a.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+    }
+    if (rows) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float h[8], l[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) tf32_split(acc[u][v], h[v], l[v]);
+        const int64_t o = (x0 + 4 * tx + u) * kDp + 8 * ty;
+        *reinterpret_cast<float4 *>(Ph + o) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4 *>(Ph + o + 4) = make_float4(h[4], h[5], h[6], h[7]);
+        *reinterpret_cast<float4 *>(Pl + o) = make_float4(l[0], l[1], l[2], l[3]);
+        *reinterpret_cast<float4 *>(Pl + o + 4) = make_float4(l[4], l[5], l[6], l[7]);
+      }
+    } else {
+      // through shared memory (Os reused as Res[x * kDd + kk]) so that the column writes are coalesced
+      __syncthreads();
+      float *Res = Os;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) Res[(4 * tx + u) * kDd + 8 * ty + v] = acc[u][v];
+      __syncthreads();
+      for (int e = tid; e < kPr * kDp; e += 256) {
+        const int x = e >> 7, kk = e & 127;
+        const float v = Res[x * kDd + kk];
+        if (j0 + kk < n) Li[(x0 + x) * ld + j0 + kk] = v;
+        float hi, lo;
+        tf32_split(v, hi, lo);
+        Rh[(x0 + x) * kDp + kk] = hi;
+        Rl[(x0 + x) * kDp + kk] = lo;
+      }
+    }
+  }
+}
+
+// Refinement from the explicit inverse Li (lower triangle; mirrored here):
+// delta_0 = L^{-T} L^{-1} g, then `iters` steps of r = g - F delta (float64),
+// delta += L^{-T} L^{-1} r.  Returns the number of launches.
+int refine_with_inverse(int64_t n, const double *F, float *Li, const double *g, double *delta, float *y, float *z,
+                        double *r, double *ref, int *status, int iters, cudaStream_t st) {
+  const unsigned nt = (unsigned)((n + 31) / 32);
+  mirror_lower_kernel<float><<<dim3(nt, nt), dim3(32, 8), 0, st>>>(n, Li);
+  const unsigned gb = (unsigned)((n + 7) / 8);
+  gemv_col_kernel<float, double, float, 0><<<gb, 256, 0, st>>>(n, Li, g, y, nullptr, nullptr);
+  gemv_col_kernel<float, float, float, 1><<<gb, 256, 0, st>>>(n, Li, y, z, nullptr, nullptr);
+  refine_update_kernel<<<1, 1024, 0, st>>>(n, z, delta, ref, status, 1);
+  int cnt = 4;
+  for (int it = 0; it < iters; ++it) {
+    gemv_col_kernel<double, double, double, 2><<<gb, 256, 0, st>>>(n, F, delta, r, g, ref);  // r = g - F delta
+    gemv_col_kernel<float, double, float, 0><<<gb, 256, 0, st>>>(n, Li, r, y, nullptr, ref);
+    gemv_col_kernel<float, float, float, 1><<<gb, 256, 0, st>>>(n, Li, y, z, nullptr, ref);
+    refine_update_kernel<<<1, 1024, 0, st>>>(n, z, delta, ref, status, 0);
+    cnt += 4;
+  }
+  refine_check_kernel<<<1, 1, 0, st>>>(ref, status);
+  return cnt + 1;
+}
+
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 int64_t panels(int64_t n) { return (n + kCb - 1) / kCb; }
@@ -848,23 +1124,95 @@ cudaError_t launch_mixed_solve(int64_t n, const double *F, float *F32, const dou
   if (!f32_ready) f64_to_f32_lower_kernel<<<grid, 256, 0, st>>>(n, F, F32);
   if ((e = cudaMemsetAsync(Li, 0, (size_t)n * n * 4, st)) != cudaSuccess) return e;
   if ((e = launch_coop<float, true>(n, F32, Li, Dblk, dinv, bar, status, 8, err, st)) != cudaSuccess) return e;
-  const unsigned nt = (unsigned)((n + 31) / 32);
-  mirror_lower_kernel<float><<<dim3(nt, nt), dim3(32, 8), 0, st>>>(n, Li);
-  const unsigned gb = (unsigned)((n + 7) / 8);
-  // delta_0 = L^{-T} (L^{-1} g)
-  gemv_col_kernel<float, double, float, 0><<<gb, 256, 0, st>>>(n, Li, g, y, nullptr, nullptr);
-  gemv_col_kernel<float, float, float, 1><<<gb, 256, 0, st>>>(n, Li, y, z, nullptr, nullptr);
-  refine_update_kernel<<<1, 1024, 0, st>>>(n, z, delta, ref, status, 1);
-  int cnt = f32_ready ? 6 : 7;
-  for (int it = 0; it < iters; ++it) {
-    gemv_col_kernel<double, double, double, 2><<<gb, 256, 0, st>>>(n, F, delta, r, g, ref);  // r = g - F delta
-    gemv_col_kernel<float, double, float, 0><<<gb, 256, 0, st>>>(n, Li, r, y, nullptr, ref);
-    gemv_col_kernel<float, float, float, 1><<<gb, 256, 0, st>>>(n, Li, y, z, nullptr, ref);
-    refine_update_kernel<<<1, 1024, 0, st>>>(n, z, delta, ref, status, 0);
-    cnt += 4;
+  const int cnt = (f32_ready ? 1 : 2) + refine_with_inverse(n, F, Li, g, delta, y, z, r, ref, status, iters, st);
+  if (launches) *launches = cnt;
+  return cudaGetLastError();
+}
+
+size_t tc_chol_bytes(int64_t n) {
+  const int64_t np = (n + kDp - 1) / kDp, n_pad = np * kDp;
+  int64_t units = 0;
+  for (int64_t k = 0; k + 1 < np; ++k) {
+    const int64_t m = np - 1 - k;
+    units += m * (m + 1) / 2 + m * (k + 1);
   }
-  refine_check_kernel<<<1, 1, 0, st>>>(ref, status);
-  ++cnt;
+  return round256(4 * sizeof(CUtensorMap)) + 4 * round256((size_t)n_pad * kDp * 4) +
+         round256((size_t)np * kDp * kDp * 4) + round256((size_t)units * sizeof(CholUnit));
+}
+
+cudaError_t tc_chol_prepare(int64_t n, void *ws, int num_sms, TcCholPlan *P) {
+  P->ready = false;
+  P->n = n;
+  P->np = (int)((n + kDp - 1) / kDp);
+  P->n_pad = (int64_t)P->np * kDp;
+  P->ws = ws;
+  unsigned char *w = static_cast<unsigned char *>(ws);
+  size_t o = 0;
+  P->maps = reinterpret_cast<CUtensorMap *>(w + o); o += round256(4 * sizeof(CUtensorMap));
+  float **bufs[4] = {&P->Ph, &P->Pl, &P->Rh, &P->Rl};
+  for (float **b : bufs) { *b = reinterpret_cast<float *>(w + o); o += round256((size_t)P->n_pad * kDp * 4); }
+  P->InvT = reinterpret_cast<float *>(w + o); o += round256((size_t)P->np * kDp * kDp * 4);
+  P->units = reinterpret_cast<CholUnit *>(w + o);
+  std::vector<CholUnit> u;
+  P->unit_off.assign(1, 0);
+  for (int k = 0; k + 1 < P->np; ++k) {
+    for (int ti = k + 1; ti < P->np; ++ti)
+      for (int tj = k + 1; tj <= ti; ++tj) u.push_back(CholUnit{ti, tj, 0, 0, ti == tj ? 1 : 0, 0});
+    for (int ti = k + 1; ti < P->np; ++ti)
+      for (int tj = 0; tj <= k; ++tj) u.push_back(CholUnit{ti, tj, 1, 1, 0, 0});
+    P->unit_off.push_back((int)u.size());
+  }
+  CUtensorMap hm[4];
+  cudaError_t e;
+  for (int i = 0; i < 4; ++i)
+    if ((e = encode_operand_map(OpType::TF32, *bufs[i], P->n_pad, kDp, &hm[i])) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(P->maps, hm, sizeof(hm), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  if (!u.empty() && (e = cudaMemcpy(P->units, u.data(), u.size() * sizeof(CholUnit), cudaMemcpyHostToDevice)) !=
+                        cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(chol_diag128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kDiag128Smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(chol_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kPanelSmem)) != cudaSuccess)
+    return e;
+  if ((e = chol_update_tc_setup()) != cudaSuccess) return e;
+  P->grid = num_sms;
+  P->ready = true;
+  return cudaSuccess;
+}
+
+cudaError_t launch_mixed_solve_tc(const TcCholPlan &P, const double *F, float *F32, const double *g, double *delta,
+                                  void *work, int *status, int *err, int iters, uint64_t wait_ns, cudaStream_t st,
+                                  int *launches) {
+  if (!P.ready) return cudaErrorInvalidValue;
+  const int64_t n = P.n;
+  const MixedLayout L = mixed_layout(n);
+  unsigned char *w = static_cast<unsigned char *>(work);
+  float *Li = reinterpret_cast<float *>(w + L.li), *y = reinterpret_cast<float *>(w + L.y);
+  float *z = reinterpret_cast<float *>(w + L.z);
+  double *r = reinterpret_cast<double *>(w + L.r), *ref = reinterpret_cast<double *>(w + L.ref);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(Li, 0, (size_t)n * n * 4, st)) != cudaSuccess) return e;
+  int cnt = 0;
+  for (int k = 0; k < P.np; ++k) {
+    chol_diag128_kernel<<<1, 256, kDiag128Smem, st>>>(F32, n, n, k, Li, P.InvT, P.Rh, P.Rl, status, 8);
+    const int64_t j0 = (int64_t)k * kDp;
+    const int items = (int)((P.n_pad - j0 - kDp) / kPr + j0 / kPr);
+    if (items > 0)
+      chol_panel_kernel<<<std::min(items, 2 * P.grid), 256, kPanelSmem, st>>>(F32, n, n, P.n_pad, k, Li, P.InvT, P.Ph,
+                                                                            P.Pl, P.Rh, P.Rl);
+    cnt += items > 0 ? 2 : 1;
+    if (k + 1 < P.np) {
+      const int u0 = P.unit_off[(size_t)k], nu = P.unit_off[(size_t)k + 1] - u0;
+      if ((e = launch_chol_update_tc(P.maps, P.units + u0, nu, std::min(nu, P.grid), F32, Li, n, n, err, wait_ns,
+                                     st)) != cudaSuccess)
+        return e;
+      ++cnt;
+    }
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  cnt += refine_with_inverse(n, F, Li, g, delta, y, z, r, ref, status, iters, st);
   if (launches) *launches = cnt;
   return cudaGetLastError();
 }

@@ -88,15 +88,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 // Wait for the phase of `parity` to complete.  Returns false when another role
 // raised the abort flag (if honour_abort) or after kTimeoutNs (then raises the
 // abort flag and records `code` in the error word).
+// Waits that drain copies or MMAs already issued (honour_abort = false) always
+// use the full bound, so that nothing is left writing into shared memory or
+// TMEM when the CTA exits.
 __device__ bool wait_bounded(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *err, int code,
-                             bool honour_abort = true) {
+                             bool honour_abort = true, uint64_t bound_ns = kTimeoutNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = gtimer();
+  const uint64_t lim = honour_abort ? bound_ns : kTimeoutNs;
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 31u) == 0) {
       if (honour_abort && *abort_flag) return false;
-      if (gtimer() - t0 > kTimeoutNs) {
+      if (gtimer() - t0 > lim) {
         *abort_flag = 1;
         atomicOr(err, code);
         return false;
@@ -330,6 +334,183 @@ __global__ void __launch_bounds__(192, 1) syrk_tc_kernel(const CUtensorMap *__re
   }
 }
 
+// ---------------------------------------------------------------------------
+// Trailing updates of the blocked float32 Cholesky factorisation (and of the
+// inverse of the factor carried along with it), C -= A B^T over one panel of
+// kCholPanel = 128 columns, on the tensor cores in three TF32 passes:
+// every operand is held as hi + lo (hi = TF32 rounding of the float32 value,
+// lo = TF32 rounding of the remainder) and A B^T = Ah Bh^T + Ah Bl^T + Al Bh^T
+// up to the Al Bl^T term, about 2^-21 relative: float32 accuracy from the
+// TF32 datapath.  The operands are the panel buffers written by the panel
+// kernel (rows contiguous along the 128 panel columns, i.e. K-major), so
+// every TMA box is 128 rows x 32 floats.
+// A unit is one 128 x 128 output tile of C (column-major, leading dimension
+// ld), A = rows ti of maps (0, 1), B = rows tj of maps (2 bmap, 2 bmap + 1);
+// tri: only entries on or below the diagonal of the tile are written.
+// Roles as in the SYRK kernel: warp 0 TMA producer, warp 1 MMA issuer (one
+// lane) and TMEM owner, warps 2-5 the epilogue (read C, subtract, write C,
+// 128 contiguous bytes per store instruction across the warp).
+// ---------------------------------------------------------------------------
+constexpr int kCuStages = 3;
+constexpr int kCuStageBytes = 4 * kOpBytes;  // Ah, Al, Bh, Bl
+constexpr int kCuSmemBytes = kCuStages * kCuStageBytes + 256 + 1024;
+
+__global__ void __launch_bounds__(192, 1) chol_update_tc_kernel(const CUtensorMap *__restrict__ maps,
+                                                                const CholUnit *__restrict__ units, int nunits,
+                                                                float *__restrict__ C0, float *__restrict__ C1,
+                                                                int64_t ld, int64_t n, int *__restrict__ err,
+                                                                uint64_t wait_ns) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kCuStages * kCuStageBytes);
+  uint64_t *empty = full + kCuStages;
+  uint64_t *tfull = empty + kCuStages;
+  uint64_t *tempty = tfull + 2;
+  uint64_t *drain = tempty + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  constexpr int kTmemCols = 2 * kTile;
+  constexpr int kKb = kCholPanel / kBkTf32;  // K-blocks per unit
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kCuStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 4); }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int last_par[kCuStages];
+      for (int s = 0; s < kCuStages; ++s) last_par[s] = -1;
+      bool ok = true;
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        const CholUnit w = units[u];
+        const bool same = w.bmap == 0 && w.ti == w.tj;  // B = A: one pair of boxes
+        const CUtensorMap *ma = maps, *mb = maps + 2 * w.bmap;
+        for (int kb = 0; kb < kKb; ++kb) {
+          if (!wait_bounded(&empty[stage], phase ^ 1u, abort_flag, err, kErrProducer, true, wait_ns)) {
+            ok = false;
+            break;
+          }
+          uint8_t *dst = smem + stage * kCuStageBytes;
+          mbar_arrive_expect_tx(&full[stage], (same ? 2 : 4) * kOpBytes);
+          tma_load_2d(ma, &full[stage], dst, kb * kBkTf32, w.ti * kTile);
+          tma_load_2d(ma + 1, &full[stage], dst + kOpBytes, kb * kBkTf32, w.ti * kTile);
+          if (!same) {
+            tma_load_2d(mb, &full[stage], dst + 2 * kOpBytes, kb * kBkTf32, w.tj * kTile);
+            tma_load_2d(mb + 1, &full[stage], dst + 3 * kOpBytes, kb * kBkTf32, w.tj * kTile);
+          }
+          last_par[stage] = (int)phase;
+          if (++stage == kCuStages) { stage = 0; phase ^= 1u; }
+        }
+      }
+      for (int s = 0; s < kCuStages; ++s)
+        if (last_par[s] >= 0) wait_bounded(&full[s], (uint32_t)last_par[s], abort_flag, err, kErrDrain, false);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t acc_ph[2] = {0u, 0u};
+      int local = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        const CholUnit w = units[u];
+        const bool same = w.bmap == 0 && w.ti == w.tj;
+        const int b = local & 1;
+        ++local;
+        if (!wait_bounded(&tempty[b], acc_ph[b] ^ 1u, abort_flag, err, kErrMma, true, wait_ns)) break;
+        acc_ph[b] ^= 1u;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(b * kTile);
+        for (int kb = 0; kb < kKb; ++kb) {
+          if (!wait_bounded(&full[stage], phase, abort_flag, err, kErrMma, true, wait_ns)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t a0 = saddr(smem + stage * kCuStageBytes);
+          const uint64_t ah = sw128_desc(a0), al = sw128_desc(a0 + kOpBytes);
+          const uint64_t bh = same ? ah : sw128_desc(a0 + 2 * kOpBytes);
+          const uint64_t bl = same ? al : sw128_desc(a0 + 3 * kOpBytes);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {  // 4 x 8 TF32 values along K inside the 128-byte row
+            const uint64_t o = (uint64_t)(2 * k);
+            tc_mma<true, kTile>(d_tmem, al + o, bh + o, (kb > 0 || k > 0) ? 1u : 0u);
+            tc_mma<true, kTile>(d_tmem, ah + o, bl + o, 1u);
+            tc_mma<true, kTile>(d_tmem, ah + o, bh + o, 1u);
+          }
+          tc_commit(&empty[stage]);
+          if (++stage == kCuStages) { stage = 0; phase ^= 1u; }
+        }
+        if (!ok) break;
+        tc_commit(&tfull[b]);
+      }
+      tc_commit(drain);
+      wait_bounded(drain, 0u, abort_flag, err, kErrDrain, false);
+    }
+  } else {
+    const int quarter = warp & 3;
+    uint32_t acc_ph[2] = {0u, 0u};
+    int local = 0;
+    for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+      const CholUnit w = units[u];
+      const int b = local & 1;
+      ++local;
+      int ok = 0;
+      if (lane == 0) ok = wait_bounded(&tfull[b], acc_ph[b], abort_flag, err, kErrEpilogue, true, wait_ns) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      acc_ph[b] ^= 1u;
+      tc_fence_after();
+      float *C = w.cbuf ? C1 : C0;
+      const int64_t row = (int64_t)w.ti * kTile + quarter * 32 + lane;
+#pragma unroll 1
+      for (int c0 = 0; c0 < kTile; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kTile + c0), v);
+        const int64_t col0 = (int64_t)w.tj * kTile + c0;
+        if (row >= n) continue;
+        float *dst = C + col0 * ld + row;
+        float prev[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int64_t col = col0 + j;
+          prev[j] = (col < n && (!w.tri || col <= row)) ? dst[(int64_t)j * ld] : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int64_t col = col0 + j;
+          if (col < n && (!w.tri || col <= row)) dst[(int64_t)j * ld] = prev[j] - __uint_as_float(v[j]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -445,6 +626,20 @@ cudaError_t launch_syrk_tc(OpType t, const CUtensorMap *maps, const SyrkUnit *un
                              : launch_tc<false, 256>(maps, units, nunits, active, grid, out, err, st);
   return t == OpType::TF32 ? launch_tc<true, 128>(maps, units, nunits, active, grid, out, err, st)
                            : launch_tc<false, 128>(maps, units, nunits, active, grid, out, err, st);
+}
+
+size_t chol_update_smem_bytes() { return kCuSmemBytes; }
+
+cudaError_t chol_update_tc_setup() {
+  return cudaFuncSetAttribute(chol_update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCuSmemBytes);
+}
+
+cudaError_t launch_chol_update_tc(const CUtensorMap *maps, const CholUnit *units, int nunits, int grid, float *C0,
+                                  float *C1, int64_t ld, int64_t n, int *err, uint64_t wait_ns, cudaStream_t st) {
+  if (nunits <= 0) return cudaSuccess;
+  chol_update_tc_kernel<<<grid, 192, kCuSmemBytes, st>>>(maps, units, nunits, C0, C1, ld, n, err,
+                                                         wait_ns ? wait_ns : kTimeoutNs);
+  return cudaGetLastError();
 }
 
 }  // namespace mnl
