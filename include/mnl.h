@@ -122,7 +122,7 @@ typedef struct mnl_step_info {
 /* mnl_step_info.factor_kind: the cooperative blocked Cholesky on the CUDA
  * cores (float32 in a mixed solve, float64 otherwise), or the panel
  * factorisation whose trailing updates run on the tensor cores (mixed solves
- * with n_theta >= 1024; environment variable MNL_TC_CHOL_MIN_N, read by
+ * with n_theta >= 4096; environment variable MNL_TC_CHOL_MIN_N, read by
  * mnl_create, moves that threshold). */
 enum { MNL_FACTOR_NONE = 0, MNL_FACTOR_COOP = 1, MNL_FACTOR_TENSOR = 2 };
 

@@ -125,7 +125,21 @@ struct BuildDims {
   int kc;  // classes per Y (and Z) staging chunk
   int f;   // Z operand (Az != nullptr): generic columns and its row-block offsets
   int64_t oY, oW, oZ;
+  int64_t rpA, rpZ;  // padded row counts of At / Ad and of Az (K-blocked layout)
 };
+
+// Element offset of operand row `row`, observation i.  float64 operands are
+// row-major ([rows][ldn]).  TF32 / BF16 operands, which the tensor cores read
+// through TMA, are K-blocked: [ldn / BK][rows_pad][BK] with BK = 32 (TF32) or
+// 64 (BF16) observations = 128 bytes, so that the 128-row box of one K-block
+// is 16 KB of contiguous memory (no strided rows: DRAM pages and TLB entries
+// stay few however large N is).
+template <OpType OT>
+__device__ __forceinline__ int64_t op_off(int64_t row, int64_t i, int64_t ldn, int64_t rows_pad) {
+  if (OT == OpType::F64) return row * ldn + i;
+  constexpr int BK = OT == OpType::TF32 ? kBkTf32 : kBkBf16;
+  return ((i / BK) * rows_pad + row) * BK + (i % BK);
+}
 
 // Shared memory, transposed so that observations are contiguous:
 //   PsT[K][kBs], WsT[K][kBs] (P and sqrt(P(1-P)), compute type),
@@ -200,7 +214,7 @@ __device__ __forceinline__ void build_block(const BuildDims &D, const float *__r
   constexpr bool kRand = OT == OpType::BF16;
   auto put_z = [&](int64_t row, const CT v[8]) {  // one row of the Z-block operand
     const uint4 rw = kRand ? words4(mix3(5u, (uint32_t)row, iobs)) : make_uint4(0u, 0u, 0u, 0u);
-    OpStore<OT>::put8(reinterpret_cast<unsigned char *>(Az) + (row * D.ldn + i0 + oc) * esz, v, rw);
+    OpStore<OT>::put8(reinterpret_cast<unsigned char *>(Az) + op_off<OT>(row, i0 + oc, D.ldn, D.rpZ) * esz, v, rw);
   };
   if (Az) {
     __syncthreads();
@@ -294,8 +308,9 @@ __device__ __forceinline__ void build_block(const BuildDims &D, const float *__r
         rd = make_uint4(__funnelshift_l(ra.x, ra.x, 16), __funnelshift_l(ra.y, ra.y, 16),
                         __funnelshift_l(ra.z, ra.z, 16), __funnelshift_l(ra.w, ra.w, 16));
       }
-      unsigned char *rowA = reinterpret_cast<unsigned char *>(At) + (c * D.ldn + i0 + oc) * esz;
-      unsigned char *rowD = reinterpret_cast<unsigned char *>(Ad) + (c * D.ldn + i0 + oc) * esz;
+      const int64_t off = op_off<OT>(c, i0 + oc, D.ldn, D.rpA) * esz;
+      unsigned char *rowA = reinterpret_cast<unsigned char *>(At) + off;
+      unsigned char *rowD = reinterpret_cast<unsigned char *>(Ad) + off;
       OpStore<OT>::put8(rowA, pv, ra);
       OpStore<OT>::put8(rowD, wv, rd);
     }
@@ -357,6 +372,7 @@ __global__ void __launch_bounds__(256) grouped_build_kernel(const GroupProblem *
   BuildDims D;
   D.N = g.N; D.ldn = g.ldn; D.K = g.K; D.p = g.p; D.d = g.d; D.q = g.p + g.d;
   D.ob = g.build_ob; D.kc = g.build_kc;
+  D.rpA = g.mc_pad; D.rpZ = 0;
   build_block<OT, PT>(D, g.X, g.Y, reinterpret_cast<const PT *>(g.P), g.At, g.Ad, it.idx);
 }
 
@@ -998,6 +1014,8 @@ cudaError_t launch_build_operands(const Shape &s, OpType t, const float *X, cons
                                   void *Ad, int64_t ldn, cudaStream_t st, const float *Z, const void *zbar, void *Az) {
   BuildDims D;
   D.N = s.N; D.ldn = ldn; D.K = s.K; D.p = s.p; D.d = s.d; D.q = s.q;
+  D.rpA = (s.mc + kTile - 1) / kTile * kTile;
+  D.rpZ = 0;
   const bool with_z = Az != nullptr && s.f > 0;
   build_blocking(s, t, &D.ob, &D.kc, with_z);
   D.f = with_z ? s.f : 0;
@@ -1005,6 +1023,7 @@ cudaError_t launch_build_operands(const Shape &s, OpType t, const float *X, cons
   if (with_z) {
     const ZopLayout L = zop_layout(s);
     D.oY = L.oY; D.oW = L.oW; D.oZ = L.oZ;
+    D.rpZ = L.rows_pad;
   }
   const size_t smem = build_smem_bytes(s, t, D.ob, D.kc, with_z);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;

@@ -227,7 +227,11 @@ cudaError_t launch_syrk_f64(const double *At, int64_t ldn, int64_t N, const int2
 // over a list of work units: unit = (tensor map, problem, output tile (ti, tj),
 // K-block range [kb0, kb1)), writing out[out_off .. + 128*128) transposed.
 // Units of problems with active[problem] == 0 are skipped (active may be null).
+// TF32 / BF16 operands in the K-blocked layout [ldn / BK][rows_pad][BK] (BK
+// observations = 128 bytes per row of a block; see op_off in hessian.cu).
 cudaError_t encode_operand_map(OpType t, const void *At, int64_t rows_pad, int64_t ldn, CUtensorMap *out);
+// A row-major float32 [rows][cols] matrix read as TF32 boxes of 128 rows x 32 columns.
+cudaError_t encode_rows_map(const float *A, int64_t rows, int64_t cols, CUtensorMap *out);
 int tc_kblocks(OpType t, int64_t ldn);
 int tc_pick_split(int ntiles, int kblocks, int num_sms);
 // K-blocks of one accumulation chunk of the tensor-core SYRK (16384 observations):
@@ -347,7 +351,7 @@ struct TcCholPlan {
   bool ready = false;
 };
 // Use the tensor-core factorisation for n_theta at or above this.
-constexpr int64_t kTcCholMinN = 1024;
+constexpr int64_t kTcCholMinN = 4096;
 size_t tc_chol_bytes(int64_t n);
 // Encodes the tensor maps and uploads the unit lists (synchronous; call at set-up).
 cudaError_t tc_chol_prepare(int64_t n, void *ws, int num_sms, TcCholPlan *plan);

@@ -819,10 +819,23 @@ __global__ void __launch_bounds__(256, 1) chol_diag128_kernel(const float *__res
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t j0 = (int64_t)k * kDp;
   const int nb = (int)(n - j0 < kDp ? n - j0 : kDp);
-  for (int e = tid; e < kDp * kDp; e += 256) {
-    const int c = e >> 7, r = e & 127;
-    D[c * kDd + r] = (r < nb && c < nb) ? (r >= c ? F32[(j0 + c) * ld + j0 + r] : 0.f) : (r == c ? 1.f : 0.f);
-    X[c * kDd + r] = 0.f;
+  // Loads in batches of 16 per thread, unconditional (an element outside the
+  // block's lower triangle reads the diagonal's first element instead and is
+  // replaced afterwards), so that they are all in flight at once.
+  for (int u0 = 0; u0 < kDp * kDp / 256; u0 += 16) {
+    float v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int e = tid + 256 * (u0 + u), c = e >> 7, r = e & 127;
+      const bool in = r < nb && c < nb && r >= c;
+      v[u] = F32[in ? (j0 + c) * ld + j0 + r : j0 * ld + j0];
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int e = tid + 256 * (u0 + u), c = e >> 7, r = e & 127;
+      D[c * kDd + r] = (r < nb && c < nb) ? (r >= c ? v[u] : 0.f) : (r == c ? 1.f : 0.f);
+      X[c * kDd + r] = 0.f;
+    }
   }
   for (int e = tid; e < 32 * kLts; e += 256) Lt[e] = 0.f;
   __syncthreads();
@@ -952,21 +965,34 @@ __global__ void __launch_bounds__(256, 2) chol_panel_kernel(const float *__restr
   const int64_t j0 = (int64_t)k * kDp, r_begin = j0 + kDp;
   const int na = (int)((n_pad - r_begin) / kPr), nbi = (int)(j0 / kPr);
   const float *Ik = InvT + (int64_t)k * kDp * kDp;
-  for (int e = tid; e < kDp * kDp; e += 256) Is[(e >> 7) * kDd + (e & 127)] = Ik[e];
+#pragma unroll 16
+  for (int u = 0; u < kDp * kDp / 256; ++u) {
+    const int e = tid + 256 * u;
+    Is[(e >> 7) * kDd + (e & 127)] = Ik[e];
+  }
   const int mend = 8 * ty + 8;  // Inv(kk, m) = 0 for m > kk >= 8 ty + 7
   for (int item = blockIdx.x; item < na + nbi; item += gridDim.x) {
     const bool rows = item < na;
     const int64_t x0 = rows ? r_begin + (int64_t)item * kPr : (int64_t)(item - na) * kPr;
     __syncthreads();  // Is is loaded; the previous item is done with Os
-    if (rows) {
-      for (int e = tid; e < kDp * kPr; e += 256) {
-        const int m = e >> 6, x = e & 63;
-        Os[m * kPs + x] = (x0 + x < n && j0 + m < n) ? F32[(j0 + m) * ld + x0 + x] : 0.f;
+    // batches of 16 unconditional loads per thread (out-of-range elements read
+    // element (j0, 0) of the operand and are replaced by zero)
+    const float *src = rows ? F32 : Li;
+    for (int u0 = 0; u0 < kDp * kPr / 256; u0 += 16) {
+      float v[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int e = tid + 256 * (u0 + u);
+        const int m = rows ? e >> 6 : e & 127, x = rows ? e & 63 : e >> 7;
+        const bool in = rows ? (x0 + x < n && j0 + m < n) : j0 + m < n;
+        v[u] = src[in ? (rows ? (j0 + m) * ld + x0 + x : (x0 + x) * ld + j0 + m) : j0];
       }
-    } else {
-      for (int e = tid; e < kDp * kPr; e += 256) {
-        const int x = e >> 7, m = e & 127;
-        Os[m * kPs + x] = j0 + m < n ? Li[(x0 + x) * ld + j0 + m] : 0.f;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int e = tid + 256 * (u0 + u);
+        const int m = rows ? e >> 6 : e & 127, x = rows ? e & 63 : e >> 7;
+        const bool in = rows ? (x0 + x < n && j0 + m < n) : j0 + m < n;
+        Os[m * kPs + x] = in ? v[u] : 0.f;
       }
     }
     __syncthreads();
@@ -1165,7 +1191,7 @@ cudaError_t tc_chol_prepare(int64_t n, void *ws, int num_sms, TcCholPlan *P) {
   CUtensorMap hm[4];
   cudaError_t e;
   for (int i = 0; i < 4; ++i)
-    if ((e = encode_operand_map(OpType::TF32, *bufs[i], P->n_pad, kDp, &hm[i])) != cudaSuccess) return e;
+    if ((e = encode_rows_map(*bufs[i], P->n_pad, kDp, &hm[i])) != cudaSuccess) return e;
   if ((e = cudaMemcpy(P->maps, hm, sizeof(hm), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
   if (!u.empty() && (e = cudaMemcpy(P->units, u.data(), u.size() * sizeof(CholUnit), cudaMemcpyHostToDevice)) !=
                         cudaSuccess)

@@ -117,6 +117,15 @@ __device__ __forceinline__ void tma_load_2d(const CUtensorMap *map, uint64_t *ba
       : "memory");
 }
 
+// Box (0, y, z) of a 3-D map: the K-blocked operands (K-block z, rows y ..).
+__device__ __forceinline__ void tma_load_3d(const CUtensorMap *map, uint64_t *bar, void *dst, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
+          "r"(saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(saddr(bar)), "r"(0), "r"(y), "r"(z)
+      : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -229,11 +238,11 @@ __global__ void __launch_bounds__(192, 1) syrk_tc_kernel(const CUtensorMap *__re
           if (!wait_bounded(&empty[stage], phase ^ 1u, abort_flag, err, kErrProducer)) { ok = false; break; }
           uint8_t *dst = smem + stage * kStageBytes;
           mbar_arrive_expect_tx(&full[stage], diag ? kOpBytes : (1 + BN / kTile) * kOpBytes);
-          tma_load_2d(map, &full[stage], dst, kb * kBk, w.ti * kTile);
+          tma_load_3d(map, &full[stage], dst, w.ti * kTile, kb);
           if (!diag)
 #pragma unroll
             for (int h = 0; h < BN / kTile; ++h)  // B: BN / 128 consecutive tiles (zero-filled past the last row)
-              tma_load_2d(map, &full[stage], dst + (1 + h) * kOpBytes, kb * kBk, (w.tj + h) * kTile);
+              tma_load_3d(map, &full[stage], dst + (1 + h) * kOpBytes, (w.tj + h) * kTile, kb);
           last_par[stage] = (int)phase;
           if (++stage == kStages) { stage = 0; phase ^= 1u; }
         }
@@ -536,16 +545,31 @@ cudaError_t encode_operand_map(OpType t, const void *At, int64_t rows_pad, int64
   const bool tf32 = t == OpType::TF32;
   const int bk = tf32 ? kBkTf32 : kBkBf16;
   const size_t esz = tf32 ? 4 : 2;
-  if (ldn % bk != 0 || (ldn * esz) % 16 != 0 || rows_pad % kTile != 0 ||
-      (reinterpret_cast<uintptr_t>(At) & 15) != 0)
+  if (ldn % bk != 0 || rows_pad % kTile != 0 || (reinterpret_cast<uintptr_t>(At) & 15) != 0)
     return cudaErrorInvalidValue;
-  cuuint64_t dims[2] = {(cuuint64_t)ldn, (cuuint64_t)rows_pad};
-  cuuint64_t strides[1] = {(cuuint64_t)(ldn * esz)};
-  cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)kTile};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(out, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+  // K-blocked layout [ldn / bk][rows_pad][bk]: one box = 128 rows x 128 bytes, contiguous
+  cuuint64_t dims[3] = {(cuuint64_t)bk, (cuuint64_t)rows_pad, (cuuint64_t)(ldn / bk)};
+  cuuint64_t strides[2] = {(cuuint64_t)(bk * esz), (cuuint64_t)(rows_pad * bk * esz)};
+  cuuint32_t box[3] = {(cuuint32_t)bk, (cuuint32_t)kTile, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(out, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
                    const_cast<void *>(At), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t encode_rows_map(const float *A, int64_t rows, int64_t cols, CUtensorMap *out) {
+  EncodeTiled enc = get_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  if (cols % kBkTf32 != 0 || rows % kTile != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0)
+    return cudaErrorInvalidValue;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(cols * sizeof(float))};
+  cuuint32_t box[2] = {(cuuint32_t)kBkTf32, (cuuint32_t)kTile};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(A), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -595,6 +619,25 @@ std::vector<SyrkUnit> schedule_syrk_units(const std::vector<SyrkUnit> &jobs, int
       per[(size_t)top.second].push_back(u);
     }
     heap.push({top.first + len + 8, top.second});  // 8 K-blocks of fixed cost per job
+  }
+  // Within a CTA, the chunks of its jobs are taken chunk-major (the first chunk of
+  // every job, then the second, ...; a job's chunks keep their order, so stores
+  // still precede adds): all CTAs then walk the same observation range at the
+  // same time however long the jobs are, which keeps the operand rows in L2.
+  for (auto &v : per) {
+    std::vector<std::vector<SyrkUnit>> jobs_of;
+    for (const SyrkUnit &u : v) {
+      if (!(u.flags & kUnitAcc)) jobs_of.emplace_back();
+      jobs_of.back().push_back(u);
+    }
+    std::vector<SyrkUnit> out2;
+    for (size_t c = 0;; ++c) {
+      bool any = false;
+      for (const auto &j : jobs_of)
+        if (c < j.size()) { out2.push_back(j[c]); any = true; }
+      if (!any) break;
+    }
+    v.swap(out2);
   }
   size_t depth = 0;
   for (const auto &v : per) depth = std::max(depth, v.size());
