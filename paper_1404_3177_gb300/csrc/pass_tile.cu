@@ -33,9 +33,12 @@ namespace {
 
 constexpr int kPT = 256;          // threads per CTA
 constexpr int kBetaItems = 2;     // beta-gradient register tiles per warp
-constexpr int kYZSlots = 2;       // gamma / alpha outputs per thread
+// gamma / alpha outputs per thread: YZS (a template parameter) = 2, or 4 when (K-1) d + K f > 512
 constexpr int kRegYZ = 8;         // d, f up to this: gamma and alpha coefficients in registers
 constexpr uint64_t kTileWaitNs = 2000000000ull;
+constexpr int kGbRows = 32;   // beta-gradient kernel: observations per tile
+constexpr int kGbStages = 3;  // and stages of its copy ring
+constexpr int kGbMaxJ = 8, kGbMaxK = 8;  // its register tile: up to 16 * 8 columns x 16 * 8 classes
 
 struct TileDims {
   int64_t N, ntiles;
@@ -45,6 +48,7 @@ struct TileDims {
   int stage_bytes, off_x, off_y, off_z, off_c;                       // within a stage
   int off_bt, off_gt, off_al, off_xt, off_rt, off_red, off_bar, off_stage;
   int kp2, lq, wk, wl, nyz;                                          // gradient work
+  int beta_ext;  // the beta gradient is left to grad_beta_kernel (too many outputs for the register tiles)
 };
 
 struct KahanF {
@@ -116,8 +120,9 @@ __device__ __forceinline__ void load_rows(const float *p, float v[RPW]) {
   }
 }
 
-template <int RPW, int CS, bool FULL>
-__global__ void __launch_bounds__(kPT, 2) pass_tile_kernel(TileDims D, PassIO io) {
+// kYZSlots = 4 is the wide-shape variant (one CTA per SM: its ring fills the shared memory).
+template <int RPW, int CS, bool FULL, int kYZSlots>
+__global__ void __launch_bounds__(kPT, kYZSlots == 4 ? 1 : 2) pass_tile_kernel(TileDims D, PassIO io) {
   extern __shared__ __align__(128) unsigned char sm[];
   float *Bt = reinterpret_cast<float *>(sm + D.off_bt);  // [p][Kpad]
   float *Gt = reinterpret_cast<float *>(sm + D.off_gt);  // [d][Kpad]
@@ -335,7 +340,7 @@ __global__ void __launch_bounds__(kPT, 2) pass_tile_kernel(TileDims D, PassIO io
     if (FULL) {
       __syncthreads();  // residuals of every row are in Rt
       // ---- beta gradient: warp item (wkp, wlq) covers classes 1 + 2 kp, 2 + 2 kp and columns 4 lq .. 4 lq + 3 ----
-      const int nitems = D.wk * D.wl;
+      const int nitems = D.beta_ext ? 0 : D.wk * D.wl;
 #pragma unroll
       for (int ii = 0; ii < kBetaItems; ++ii) {
         const int item = warp + 8 * ii;
@@ -406,7 +411,7 @@ __global__ void __launch_bounds__(kPT, 2) pass_tile_kernel(TileDims D, PassIO io
     out[1] = b;
   }
   if (!FULL) return;
-  const int nitems = D.wk * D.wl;
+  const int nitems = D.beta_ext ? 0 : D.wk * D.wl;
 #pragma unroll
   for (int ii = 0; ii < kBetaItems; ++ii) {
     const int item = warp + 8 * ii;
@@ -440,6 +445,155 @@ __global__ void __launch_bounds__(kPT, 2) pass_tile_kernel(TileDims D, PassIO io
     for (int k = 0; k < K; ++k) sa2 += red[k * f + j];
     out[2 + D.mc + j] = sa2;
   }
+}
+
+// ---------------------------------------------------------------------------
+// beta gradient for shapes whose (K - 1) p outputs do not fit the pass's
+// register tiles (eq. "loglik gradient"):  g_beta_k[j] = sum_i x_ij (I(y_i = k) - P_ik).
+// A tall-skinny product X^T R over the observations, R = onehot(y) - P, run
+// after the pass on the same grid: CTA b takes the tiles of kGbRows
+// observations b, b + grid, ... (X, P and choice rows by bulk asynchronous
+// copies into a 3-stage ring, bounded waits) and writes the beta entries of
+// its own partial row.  Thread (tx, ty) of a 16 x 16 grid owns the outputs
+// j = tx + 16 a (a < JA), k = ty + 16 b (b < KB); per tile the float32 sums
+// are folded into Kahan-compensated running sums.
+// ---------------------------------------------------------------------------
+template <int JA, int KB>
+__global__ void __launch_bounds__(256, 1) grad_beta_kernel(int64_t N, int K, int p, int64_t n,
+                                                           const float *__restrict__ X, const float *__restrict__ P,
+                                                           const int *__restrict__ choice, double *partials,
+                                                           int *err) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const int sx = ((kGbRows * p * 4) + 127) & ~127, sp = ((kGbRows * K * 4) + 127) & ~127;
+  const int stage_bytes = sx + sp + 128;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kGbStages * stage_bytes);
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t ntiles = (N + kGbRows - 1) / kGbRows;
+  if (tid == 0) {
+    s_abort = 0;
+    for (int st = 0; st < kGbStages; ++st)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sa(&bar[st])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const uint32_t tile_bytes = (uint32_t)(kGbRows * (p + K + 1) * 4);
+  auto full_tile = [&](int64_t tl) { return (tl + 1) * kGbRows <= N; };
+  auto issue = [&](int64_t tl, int st) {
+    const int64_t r0 = tl * kGbRows;
+    unsigned char *b = sm + st * stage_bytes;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(&bar[st])), "r"(tile_bytes)
+                 : "memory");
+    bulk_copy(b, X + r0 * p, (uint32_t)(kGbRows * p * 4), &bar[st]);
+    bulk_copy(b + sx, P + r0 * K, (uint32_t)(kGbRows * K * 4), &bar[st]);
+    bulk_copy(b + sx + sp, choice + r0, (uint32_t)(kGbRows * 4), &bar[st]);
+  };
+  int pend[kGbStages];
+  for (int st = 0; st < kGbStages; ++st) pend[st] = -1;
+  if (tid == 0)
+    for (int st = 0; st < kGbStages; ++st) {
+      const int64_t tl = blockIdx.x + (int64_t)st * gridDim.x;
+      if (tl < ntiles && full_tile(tl)) { issue(tl, st); pend[st] = 0; }
+    }
+  KahanF ks[JA][KB];
+  int it = 0;
+  for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x, ++it) {
+    const int st = it % kGbStages;
+    const uint32_t par = (uint32_t)((it / kGbStages) & 1);
+    unsigned char *b = sm + st * stage_bytes;
+    float *Xs = reinterpret_cast<float *>(b);
+    float *Ps = reinterpret_cast<float *>(b + sx);
+    int *cs = reinterpret_cast<int *>(b + sx + sp);
+    const int64_t r0 = tl * kGbRows;
+    const int nrows = (int)(N - r0 < kGbRows ? N - r0 : kGbRows);
+    if (nrows == kGbRows) {
+      if (!stage_wait(&bar[st], par)) s_abort = 1;
+      else if (tid == 0) pend[st] = -1;
+    } else {  // the partial last tile: plain loads, zero padding
+      for (int e = tid; e < kGbRows * p; e += 256) Xs[e] = e < nrows * p ? X[r0 * p + e] : 0.f;
+      for (int e = tid; e < kGbRows * K; e += 256) Ps[e] = e < nrows * K ? P[r0 * K + e] : 0.f;
+      for (int e = tid; e < kGbRows; e += 256) cs[e] = e < nrows ? choice[r0 + e] : -1;
+    }
+    __syncthreads();
+    if (s_abort) break;
+    float acc[JA][KB];
+#pragma unroll
+    for (int a = 0; a < JA; ++a)
+#pragma unroll
+      for (int c = 0; c < KB; ++c) acc[a][c] = 0.f;
+#pragma unroll 2
+    for (int r = 0; r < kGbRows; ++r) {
+      const int y = cs[r];
+      float x[JA], rr[KB];
+#pragma unroll
+      for (int a = 0; a < JA; ++a) {
+        const int j = tx + 16 * a;
+        x[a] = j < p ? Xs[r * p + j] : 0.f;
+      }
+#pragma unroll
+      for (int c = 0; c < KB; ++c) {
+        const int k = ty + 16 * c;
+        rr[c] = k < K ? (k == y ? 1.f : 0.f) - Ps[r * K + k] : 0.f;
+      }
+#pragma unroll
+      for (int a = 0; a < JA; ++a)
+#pragma unroll
+        for (int c = 0; c < KB; ++c) acc[a][c] = fmaf(x[a], rr[c], acc[a][c]);
+    }
+#pragma unroll
+    for (int a = 0; a < JA; ++a)
+#pragma unroll
+      for (int c = 0; c < KB; ++c) ks[a][c].add(acc[a][c]);
+    __syncthreads();  // the stage is free
+    if (tid == 0) {
+      const int64_t nx = tl + (int64_t)kGbStages * gridDim.x;
+      if (nx < ntiles && full_tile(nx)) { issue(nx, st); pend[st] = (int)(((it + kGbStages) / kGbStages) & 1); }
+    }
+  }
+  if (s_abort) {
+    if (tid == 0) {
+      atomicOr(err, 16);
+      for (int st = 0; st < kGbStages; ++st)
+        if (pend[st] >= 0) stage_wait(&bar[st], (uint32_t)pend[st]);
+    }
+    __syncthreads();
+    return;
+  }
+  double *out = partials + (int64_t)blockIdx.x * (2 + n);
+#pragma unroll
+  for (int a = 0; a < JA; ++a)
+#pragma unroll
+    for (int c = 0; c < KB; ++c) {
+      const int j = tx + 16 * a, k = ty + 16 * c;
+      if (j < p && k >= 1 && k < K) out[2 + (int64_t)(k - 1) * p + j] = ks[a][c].value();
+    }
+}
+
+size_t grad_beta_smem(int K, int p) {
+  const int sx = ((kGbRows * p * 4) + 127) & ~127, sp = ((kGbRows * K * 4) + 127) & ~127;
+  return (size_t)kGbStages * (sx + sp + 128) + kGbStages * 8;
+}
+
+template <int JA, int KB>
+cudaError_t launch_gb(const Shape &s, int grid, const PassIO &io, cudaStream_t st) {
+  auto kern = grad_beta_kernel<JA, KB>;
+  const size_t smem = grad_beta_smem(s.K, s.p);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, 256, smem, st>>>(s.N, s.K, s.p, s.n, io.X, reinterpret_cast<const float *>(io.P), io.choice,
+                                io.partials, io.err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_beta(const Shape &s, int grid, const PassIO &io, cudaStream_t st) {
+  const int ja = (s.p + 15) / 16, kb = (s.K + 15) / 16;
+  // register tiles of 4, 7 or 8 (columns) x 4, 7 or 8 (classes)
+  const int JA = ja <= 4 ? 4 : ja <= 7 ? 7 : 8, KBv = kb <= 4 ? 4 : kb <= 7 ? 7 : 8;
+  if (ja > 8 || kb > 8) return cudaErrorInvalidValue;
+#define MNL_GB(a, b) if (JA == a && KBv == b) return launch_gb<a, b>(s, grid, io, st);
+  MNL_GB(4, 4) MNL_GB(4, 7) MNL_GB(4, 8) MNL_GB(7, 4) MNL_GB(7, 7) MNL_GB(7, 8) MNL_GB(8, 4) MNL_GB(8, 7) MNL_GB(8, 8)
+#undef MNL_GB
+  return cudaErrorInvalidValue;
 }
 
 int round_up_int(int v, int m) { return (v + m - 1) / m * m; }
@@ -476,9 +630,11 @@ bool make_tile_dims(const Shape &s, bool full, int rpw, TileDims &D, size_t &sme
   D.wk = (D.kp2 + 3) / 4;
   D.wl = (D.lq + 7) / 8;
   D.nyz = (s.K - 1) * s.d + s.K * s.f;
-  if (full && (D.wk * D.wl > 8 * kBetaItems || D.nyz > kPT * kYZSlots)) return false;
+  D.beta_ext = full && D.wk * D.wl > 8 * kBetaItems;
+  if (D.beta_ext && (s.p > 16 * kGbMaxJ || s.K > 16 * kGbMaxK)) return false;
+  if (full && D.nyz > kPT * 4) return false;
   // two CTAs per SM when a 2-stage ring fits in half of the shared memory, else one
-  for (size_t budget : {(size_t)110 * 1024, (size_t)200 * 1024})
+  for (size_t budget : {(size_t)110 * 1024, (size_t)224 * 1024})
     for (int S = 3; S >= 2; --S) {
       const size_t b = (size_t)o + (size_t)S * D.stage_bytes;
       if (b <= budget) { D.S = S; smem = b; return true; }
@@ -486,9 +642,9 @@ bool make_tile_dims(const Shape &s, bool full, int rpw, TileDims &D, size_t &sme
   return false;
 }
 
-template <int RPW, int CS, bool FULL>
+template <int RPW, int CS, bool FULL, int YZS>
 cudaError_t launch_t(const TileDims &D, int grid, size_t smem, const PassIO &io, cudaStream_t st) {
-  auto kern = pass_tile_kernel<RPW, CS, FULL>;
+  auto kern = pass_tile_kernel<RPW, CS, FULL, YZS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, kPT, smem, st>>>(D, io);
@@ -497,11 +653,12 @@ cudaError_t launch_t(const TileDims &D, int grid, size_t smem, const PassIO &io,
 
 template <int RPW, bool FULL>
 cudaError_t launch_cs(const TileDims &D, int grid, size_t smem, const PassIO &io, cudaStream_t st) {
+  const bool wide = FULL && D.nyz > kPT * 2;
   switch (D.Kpad / 32) {
-    case 1: return launch_t<RPW, 1, FULL>(D, grid, smem, io, st);
-    case 2: return launch_t<RPW, 2, FULL>(D, grid, smem, io, st);
-    case 4: return launch_t<RPW, 4, FULL>(D, grid, smem, io, st);
-    case 8: return launch_t<RPW, 8, FULL>(D, grid, smem, io, st);
+    case 1: return wide ? launch_t<RPW, 1, FULL, 4>(D, grid, smem, io, st) : launch_t<RPW, 1, FULL, 2>(D, grid, smem, io, st);
+    case 2: return wide ? launch_t<RPW, 2, FULL, 4>(D, grid, smem, io, st) : launch_t<RPW, 2, FULL, 2>(D, grid, smem, io, st);
+    case 4: return wide ? launch_t<RPW, 4, FULL, 4>(D, grid, smem, io, st) : launch_t<RPW, 4, FULL, 2>(D, grid, smem, io, st);
+    case 8: return wide ? launch_t<RPW, 8, FULL, 4>(D, grid, smem, io, st) : launch_t<RPW, 8, FULL, 2>(D, grid, smem, io, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -534,8 +691,11 @@ cudaError_t launch_pass_tiled(const Shape &s, const PassPlan &pl, bool full, con
                          (s.d ? reinterpret_cast<uintptr_t>(io.Y) : 0) | (s.f ? reinterpret_cast<uintptr_t>(io.Z) : 0)) &
                         15) == 0;
   if (!aligned) return cudaErrorInvalidValue;
-  if (pl.rows == 16) return full ? launch_cs<2, true>(D, pl.grid, smem, io, st) : launch_cs<2, false>(D, pl.grid, smem, io, st);
-  return cudaErrorInvalidValue;
+  if (pl.rows != 16) return cudaErrorInvalidValue;
+  if (!full) return launch_cs<2, false>(D, pl.grid, smem, io, st);
+  cudaError_t e = launch_cs<2, true>(D, pl.grid, smem, io, st);
+  if (e == cudaSuccess && D.beta_ext) e = launch_grad_beta(s, pl.grid, io, st);
+  return e;
 }
 
 }  // namespace mnl

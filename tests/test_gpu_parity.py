@@ -96,6 +96,8 @@ EDGE_SHAPES = [
     (1500, 3, 150, 0, 0, True),   # q > 128: a class block spans three tiles
     (2000, 9, 7, 0, 0, False),    # X only, no intercept
     (2100, 4, 0, 5, 0, False),    # Y only
+    (3001, 70, 40, 0, 8, True),   # wide: beta gradient in its own kernel, 4 gamma/alpha slots per thread
+    (1037, 128, 120, 1, 1, False),  # widest shape of that kernel (p, K up to 128)
 ]
 
 
