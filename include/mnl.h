@@ -339,6 +339,11 @@ MNL_API int mnl_server_step(mnl_server *s, int32_t *n_active, int32_t *n_queued)
 /* MNL_OK and the result (theta: HOST [n_theta] or NULL) once the request has
  * finished - the ticket is then released; MNL_PENDING before that. */
 MNL_API int mnl_server_poll(mnl_server *s, uint64_t ticket, double *theta, mnl_request_result *result);
+/* Tickets of requests that finished since the previous call (up to cap of
+ * them, oldest first; those beyond cap are kept for the next call), so that a
+ * caller polls only requests that are done.  *count receives how many were
+ * written to tickets (HOST [cap]). */
+MNL_API int mnl_server_finished(mnl_server *s, uint64_t *tickets, int32_t cap, int32_t *count);
 /* Device bytes held by admitted requests. */
 MNL_API size_t mnl_server_memory_in_use(const mnl_server *s);
 MNL_API int mnl_server_destroy(mnl_server *s);

@@ -35,7 +35,7 @@ EXPORTS = (
     "mnl_upload", "mnl_loglik_grad", "mnl_hessian", "mnl_newton_step", "mnl_fit", "mnl_destroy",
     "mnl_loglik_grad_noalloc", "mnl_set_solve", "mnl_batch_create", "mnl_batch_num_params", "mnl_batch_fit",
     "mnl_batch_destroy", "mnl_server_opts_default", "mnl_server_create", "mnl_server_submit", "mnl_server_step",
-    "mnl_server_poll", "mnl_server_memory_in_use", "mnl_server_destroy",
+    "mnl_server_poll", "mnl_server_finished", "mnl_server_memory_in_use", "mnl_server_destroy",
 )
 
 MNL_SOLVE_AUTO, MNL_SOLVE_FP64, MNL_SOLVE_MIXED = 0, 1, 2
@@ -161,6 +161,8 @@ def load() -> C.CDLL:
         lib.mnl_server_step.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         lib.mnl_server_poll.restype = i32
         lib.mnl_server_poll.argtypes = [vp, C.c_uint64, vp, C.POINTER(mnl_request_result)]
+        lib.mnl_server_finished.restype = i32
+        lib.mnl_server_finished.argtypes = [vp, C.POINTER(C.c_uint64), C.c_int32, C.POINTER(C.c_int32)]
         lib.mnl_server_memory_in_use.restype = C.c_size_t
         lib.mnl_server_memory_in_use.argtypes = [vp]
         lib.mnl_server_destroy.restype = i32
@@ -325,6 +327,13 @@ def mnl_server_poll(handle: int, ticket: int, theta_ptr: int | None):
         return False, None
     _check(rc, "mnl_server_poll")
     return True, struct_dict(res)
+
+
+def mnl_server_finished(handle: int, cap: int = 4096) -> list[int]:
+    buf = (C.c_uint64 * cap)()
+    n = C.c_int32()
+    _check(load().mnl_server_finished(handle, buf, cap, C.byref(n)), "mnl_server_finished")
+    return list(buf[: n.value])
 
 
 def mnl_server_memory_in_use(handle: int) -> int:

@@ -220,6 +220,17 @@ class MNLServer:
         del self._sizes[ticket]
         return out, res
 
+    def finished(self):
+        """(ticket, result dict) of every request that finished since the last call (theta: poll it first)."""
+        out = []
+        while True:
+            ts = nat.mnl_server_finished(self.h)
+            for t in ts:
+                r = self.poll(t)
+                out.append((t, r[1]))
+            if len(ts) < 4096:
+                return out
+
     def memory_in_use(self):
         return nat.mnl_server_memory_in_use(self.h)
 

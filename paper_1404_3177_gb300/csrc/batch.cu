@@ -969,6 +969,7 @@ struct mnl_server {
   std::deque<uint64_t> queue;
   std::vector<uint64_t> members;
   std::map<uint64_t, Request> reqs;
+  std::vector<uint64_t> finished;  // retired, not yet reported by mnl_server_finished
   bool dirty = true;
   std::mutex mu;
   int ticks = 0;
@@ -1182,6 +1183,7 @@ int mnl_server_step(mnl_server *s, int32_t *n_active, int32_t *n_queued) {
       r.res.latency_ms = std::chrono::duration<double, std::milli>(now - r.t_submit).count();
       r.res.queue_ms = std::chrono::duration<double, std::milli>(r.t_admit - r.t_submit).count();
       r.done = true;
+      s->finished.push_back(s->members[i]);
       s->pool.release(r.off, r.L.bytes);
       r.X.clear(); r.X.shrink_to_fit();
       r.Y.clear(); r.Y.shrink_to_fit();
@@ -1205,6 +1207,16 @@ int mnl_server_poll(mnl_server *s, uint64_t ticket, double *theta, mnl_request_r
   if (theta) std::copy(it->second.theta_out.begin(), it->second.theta_out.end(), theta);
   if (res) *res = it->second.res;
   s->reqs.erase(it);
+  return MNL_OK;
+}
+
+int mnl_server_finished(mnl_server *s, uint64_t *tickets, int32_t cap, int32_t *count) {
+  if (!s || !count || cap < 0 || (cap > 0 && !tickets)) return MNL_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(s->mu);
+  const int32_t k = (int32_t)std::min<size_t>((size_t)cap, s->finished.size());
+  std::copy(s->finished.begin(), s->finished.begin() + k, tickets);
+  s->finished.erase(s->finished.begin(), s->finished.begin() + k);
+  *count = k;
   return MNL_OK;
 }
 
