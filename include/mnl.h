@@ -117,7 +117,14 @@ typedef struct mnl_step_info {
   int32_t refine_steps;/* refinement steps of a mixed solve                 */
   int32_t fallback;    /* 1 when a mixed solve fell back to float64          */
   int32_t factor_kind; /* factorisation of the (first) solve: MNL_FACTOR_*   */
+  int32_t wait_errors; /* after MNL_ERR_TIMEOUT: MNL_WAIT_* bits of the kernels whose waits gave up */
 } mnl_step_info;
+
+/* mnl_step_info.wait_errors: which kernels' bounded device waits gave up
+ * (the tensor-core contraction of the Hessian, the pass's tile copies, the
+ * cooperative factorisation's grid barrier, the tensor-core trailing updates
+ * of the panel factorisation). */
+enum { MNL_WAIT_SYRK = 15, MNL_WAIT_PASS = 16, MNL_WAIT_COOP = 32, MNL_WAIT_PANEL = 64 };
 
 /* mnl_step_info.factor_kind: the cooperative blocked Cholesky on the CUDA
  * cores (float32 in a mixed solve, float64 otherwise), or the panel
@@ -233,6 +240,15 @@ MNL_API int mnl_fit(mnl_handle *h, const mnl_fit_opts *opts, double *theta, mnl_
  *   MNL_SOLVE_AUTO (default): FP64 for MNL_FP64 handles, MIXED otherwise. */
 enum { MNL_SOLVE_AUTO = 0, MNL_SOLVE_FP64 = 1, MNL_SOLVE_MIXED = 2 };
 MNL_API int mnl_set_solve(mnl_handle *h, int mode);
+
+/* Bound, in nanoseconds, of every bounded device-side wait of this handle's
+ * kernels (pipeline stages, tile copies, grid barriers); 0 restores their
+ * defaults (2 s, 4 s for a grid barrier).  A wait that runs out makes every
+ * block of its kernel stop (after waiting, with the default bound, for the
+ * copies and tensor-core operations it has issued) and the call returns
+ * MNL_ERR_TIMEOUT; the handle stays usable.  A bound shorter than the work
+ * between two waits makes every call time out: it exists to test that path. */
+MNL_API int mnl_set_wait_bound(mnl_handle *h, uint64_t ns);
 
 /* Free the handle and every device buffer it owns (NULL is a no-op). */
 MNL_API int mnl_destroy(mnl_handle *h);
@@ -367,12 +383,17 @@ MNL_API int mnl_server_destroy(mnl_server *s);
  *   zbar        DEVICE [N][f] expected Z per observation, sum_k P_ik Z_ik
  *               (same type as P); NULL when f = 0.
  *   stream      cudaStream_t (as void*); the call only enqueues work.
- * Scratch: a fixed 4 MiB array inside the library holds the partial sums
- * between the two kernels of the pass; every GPU that loads the library keeps
- * it until the process exits.  Problems needing more than that, i.e. with
- * (K-1)(p+d) + K f > 524284, or with K > 256, return MNL_ERR_UNSUPPORTED.
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Limits: (K-1)(p+d) + K f <= 16384 raw gradient sums and K <= 256, and the
+ * pass's tile of one observation's X, Y, Z rows must fit its shared memory
+ * (p + K (d + f) up to about 50000 floats); beyond them the call returns
+ * MNL_ERR_UNSUPPORTED (the size limits before any CUDA call).
+ * Scratch: a fixed 4 MiB array inside the library holds the per-block partial
+ * sums between the two kernels of the pass ((K-1)(p+d) + f + 2 doubles per
+ * block; large problems run on fewer blocks so that they fit); every GPU that
+ * loads the library keeps it until the process exits.  The first call on each
+ * device (and after a device reset, in the new context) looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.
  * All calls share the one array: calls that can overlap on the GPU (other
  * streams, other threads) race and corrupt each other's results, so order
  * them, e.g. on one stream.  Nothing in the array needs to start at zero;

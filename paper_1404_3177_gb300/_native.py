@@ -33,12 +33,14 @@ MNL_STOP_GTOL, MNL_STOP_FTOL, MNL_STOP_STEPTOL, MNL_STOP_MAXITER, MNL_STOP_NOISE
 EXPORTS = (
     "mnl_num_params", "mnl_status_string", "mnl_workspace_bytes", "mnl_fit_opts_default", "mnl_create",
     "mnl_upload", "mnl_loglik_grad", "mnl_hessian", "mnl_newton_step", "mnl_fit", "mnl_destroy",
-    "mnl_loglik_grad_noalloc", "mnl_set_solve", "mnl_batch_create", "mnl_batch_num_params", "mnl_batch_fit",
+    "mnl_loglik_grad_noalloc", "mnl_set_solve", "mnl_set_wait_bound", "mnl_batch_create", "mnl_batch_num_params", "mnl_batch_fit",
     "mnl_batch_destroy", "mnl_server_opts_default", "mnl_server_create", "mnl_server_submit", "mnl_server_step",
     "mnl_server_poll", "mnl_server_finished", "mnl_server_memory_in_use", "mnl_server_destroy",
 )
 
 MNL_SOLVE_AUTO, MNL_SOLVE_FP64, MNL_SOLVE_MIXED = 0, 1, 2
+MNL_FACTOR_NONE, MNL_FACTOR_COOP, MNL_FACTOR_TENSOR = 0, 1, 2
+MNL_WAIT_SYRK, MNL_WAIT_PASS, MNL_WAIT_COOP, MNL_WAIT_PANEL = 15, 16, 32, 64
 SOLVES = {"auto": MNL_SOLVE_AUTO, "fp64": MNL_SOLVE_FP64, "mixed": MNL_SOLVE_MIXED}
 
 
@@ -60,7 +62,7 @@ class mnl_step_info(C.Structure):
                 ("t_band_ms", C.c_float), ("t_zblk_ms", C.c_float), ("t_asm_ms", C.c_float),
                 ("t_factor_ms", C.c_float), ("t_solve_ms", C.c_float), ("t_fallback_ms", C.c_float),
                 ("launches", C.c_int32), ("solve_mode", C.c_int32), ("refine_steps", C.c_int32),
-                ("fallback", C.c_int32), ("factor_kind", C.c_int32)]
+                ("fallback", C.c_int32), ("factor_kind", C.c_int32), ("wait_errors", C.c_int32)]
 
 
 class mnl_fit_opts(C.Structure):
@@ -141,6 +143,8 @@ def load() -> C.CDLL:
         lib.mnl_newton_step.argtypes = [vp, vp, C.POINTER(mnl_step_info)]
         lib.mnl_fit.restype = i32
         lib.mnl_fit.argtypes = [vp, C.POINTER(mnl_fit_opts), vp, C.POINTER(mnl_fit_info)]
+        lib.mnl_set_wait_bound.restype = i32
+        lib.mnl_set_wait_bound.argtypes = [vp, C.c_uint64]
         lib.mnl_destroy.restype = i32
         lib.mnl_destroy.argtypes = [vp]
         lib.mnl_batch_create.restype = i32
@@ -233,8 +237,13 @@ def mnl_hessian(handle: int, theta_ptr: int, H_ptr: int) -> None:
 
 
 def mnl_newton_step(handle: int, theta_ptr: int) -> mnl_step_info:
+    """Raises MnlError on failure; after MNL_ERR_TIMEOUT its `info` holds the step info (wait_errors)."""
     info = mnl_step_info()
-    _check(load().mnl_newton_step(C.c_void_p(handle), C.c_void_p(theta_ptr), C.byref(info)), "mnl_newton_step")
+    rc = load().mnl_newton_step(C.c_void_p(handle), C.c_void_p(theta_ptr), C.byref(info))
+    if rc != MNL_OK:
+        err = MnlError(rc, "mnl_newton_step")
+        err.info = struct_dict(info)
+        raise err
     return info
 
 
@@ -248,6 +257,10 @@ def mnl_fit(handle: int, opts: mnl_fit_opts | None, theta_ptr: int) -> mnl_fit_i
 
 def mnl_set_solve(handle: int, mode: int) -> None:
     _check(load().mnl_set_solve(C.c_void_p(handle), mode), "mnl_set_solve")
+
+
+def mnl_set_wait_bound(handle: int, ns: int) -> None:
+    _check(load().mnl_set_wait_bound(C.c_void_p(handle), C.c_uint64(ns)), "mnl_set_wait_bound")
 
 
 def mnl_destroy(handle: int) -> None:

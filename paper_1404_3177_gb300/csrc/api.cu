@@ -262,6 +262,7 @@ int run_pass(mnl_handle *h, const double *theta, bool full, const double *delta,
   const PassPlan &pl = full ? h->pfull : h->pll;
   io.partials = full ? h->part_full : h->part_ll;
   io.err = h->err;
+  io.wait_ns = h->wait_ns;
   CK(launch_pass(h->S, pl, h->fp64, full, io, h->st));
   CK(launch_pass_reduce(h->S, pl.grid, full, io.partials, h->scal + base, full ? h->grad : nullptr, h->st));
   h->launches += 2;
@@ -296,10 +297,10 @@ int run_hessian(mnl_handle *h, cudaEvent_t *ev = nullptr) {
                          h->band_split, reinterpret_cast<double *>(h->band_part), h->st));
     } else {
       CK(launch_syrk_tc(h->op, h->maps, h->units_main, h->nunits_main, nullptr, h->grid_main,
-                        reinterpret_cast<float *>(h->main_part), h->err, h->st, 256));
+                        reinterpret_cast<float *>(h->main_part), h->err, h->st, 256, h->wait_ns));
       if ((rc = mark(h, ev ? ev + 1 : nullptr))) return rc;
       CK(launch_syrk_tc(h->op, h->maps, h->units_band, h->nunits_band, nullptr, h->grid_band,
-                        reinterpret_cast<float *>(h->band_part), h->err, h->st));
+                        reinterpret_cast<float *>(h->band_part), h->err, h->st, 128, h->wait_ns));
     }
     h->launches += 2;
   } else {
@@ -307,7 +308,8 @@ int run_hessian(mnl_handle *h, cudaEvent_t *ev = nullptr) {
   }
   if ((rc = mark(h, ev ? ev + 2 : nullptr))) return rc;
   if (S.f > 0 && h->tcz) {
-    CK(launch_syrk_tc(h->op, h->maps, h->units_z, h->nunits_z, nullptr, h->grid_z, h->zt_part, h->err, h->st));
+    CK(launch_syrk_tc(h->op, h->maps, h->units_z, h->nunits_z, nullptr, h->grid_z, h->zt_part, h->err, h->st, 128,
+                      h->wait_ns));
     h->launches += 1;
   } else if (S.f > 0) {
     CK(launch_zblocks(S, h->fp64, h->X, h->Y, h->Z, h->P, h->zbar, h->z_split, h->z_part, h->st));
@@ -406,11 +408,11 @@ int step_impl(mnl_handle *h, double *theta, mnl_step_info *info, double gtol, bo
     CK(cudaEventRecord(h->ev[9], h->st));
   } else if (mixed) {
     CK(launch_mixed_solve(n, h->F, h->F32, h->grad, h->delta, h->mwork, h->status, h->err, kRefineIters, h->st,
-                          &nl, true));
+                          &nl, true, h->wait_ns));
     h->launches += nl;
     CK(cudaEventRecord(h->ev[9], h->st));
   } else {
-    CK(launch_cholesky(n, h->F, h->dinv, h->cwork, h->status, h->err, h->st));
+    CK(launch_cholesky(n, h->F, h->dinv, h->cwork, h->status, h->err, h->st, h->wait_ns));
     h->launches += cholesky_launches(n);
     CK(cudaEventRecord(h->ev[9], h->st));
     CK(launch_cholesky_solve(n, h->F, h->dinv, h->grad, h->delta, h->status, h->st, &nl));
@@ -434,7 +436,11 @@ int step_impl(mnl_handle *h, double *theta, mnl_step_info *info, double gtol, bo
   CK(cudaMemcpyAsync(h->h_flags + 1, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   if (mixed) CK(cudaMemcpyAsync(h->h_scal + 12, h->ref, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
-  if (h->h_flags[1]) return MNL_ERR_TIMEOUT;
+  if (h->h_flags[1]) {
+    loc.wait_errors = h->h_flags[1];
+    if (info) *info = loc;
+    return MNL_ERR_TIMEOUT;
+  }
   const double l0 = h->h_scal[kL], labs = h->h_scal[kLabs], ginf = h->h_scal[kGinf];
   if (!std::isfinite(l0) || !std::isfinite(ginf)) return MNL_ERR_NONFINITE;
   loc.solve_mode = h->solve_mode;
@@ -472,14 +478,18 @@ int step_impl(mnl_handle *h, double *theta, mnl_step_info *info, double gtol, bo
     // float32 factor or refinement failed: float64 Cholesky of the intact F
     loc.fallback = 1;
     CK(cudaEventRecord(h->ev[10], h->st));
-    CK(launch_cholesky(n, h->F, h->dinv, h->cwork, h->status, h->err, h->st));
+    CK(launch_cholesky(n, h->F, h->dinv, h->cwork, h->status, h->err, h->st, h->wait_ns));
     CK(launch_cholesky_solve(n, h->F, h->dinv, h->grad, h->delta, h->status, h->st, &nl));
     h->launches += cholesky_launches(n) + nl;
     CK(cudaEventRecord(h->ev[11], h->st));
     CK(cudaMemcpyAsync(h->h_flags, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(h->h_flags + 1, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
-    if (h->h_flags[1]) return MNL_ERR_TIMEOUT;
+    if (h->h_flags[1]) {
+      loc.wait_errors = h->h_flags[1];
+      if (info) *info = loc;
+      return MNL_ERR_TIMEOUT;
+    }
     t_fallback = elapsed(h->ev[10], h->ev[11]);
   }
   if (h->h_flags[0] & 4) return MNL_ERR_NOT_PD;
@@ -830,12 +840,15 @@ int mnl_loglik_grad(mnl_handle *h, const double *theta, double *loglik, double *
   if (rc) return rc;
   if (!theta) return MNL_ERR_INVALID_ARG;
   if ((rc = set_device(h))) return rc;
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->st));
   rc = run_pass(h, theta, grad != nullptr, nullptr, kL);
   if (rc) return rc;
   if (grad) CK(cudaMemcpyAsync(grad, h->grad, h->S.n * 8, cudaMemcpyDeviceToDevice, h->st));
   if (loglik) {
     CK(cudaMemcpyAsync(h->h_scal, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(h->h_flags + 1, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
+    if (h->h_flags[1]) return MNL_ERR_TIMEOUT;
     *loglik = h->h_scal[0];
   }
   return MNL_OK;
@@ -910,6 +923,12 @@ int mnl_fit(mnl_handle *h, const mnl_fit_opts *opts, double *theta, mnl_fit_info
   fi.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = fi;
   return rc;
+}
+
+int mnl_set_wait_bound(mnl_handle *h, uint64_t ns) {
+  if (!h) return MNL_ERR_INVALID_ARG;
+  h->wait_ns = ns;
+  return MNL_OK;
 }
 
 int mnl_set_solve(mnl_handle *h, int mode) {

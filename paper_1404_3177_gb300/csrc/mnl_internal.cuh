@@ -89,7 +89,14 @@ struct PassIO {
   void *zbar;            // [N][f] T, FULL mode only
   double *partials;      // [grid][2 + n] (FULL) or [grid][2] (loglik only)
   int *err;              // error word (bit 16: a tile copy did not complete in time); tiled pass only
+  uint64_t wait_ns;      // bound of the tile-copy waits (0: the default, 2 s)
 };
+
+// Bits of the device error word: which kernel's bounded wait gave up.
+constexpr int kWaitSyrk = 1 | 2 | 4 | 8;  // tensor-core contraction (producer, MMA, epilogue, drain)
+constexpr int kWaitPass = 16;             // tiled pass / beta-gradient tile copies
+constexpr int kWaitCoop = 32;             // cooperative factorisation's grid barrier
+constexpr int kWaitPanel = 64;            // tensor-core trailing updates of the panel factorisation
 
 // Configuration of the fused utility/softmax/log-likelihood/gradient pass.
 struct PassPlan {
@@ -245,7 +252,7 @@ int tc_chunk_kblocks(OpType t);
 std::vector<SyrkUnit> schedule_syrk_units(const std::vector<SyrkUnit> &jobs, int grid, int max_kb);
 size_t tc_smem_bytes();
 cudaError_t launch_syrk_tc(OpType t, const CUtensorMap *maps, const SyrkUnit *units, int nunits, const int *active,
-                           int grid, float *out, int *err, cudaStream_t st, int bn = 128);
+                           int grid, float *out, int *err, cudaStream_t st, int bn = 128, uint64_t wait_ns = 0);
 
 // Z blocks (FP32 or FP64 accumulation) per observation split s:
 // out[s][zblocks_outputs()] = [C_X: p*K*f | C_Y: K*d*f | A: f*f] (see hessian.cu).
@@ -295,7 +302,8 @@ cudaError_t launch_export_hessian(int64_t n, const double *F, double *H, cudaStr
 // grid barrier wait ran out (the kernel then returns early).
 size_t chol_work_bytes(int64_t n);
 int cholesky_launches(int64_t n);
-cudaError_t launch_cholesky(int64_t n, double *F, double *dinv, void *work, int *status, int *err, cudaStream_t st);
+cudaError_t launch_cholesky(int64_t n, double *F, double *dinv, void *work, int *status, int *err, cudaStream_t st,
+                            uint64_t wait_ns = 0);
 // Solve L L^T x = b with the factor above (FP64; skipped when status & 4).
 cudaError_t launch_cholesky_solve(int64_t n, const double *L, const double *dinv, const double *b, double *x,
                                   const int *status, cudaStream_t st, int *launches);
@@ -310,7 +318,7 @@ double *mixed_solve_ref(void *work, int64_t n);
 // f32_ready: F32 already holds the float32 lower triangle of F (written by the assembly).
 cudaError_t launch_mixed_solve(int64_t n, const double *F, float *F32, const double *g, double *delta, void *work,
                                int *status, int *err, int iters, cudaStream_t st, int *launches,
-                               bool f32_ready = false);
+                               bool f32_ready = false, uint64_t wait_ns = 0);
 // status &= mask (device word).
 cudaError_t launch_status_and(int *status, int mask, cudaStream_t st);
 // `iters` more refinement steps after launch_mixed_solve (the caller first clears status bit 16).

@@ -19,18 +19,45 @@ namespace {
 constexpr size_t kScratchDoubles = size_t(1) << 19;  // 4 MiB per GPU
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
+// Largest raw gradient count (K-1)(p+d) + K f of the pass this entry point runs
+// (512 threads x 32 accumulators), and its largest K.
+constexpr int64_t kMaxOutputs = 16384;
+constexpr int kMaxK = 256;
+
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
+// Per device: the array's device address and the context it was looked up in.
+// A device reset (or a new primary context) changes the context, and the
+// address is then looked up again instead of being reused.
 double *g_scratch_addr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (set up once per device).
+using CtxGetCurrent = CUresult (*)(CUcontext *);
+CtxGetCurrent ctx_get_current() {
+  static CtxGetCurrent fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrent>(p);
+  }
+  return fn;
+}
+
+// Device address of the scratch array on the current device (looked up once per
+// device and context, with that device current).
 cudaError_t scratch_address(int dev, double **out) {
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_addr[dev]) {
+  CUcontext ctx = nullptr;
+  CtxGetCurrent get = ctx_get_current();
+  if (!get || get(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorInitializationError;
+  if (!g_scratch_addr[dev] || g_scratch_ctx[dev] != ctx) {
     void *p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_scratch_addr[dev] = static_cast<double *>(p);
+    g_scratch_ctx[dev] = ctx;
   }
   *out = g_scratch_addr[dev];
   return cudaSuccess;
@@ -54,6 +81,8 @@ extern "C" MNL_API int mnl_loglik_grad_noalloc(const mnl_dims *dims, const mnl_d
     return MNL_ERR_INVALID_ARG;
   const Shape S = make_shape(*dims);
   const bool fp64 = precision == MNL_FP64;
+  // sizes beyond the limits are refused before any CUDA call
+  if (S.nout > kMaxOutputs || S.K > kMaxK) return MNL_ERR_UNSUPPORTED;
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) { cudaGetLastError(); return MNL_ERR_CUDA; }
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {

@@ -88,11 +88,14 @@ __device__ __forceinline__ bool mbar_done(uint64_t *bar, uint32_t parity) {
 }
 
 // Bounded wait for phase `parity` of a stage barrier.
-__device__ __forceinline__ bool stage_wait(uint64_t *bar, uint32_t parity) {
+// bound_ns = 0: kTileWaitNs.  Waits for copies already issued before a CTA
+// stops (the drain) always use kTileWaitNs.
+__device__ __forceinline__ bool stage_wait(uint64_t *bar, uint32_t parity, uint64_t bound_ns = 0) {
   if (mbar_done(bar, parity)) return true;
+  const uint64_t lim = bound_ns ? bound_ns : kTileWaitNs;
   const uint64_t t0 = gclock();
   while (!mbar_done(bar, parity))
-    if (gclock() - t0 > kTileWaitNs) return false;
+    if (gclock() - t0 > lim) return false;
   return true;
 }
 
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(kPT, kYZSlots == 4 ? 1 : 2) pass_tile_kernel(T
     const int64_t row0 = tl * R;
     const int nrows = (int)(N - row0 < R ? N - row0 : R);
     if (nrows == R) {
-      if (!stage_wait(&bar[s], par)) s_abort = 1;
+      if (!stage_wait(&bar[s], par, io.wait_ns)) s_abort = 1;
       else if (tid == 0) pend[s] = -1;
     } else {  // the partial last tile: plain loads, zero padding
       for (int e = tid; e < R * p; e += kPT) Xs[e] = e < nrows * p ? io.X[row0 * p + e] : 0.f;
@@ -462,7 +465,7 @@ template <int JA, int KB>
 __global__ void __launch_bounds__(256, 1) grad_beta_kernel(int64_t N, int K, int p, int64_t n,
                                                            const float *__restrict__ X, const float *__restrict__ P,
                                                            const int *__restrict__ choice, double *partials,
-                                                           int *err) {
+                                                           int *err, uint64_t wait_ns) {
   extern __shared__ __align__(128) unsigned char sm[];
   const int sx = ((kGbRows * p * 4) + 127) & ~127, sp = ((kGbRows * K * 4) + 127) & ~127;
   const int stage_bytes = sx + sp + 128;
@@ -507,7 +510,7 @@ __global__ void __launch_bounds__(256, 1) grad_beta_kernel(int64_t N, int K, int
     const int64_t r0 = tl * kGbRows;
     const int nrows = (int)(N - r0 < kGbRows ? N - r0 : kGbRows);
     if (nrows == kGbRows) {
-      if (!stage_wait(&bar[st], par)) s_abort = 1;
+      if (!stage_wait(&bar[st], par, wait_ns)) s_abort = 1;
       else if (tid == 0) pend[st] = -1;
     } else {  // the partial last tile: plain loads, zero padding
       for (int e = tid; e < kGbRows * p; e += 256) Xs[e] = e < nrows * p ? X[r0 * p + e] : 0.f;
@@ -581,7 +584,7 @@ cudaError_t launch_gb(const Shape &s, int grid, const PassIO &io, cudaStream_t s
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, 256, smem, st>>>(s.N, s.K, s.p, s.n, io.X, reinterpret_cast<const float *>(io.P), io.choice,
-                                io.partials, io.err);
+                                io.partials, io.err, io.wait_ns);
   return cudaGetLastError();
 }
 

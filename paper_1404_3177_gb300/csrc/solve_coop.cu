@@ -65,7 +65,7 @@ __device__ __forceinline__ uint64_t gtimer() {
 // arrives (its writes are released to the waiting CTAs) and goes on.  Returns
 // false in every thread of the CTA when this CTA or another one gave up; the
 // caller then returns.
-__device__ bool grid_sync(GridBarrier *b, int w, unsigned nblocks, int *err, bool wait = true) {
+__device__ bool grid_sync(GridBarrier *b, int w, unsigned nblocks, int *err, uint64_t bound_ns, bool wait = true) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -83,9 +83,9 @@ __device__ bool grid_sync(GridBarrier *b, int w, unsigned nblocks, int *err, boo
         const uint64_t t0 = gtimer();
         while (*vgen == g) {
           if (*vab) { good = 0; break; }
-          if (gtimer() - t0 > kWaitNs) {
+          if (gtimer() - t0 > bound_ns) {
             atomicExch(&b->abort, 1);
-            atomicOr(err, 2);
+            atomicOr(err, kWaitCoop);
             good = 0;
             break;
           }
@@ -398,6 +398,7 @@ struct CoopArgs {
   int *status;
   int bad_bit;
   int *err;
+  uint64_t wait_ns;  // bound of one grid-barrier wait
 };
 
 // Shared-memory plan of the diagonal step (elements): Dc [64][kDs] the block
@@ -550,7 +551,7 @@ __global__ void __launch_bounds__(kCoopThreads, sizeof(T) == 4 ? 2 : 1) coop_cho
     a.bar->smid[b] = (int)sid;
   }
   if (b == 0) factor_diag<T>(a, 0, false);
-  if (!grid_sync(a.bar, 1, G, a.err)) return;
+  if (!grid_sync(a.bar, 1, G, a.err, a.wait_ns)) return;
   if (threadIdx.x == 0) {
     const volatile int *ids = a.bar->smid;
     const int s0 = ids[0];
@@ -609,7 +610,7 @@ __global__ void __launch_bounds__(kCoopThreads, sizeof(T) == 4 ? 2 : 1) coop_cho
       bsplit(1 + s_widx, s_nw);
     }
     if (k == np - 1) break;
-    if (!grid_sync(a.bar, 0, G, a.err, !arrive_only)) return;
+    if (!grid_sync(a.bar, 0, G, a.err, a.wait_ns, !arrive_only)) return;
     // ---- C: trailing update (and the inverse's rows below) ----
     const int U = m * (m + 1) / 2;
     const int nC = U + (INV ? m * (k + 1) : 0);
@@ -646,7 +647,7 @@ __global__ void __launch_bounds__(kCoopThreads, sizeof(T) == 4 ? 2 : 1) coop_cho
     } else if (worker) {
       csplit(1 + s_widx, s_nw);
     }
-    if (!grid_sync(a.bar, 1, G, a.err)) return;
+    if (!grid_sync(a.bar, 1, G, a.err, a.wait_ns)) return;
   }
 }
 
@@ -1076,7 +1077,7 @@ int64_t panels(int64_t n) { return (n + kCb - 1) / kCb; }
 
 template <typename T, bool INV>
 cudaError_t launch_coop(int64_t n, T *A, T *Li, T *Dinv, T *dinv, GridBarrier *bar, int *status, int bad_bit,
-                        int *err, cudaStream_t st) {
+                        int *err, cudaStream_t st, uint64_t wait_ns) {
   auto kern = coop_cholesky_kernel<T, INV>;
   const size_t smem = (size_t)std::max(kDiagSmem, 4 * kCb * kCs) * sizeof(T);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1091,6 +1092,7 @@ cudaError_t launch_coop(int64_t n, T *A, T *Li, T *Dinv, T *dinv, GridBarrier *b
   CoopArgs<T> a;
   a.A = A; a.Li = Li; a.Dinv = Dinv; a.dinv = dinv; a.n = n; a.bar = bar;
   a.status = status; a.bad_bit = bad_bit; a.err = err;
+  a.wait_ns = wait_ns ? wait_ns : kWaitNs;
   void *args[] = {&a};
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(kern), dim3(grid), dim3(kCoopThreads), args, smem,
                                      st);
@@ -1123,11 +1125,12 @@ size_t chol_work_bytes(int64_t n) {
 
 int cholesky_launches(int64_t) { return 1; }
 
-cudaError_t launch_cholesky(int64_t n, double *F, double *dinv, void *work, int *status, int *err, cudaStream_t st) {
+cudaError_t launch_cholesky(int64_t n, double *F, double *dinv, void *work, int *status, int *err, cudaStream_t st,
+                            uint64_t wait_ns) {
   unsigned char *w = static_cast<unsigned char *>(work);
   double *Dinv = reinterpret_cast<double *>(w);
   GridBarrier *bar = reinterpret_cast<GridBarrier *>(w + round256((size_t)panels(n) * kCb * kCb * 8));
-  return launch_coop<double, false>(n, F, nullptr, Dinv, dinv, bar, status, 4, err, st);
+  return launch_coop<double, false>(n, F, nullptr, Dinv, dinv, bar, status, 4, err, st, wait_ns);
 }
 
 size_t mixed_solve_bytes(int64_t n) { return mixed_layout(n).total; }
@@ -1137,7 +1140,8 @@ double *mixed_solve_ref(void *work, int64_t n) {
 }
 
 cudaError_t launch_mixed_solve(int64_t n, const double *F, float *F32, const double *g, double *delta, void *work,
-                               int *status, int *err, int iters, cudaStream_t st, int *launches, bool f32_ready) {
+                               int *status, int *err, int iters, cudaStream_t st, int *launches, bool f32_ready,
+                               uint64_t wait_ns) {
   const MixedLayout L = mixed_layout(n);
   unsigned char *w = static_cast<unsigned char *>(work);
   float *Li = reinterpret_cast<float *>(w + L.li), *Dblk = reinterpret_cast<float *>(w + L.dblk);
@@ -1149,7 +1153,8 @@ cudaError_t launch_mixed_solve(int64_t n, const double *F, float *F32, const dou
   dim3 grid((unsigned)((n + 255) / 256), (unsigned)std::min<int64_t>(n, 65535), (unsigned)((n + 65534) / 65535));
   if (!f32_ready) f64_to_f32_lower_kernel<<<grid, 256, 0, st>>>(n, F, F32);
   if ((e = cudaMemsetAsync(Li, 0, (size_t)n * n * 4, st)) != cudaSuccess) return e;
-  if ((e = launch_coop<float, true>(n, F32, Li, Dblk, dinv, bar, status, 8, err, st)) != cudaSuccess) return e;
+  if ((e = launch_coop<float, true>(n, F32, Li, Dblk, dinv, bar, status, 8, err, st, wait_ns)) != cudaSuccess)
+    return e;
   const int cnt = (f32_ready ? 1 : 2) + refine_with_inverse(n, F, Li, g, delta, y, z, r, ref, status, iters, st);
   if (launches) *launches = cnt;
   return cudaGetLastError();

@@ -183,7 +183,7 @@ template <bool TF32, int BN>
 __global__ void __launch_bounds__(192, 1) syrk_tc_kernel(const CUtensorMap *__restrict__ maps,
                                                          const SyrkUnit *__restrict__ units, int nunits,
                                                          const int *__restrict__ active, float *__restrict__ out,
-                                                         int *__restrict__ err) {
+                                                         int *__restrict__ err, uint64_t wait_ns) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   constexpr int kStages = TcCfg<BN>::kStages, kStageBytes = TcCfg<BN>::kStageBytes;
@@ -235,7 +235,10 @@ __global__ void __launch_bounds__(192, 1) syrk_tc_kernel(const CUtensorMap *__re
         const CUtensorMap *map = maps + w.map;
         const bool diag = BN == kTile && w.ti == w.tj;  // a 128-wide diagonal tile loads its operand once
         for (int kb = w.kb0; kb < w.kb1; ++kb) {
-          if (!wait_bounded(&empty[stage], phase ^ 1u, abort_flag, err, kErrProducer)) { ok = false; break; }
+          if (!wait_bounded(&empty[stage], phase ^ 1u, abort_flag, err, kErrProducer, true, wait_ns)) {
+            ok = false;
+            break;
+          }
           uint8_t *dst = smem + stage * kStageBytes;
           mbar_arrive_expect_tx(&full[stage], diag ? kOpBytes : (1 + BN / kTile) * kOpBytes);
           tma_load_3d(map, &full[stage], dst, w.ti * kTile, kb);
@@ -266,12 +269,12 @@ __global__ void __launch_bounds__(192, 1) syrk_tc_kernel(const CUtensorMap *__re
         const bool diag = BN == kTile && w.ti == w.tj;
         const int b = local & 1;
         ++local;
-        if (!wait_bounded(&tempty[b], acc_ph[b] ^ 1u, abort_flag, err, kErrMma)) break;
+        if (!wait_bounded(&tempty[b], acc_ph[b] ^ 1u, abort_flag, err, kErrMma, true, wait_ns)) break;
         acc_ph[b] ^= 1u;
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(b * BN);
         for (int kb = kb0; kb < kb1; ++kb) {
-          if (!wait_bounded(&full[stage], phase, abort_flag, err, kErrMma)) { ok = false; break; }
+          if (!wait_bounded(&full[stage], phase, abort_flag, err, kErrMma, true, wait_ns)) { ok = false; break; }
           tc_fence_after();
           const uint32_t a_addr = saddr(smem + stage * kStageBytes);
           const uint32_t b_addr = diag ? a_addr : a_addr + kOpBytes;
@@ -300,7 +303,7 @@ __global__ void __launch_bounds__(192, 1) syrk_tc_kernel(const CUtensorMap *__re
       const int b = local & 1;
       ++local;
       int ok = 0;
-      if (lane == 0) ok = wait_bounded(&tfull[b], acc_ph[b], abort_flag, err, kErrEpilogue) ? 1 : 0;
+      if (lane == 0) ok = wait_bounded(&tfull[b], acc_ph[b], abort_flag, err, kErrEpilogue, true, wait_ns) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
       acc_ph[b] ^= 1u;
@@ -412,7 +415,7 @@ __global__ void __launch_bounds__(192, 1) chol_update_tc_kernel(const CUtensorMa
         const bool same = w.bmap == 0 && w.ti == w.tj;  // B = A: one pair of boxes
         const CUtensorMap *ma = maps, *mb = maps + 2 * w.bmap;
         for (int kb = 0; kb < kKb; ++kb) {
-          if (!wait_bounded(&empty[stage], phase ^ 1u, abort_flag, err, kErrProducer, true, wait_ns)) {
+          if (!wait_bounded(&empty[stage], phase ^ 1u, abort_flag, err, kWaitPanel, true, wait_ns)) {
             ok = false;
             break;
           }
@@ -429,7 +432,7 @@ __global__ void __launch_bounds__(192, 1) chol_update_tc_kernel(const CUtensorMa
         }
       }
       for (int s = 0; s < kCuStages; ++s)
-        if (last_par[s] >= 0) wait_bounded(&full[s], (uint32_t)last_par[s], abort_flag, err, kErrDrain, false);
+        if (last_par[s] >= 0) wait_bounded(&full[s], (uint32_t)last_par[s], abort_flag, err, kWaitPanel, false);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -443,12 +446,12 @@ __global__ void __launch_bounds__(192, 1) chol_update_tc_kernel(const CUtensorMa
         const bool same = w.bmap == 0 && w.ti == w.tj;
         const int b = local & 1;
         ++local;
-        if (!wait_bounded(&tempty[b], acc_ph[b] ^ 1u, abort_flag, err, kErrMma, true, wait_ns)) break;
+        if (!wait_bounded(&tempty[b], acc_ph[b] ^ 1u, abort_flag, err, kWaitPanel, true, wait_ns)) break;
         acc_ph[b] ^= 1u;
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(b * kTile);
         for (int kb = 0; kb < kKb; ++kb) {
-          if (!wait_bounded(&full[stage], phase, abort_flag, err, kErrMma, true, wait_ns)) { ok = false; break; }
+          if (!wait_bounded(&full[stage], phase, abort_flag, err, kWaitPanel, true, wait_ns)) { ok = false; break; }
           tc_fence_after();
           const uint32_t a0 = saddr(smem + stage * kCuStageBytes);
           const uint64_t ah = sw128_desc(a0), al = sw128_desc(a0 + kOpBytes);
@@ -468,7 +471,7 @@ __global__ void __launch_bounds__(192, 1) chol_update_tc_kernel(const CUtensorMa
         tc_commit(&tfull[b]);
       }
       tc_commit(drain);
-      wait_bounded(drain, 0u, abort_flag, err, kErrDrain, false);
+      wait_bounded(drain, 0u, abort_flag, err, kWaitPanel, false);
     }
   } else {
     const int quarter = warp & 3;
@@ -479,7 +482,7 @@ __global__ void __launch_bounds__(192, 1) chol_update_tc_kernel(const CUtensorMa
       const int b = local & 1;
       ++local;
       int ok = 0;
-      if (lane == 0) ok = wait_bounded(&tfull[b], acc_ph[b], abort_flag, err, kErrEpilogue, true, wait_ns) ? 1 : 0;
+      if (lane == 0) ok = wait_bounded(&tfull[b], acc_ph[b], abort_flag, err, kWaitPanel, true, wait_ns) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
       acc_ph[b] ^= 1u;
@@ -653,22 +656,23 @@ size_t tc_smem_bytes() { return TcCfg<kTile>::kSmemBytes; }
 
 template <bool TF32, int BN>
 cudaError_t launch_tc(const CUtensorMap *maps, const SyrkUnit *units, int nunits, const int *active, int grid,
-                      float *out, int *err, cudaStream_t st) {
+                      float *out, int *err, cudaStream_t st, uint64_t wait_ns) {
   auto kern = syrk_tc_kernel<TF32, BN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN>::kSmemBytes);
   if (e != cudaSuccess) return e;
-  kern<<<grid, 192, TcCfg<BN>::kSmemBytes, st>>>(maps, units, nunits, active, out, err);
+  kern<<<grid, 192, TcCfg<BN>::kSmemBytes, st>>>(maps, units, nunits, active, out, err,
+                                                 wait_ns ? wait_ns : kTimeoutNs);
   return cudaGetLastError();
 }
 
 cudaError_t launch_syrk_tc(OpType t, const CUtensorMap *maps, const SyrkUnit *units, int nunits, const int *active,
-                           int grid, float *out, int *err, cudaStream_t st, int bn) {
+                           int grid, float *out, int *err, cudaStream_t st, int bn, uint64_t wait_ns) {
   if (nunits <= 0) return cudaSuccess;
   if (bn == 256)
-    return t == OpType::TF32 ? launch_tc<true, 256>(maps, units, nunits, active, grid, out, err, st)
-                             : launch_tc<false, 256>(maps, units, nunits, active, grid, out, err, st);
-  return t == OpType::TF32 ? launch_tc<true, 128>(maps, units, nunits, active, grid, out, err, st)
-                           : launch_tc<false, 128>(maps, units, nunits, active, grid, out, err, st);
+    return t == OpType::TF32 ? launch_tc<true, 256>(maps, units, nunits, active, grid, out, err, st, wait_ns)
+                             : launch_tc<false, 256>(maps, units, nunits, active, grid, out, err, st, wait_ns);
+  return t == OpType::TF32 ? launch_tc<true, 128>(maps, units, nunits, active, grid, out, err, st, wait_ns)
+                           : launch_tc<false, 128>(maps, units, nunits, active, grid, out, err, st, wait_ns);
 }
 
 size_t chol_update_smem_bytes() { return kCuSmemBytes; }

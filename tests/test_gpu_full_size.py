@@ -110,7 +110,7 @@ def c4():
     return probs, refs
 
 
-@pytest.mark.parametrize("prec", ["bf16"])
+@pytest.mark.parametrize("prec", ["bf16", "fp64"])
 def test_workload4_full_batch(lib, c4, prec):
     probs, refs = c4
     with lib.MNLBatch([dev(p) for p in probs], precision=prec) as b:

@@ -128,3 +128,32 @@ def test_large_request_in_the_mix(Server, reqs_and_ref, prec):
         ref = ref_big if pr is big else refs[reqs.index(pr)]
         assert info["status"] == 0, info
         assert np.abs(theta - ref).max() / np.abs(ref).max() <= THETA_TOL
+
+
+def test_workload5_large_request_in_a_mix_of_small_ones(Server, reqs_and_ref):
+    """A large serving request at its full size (N=100000, K=60, p=60, f=4: n_theta = 3544) admitted with small
+    ones.  The small results are compared with oracle fits; for the large one an oracle fit takes too long, so
+    its estimate theta is checked through the oracle's gradient there: one Newton correction
+    d = (-H(theta))^-1 g_oracle(theta), with the GPU's Hessian at theta (pinned to 2e-3 elsewhere), estimates
+    theta_hat - theta to within that relative error, so max|d| / max|theta| <= 1e-6 is the coefficient bar."""
+    from paper_1404_3177_gb300.api import MNL
+    reqs, refs = reqs_and_ref
+    big = datagen.config5_large(0)
+    assert big.n_theta == 3544
+    with Server(precision="bf16", mem_budget=80 << 30) as srv:
+        tickets = {submit(srv, r): r for r in reqs[:6] + [big]}
+        res = run_until_done(srv, tickets)
+    theta_big = None
+    for _, (pr, (theta, info)) in res.items():
+        assert info["status"] == 0, info
+        if pr is big:
+            theta_big = theta
+            continue
+        ref = refs[reqs.index(pr)]
+        assert np.abs(theta - ref).max() / np.abs(ref).max() <= THETA_TOL
+    _, g = oracle.loglik_grad(big, theta_big)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda() if a.size else None  # noqa: E731
+    with MNL(X=d(big.X), Z=d(big.Z), choice=torch.from_numpy(big.choice).cuda(), K=big.K, precision="bf16") as m:
+        H = m.hessian(torch.from_numpy(theta_big).cuda()).cpu().numpy()
+    corr = np.linalg.solve(-H, g)
+    assert np.abs(corr).max() / np.abs(theta_big).max() <= THETA_TOL
