@@ -17,8 +17,15 @@
  *     [ beta_1 .. beta_{K-1} (p each) | gamma_{1 or 0} .. gamma_{K-1} (d each) | alpha (f) ]
  * gamma_base = 0 (default): gamma_0 is fixed at 0 and the k = 0 rows of Y are
  *   ignored; n_theta = (K-1)(p+d) + f.
- * gamma_base = 1: gamma_0 is estimated as in the paper; n_theta = (K-1)p + Kd + f.
- *   (Accepted by mnl_num_params; mnl_create returns MNL_ERR_UNSUPPORTED.)
+ * gamma_base = 1: gamma_0 is estimated as in the paper (Sec. 2.3 "1 x K";
+ *   eq. "theta vec"); n_theta = (K-1)p + Kd + f, needs d >= 1.  Supported by
+ *   the single-problem handle (mnl_create and every call on it); the batched,
+ *   serving and allocation-free calls return MNL_ERR_UNSUPPORTED for it.
+ *   The library solves it as the equivalent gamma_base = 0 problem with d more
+ *   generic columns (z'_ikj = y_i0j for k = 0, else 0: only differences
+ *   against alternative 0 enter, and z'_ik - z'_i0 = -y_i0 for k >= 1 is the
+ *   paper's -Y_i0 gamma_0 term); theta, the gradient, the Hessian and the
+ *   standard errors are returned in the order above.
  *
  * Data layout (all row-major, float32, read-only, owned by the caller):
  *     X      [N][p]       individual-specific columns
@@ -228,6 +235,26 @@ MNL_API int mnl_newton_step(mnl_handle *h, double *theta, mnl_step_info *info);
  * (theta holds the last iterate), or an error of mnl_newton_step. */
 MNL_API int mnl_fit(mnl_handle *h, const mnl_fit_opts *opts, double *theta, mnl_fit_info *info);
 
+/* Asymptotic standard errors at theta (normally the estimate): se_j =
+ * sqrt((F^{-1})_jj), F = -H the observed information (the coefficient table
+ * of the package's summary method, Sec. 2.3).  F is formed as by
+ * mnl_hessian (in the handle's precision), factored in float64 together with
+ * the inverse of its factor, F^{-1} = L^{-T} L^{-1}, and se_j is the norm of
+ * column j of L^{-1}.  The first call allocates an n_theta^2 float64 buffer,
+ * kept until mnl_destroy.
+ *   theta  DEVICE [n_theta] float64;  se  DEVICE [n_theta] float64.
+ * Synchronises the stream.  MNL_ERR_NOT_PD when F is not positive definite. */
+MNL_API int mnl_std_errors(mnl_handle *h, const double *theta, double *se);
+
+/* Choice probabilities at theta (the package's predict method, Sec. 2.3;
+ * eqs. "probability", "base probability"), for the handle's data - a handle
+ * on new data predicts for those.
+ *   P       DEVICE [N][K] float64, row-major.
+ *   loglik  HOST, or NULL: l(theta) of the handle's choices (synchronises).
+ * Computed by the same pass as mnl_loglik_grad (float32 in the TF32 / BF16
+ * modes, float64 in MNL_FP64). */
+MNL_API int mnl_predict(mnl_handle *h, const double *theta, double *P, double *loglik);
+
 /* How mnl_newton_step / mnl_fit solve (-H) delta = g.
  *   MNL_SOLVE_FP64:  blocked float64 Cholesky and float64 triangular solves.
  *   MNL_SOLVE_MIXED: float32 Cholesky of -H and float64 iterative refinement
@@ -240,6 +267,16 @@ MNL_API int mnl_fit(mnl_handle *h, const mnl_fit_opts *opts, double *theta, mnl_
  *   MNL_SOLVE_AUTO (default): FP64 for MNL_FP64 handles, MIXED otherwise. */
 enum { MNL_SOLVE_AUTO = 0, MNL_SOLVE_FP64 = 1, MNL_SOLVE_MIXED = 2 };
 MNL_API int mnl_set_solve(mnl_handle *h, int mode);
+
+/* Observation weights (the `weights` argument of the package's mnlogit call,
+ * Sec. 2.3), read as case weights: observation i counts w_i times in l, g and
+ * H (l = sum_i w_i l_i; integer weights equal repeated rows).
+ *   w  DEVICE [N] float32, 16-byte aligned, finite and >= 0, owned by the
+ *      caller and unchanged until the handle is destroyed or the weights are
+ *      replaced; NULL removes them (all ones).
+ * Validates on the device (synchronises): MNL_ERR_NONFINITE for NaN/Inf,
+ * MNL_ERR_INVALID_ARG for a negative weight or a misaligned pointer. */
+MNL_API int mnl_set_weights(mnl_handle *h, const float *w);
 
 /* Bound, in nanoseconds, of every bounded device-side wait of this handle's
  * kernels (pipeline stages, tile copies, grid barriers); 0 restores their

@@ -33,7 +33,7 @@ MNL_STOP_GTOL, MNL_STOP_FTOL, MNL_STOP_STEPTOL, MNL_STOP_MAXITER, MNL_STOP_NOISE
 EXPORTS = (
     "mnl_num_params", "mnl_status_string", "mnl_workspace_bytes", "mnl_fit_opts_default", "mnl_create",
     "mnl_upload", "mnl_loglik_grad", "mnl_hessian", "mnl_newton_step", "mnl_fit", "mnl_destroy",
-    "mnl_loglik_grad_noalloc", "mnl_set_solve", "mnl_set_wait_bound", "mnl_batch_create", "mnl_batch_num_params", "mnl_batch_fit",
+    "mnl_loglik_grad_noalloc", "mnl_set_solve", "mnl_set_wait_bound", "mnl_set_weights", "mnl_std_errors", "mnl_predict", "mnl_batch_create", "mnl_batch_num_params", "mnl_batch_fit",
     "mnl_batch_destroy", "mnl_server_opts_default", "mnl_server_create", "mnl_server_submit", "mnl_server_step",
     "mnl_server_poll", "mnl_server_finished", "mnl_server_memory_in_use", "mnl_server_destroy",
 )
@@ -143,6 +143,12 @@ def load() -> C.CDLL:
         lib.mnl_newton_step.argtypes = [vp, vp, C.POINTER(mnl_step_info)]
         lib.mnl_fit.restype = i32
         lib.mnl_fit.argtypes = [vp, C.POINTER(mnl_fit_opts), vp, C.POINTER(mnl_fit_info)]
+        lib.mnl_std_errors.restype = i32
+        lib.mnl_std_errors.argtypes = [vp, vp, vp]
+        lib.mnl_predict.restype = i32
+        lib.mnl_predict.argtypes = [vp, vp, vp, C.POINTER(C.c_double)]
+        lib.mnl_set_weights.restype = i32
+        lib.mnl_set_weights.argtypes = [vp, vp]
         lib.mnl_set_wait_bound.restype = i32
         lib.mnl_set_wait_bound.argtypes = [vp, C.c_uint64]
         lib.mnl_destroy.restype = i32
@@ -257,6 +263,21 @@ def mnl_fit(handle: int, opts: mnl_fit_opts | None, theta_ptr: int) -> mnl_fit_i
 
 def mnl_set_solve(handle: int, mode: int) -> None:
     _check(load().mnl_set_solve(C.c_void_p(handle), mode), "mnl_set_solve")
+
+
+def mnl_std_errors(handle: int, theta_ptr: int, se_ptr: int) -> None:
+    _check(load().mnl_std_errors(C.c_void_p(handle), C.c_void_p(theta_ptr), C.c_void_p(se_ptr)), "mnl_std_errors")
+
+
+def mnl_predict(handle: int, theta_ptr: int, P_ptr: int, want_loglik: bool = True) -> float | None:
+    l = C.c_double()
+    _check(load().mnl_predict(C.c_void_p(handle), C.c_void_p(theta_ptr), C.c_void_p(P_ptr),
+                              C.byref(l) if want_loglik else None), "mnl_predict")
+    return l.value if want_loglik else None
+
+
+def mnl_set_weights(handle: int, w_ptr: int | None) -> None:
+    _check(load().mnl_set_weights(C.c_void_p(handle), C.c_void_p(w_ptr) if w_ptr else None), "mnl_set_weights")
 
 
 def mnl_set_wait_bound(handle: int, ns: int) -> None:

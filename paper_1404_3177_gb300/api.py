@@ -20,7 +20,7 @@ class MNL:
     """
 
     def __init__(self, X=None, Y=None, Z=None, choice=None, *, K=None, precision="bf16", stream=None,
-                 host_owned_dims=None, solve="auto"):
+                 host_owned_dims=None, solve="auto", gamma_base=0, weights=None):
         self.precision = nat.PRECISIONS[precision]
         self._stream = (stream or torch.cuda.current_stream()).cuda_stream
         if host_owned_dims is not None:
@@ -46,10 +46,19 @@ class MNL:
             if t is not None and (not t.is_cuda or t.dtype != dt or not t.is_contiguous()):
                 raise ValueError(f"{name} must be a contiguous CUDA tensor of dtype {dt}")
         self._keep = (X, Y, Z, choice)
-        self.dims = nat.mnl_dims(N, K, p, d, f, 0)
+        self.dims = nat.mnl_dims(N, K, p, d, f, gamma_base)
         data = nat.mnl_data(_ptr(X), _ptr(Y), _ptr(Z), _ptr(choice))
         self.h = nat.mnl_create(self.dims, data, self.precision, self._stream)
         nat.mnl_set_solve(self.h, nat.SOLVES[solve])
+        if weights is not None:
+            self.set_weights(weights)
+
+    def set_weights(self, w):
+        """Observation (case) weights: a contiguous float32 CUDA tensor [N], or None."""
+        if w is not None and (not w.is_cuda or w.dtype != torch.float32 or not w.is_contiguous()):
+            raise ValueError("weights must be a contiguous float32 CUDA tensor")
+        self._w = w
+        nat.mnl_set_weights(self.h, _ptr(w))
 
     @classmethod
     def with_host_upload(cls, N, K, p, d, f, *, precision="bf16", stream=None, solve="auto"):
@@ -85,6 +94,20 @@ class MNL:
         H = torch.empty(self.n_theta, self.n_theta, dtype=torch.float64, device=th.device)
         nat.mnl_hessian(self.h, th.data_ptr(), H.data_ptr())
         return H
+
+    def std_errors(self, theta):
+        """Standard errors sqrt(diag((-H)^-1)) at theta, float64 [n_theta] (CUDA)."""
+        th = self._theta(theta)
+        se = torch.empty(self.n_theta, dtype=torch.float64, device=th.device)
+        nat.mnl_std_errors(self.h, th.data_ptr(), se.data_ptr())
+        return se
+
+    def predict(self, theta):
+        """(choice probabilities float64 [N][K] (CUDA), l(theta))."""
+        th = self._theta(theta)
+        P = torch.empty(self.dims.N, self.dims.K, dtype=torch.float64, device=th.device)
+        l = nat.mnl_predict(self.h, th.data_ptr(), P.data_ptr())
+        return P, l
 
     def newton_step(self, theta):
         """One Newton-Raphson iteration; theta (float64 CUDA) is updated in place."""

@@ -14,16 +14,23 @@
 using namespace mnl;
 
 struct mnl_handle {
-  mnl_dims dims;
-  Shape S;
+  mnl_dims dims;  // as given (gamma_base 0 or 1)
+  Shape S;        // of the problem the kernels solve (gamma_base = 1: f + d generic columns)
   int prec;
   OpType op;
   bool fp64;
   cudaStream_t st;
   int dev, nsm;
   // data
-  const float *X, *Y, *Z;
+  const float *X, *Y, *Z;  // Z: the kernels' generic columns (Zaug when gamma_base = 1)
   const int32_t *choice;
+  const float *Zu;         // the caller's Z
+  const float *w;          // observation weights (device [N]) or nullptr
+  // gamma_base = 1: augmented Z, theta permutation and internal-order vectors
+  bool gb1;
+  float *Zaug;
+  int64_t *perm;
+  double *th_int, *vec_int;
   bool owns_data, data_ready;
   void *owned[4];
   // pass
@@ -61,6 +68,7 @@ struct mnl_handle {
   float *F32;
   void *mwork, *cwork;  // mixed-solve and float64-factor workspaces
   void *tcwork;         // tensor-core factorisation (n_theta >= the threshold)
+  double *Binv;         // inverse of the float64 factor (standard errors; allocated at the first call)
   TcCholPlan tcp;
   uint64_t wait_ns;     // bound of the kernels' device waits (0: their defaults)
   // host mirrors (pinned)
@@ -244,7 +252,9 @@ void free_all(mnl_handle *h) {
 
 int validate(mnl_handle *h) {
   CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
-  CK(launch_validate(h->S, h->X, h->Y, h->Z, h->choice, h->status, h->st));
+  const Shape U = shape_of(h->dims.N, h->dims.K, h->dims.p, h->dims.d, h->dims.f);  // the caller's arrays
+  CK(launch_validate(U, h->X, h->Y, h->Zu, h->choice, h->status, h->st));
+  if (h->gb1) CK(launch_augment_z(U.N, U.K, U.d, U.f, h->Y, h->Zu, h->Zaug, h->st));
   CK(cudaMemcpyAsync(h->h_flags, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
   if (h->h_flags[0] & 1) return MNL_ERR_INVALID_ARG;
@@ -263,6 +273,7 @@ int run_pass(mnl_handle *h, const double *theta, bool full, const double *delta,
   io.partials = full ? h->part_full : h->part_ll;
   io.err = h->err;
   io.wait_ns = h->wait_ns;
+  io.w = h->w;
   CK(launch_pass(h->S, pl, h->fp64, full, io, h->st));
   CK(launch_pass_reduce(h->S, pl.grid, full, io.partials, h->scal + base, full ? h->grad : nullptr, h->st));
   h->launches += 2;
@@ -284,7 +295,7 @@ int run_hessian(mnl_handle *h, cudaEvent_t *ev = nullptr) {
   // class operands (and the Z-block operand's rows, from the same staged blocks)
   if (S.mc > 0 || h->tcz) {
     CK(launch_build_operands(S, h->op, h->X, h->Y, h->P, h->At, h->Ad, h->ldn, h->st, h->tcz ? h->Z : nullptr,
-                             h->zbar, h->tcz ? h->Az : nullptr));
+                             h->zbar, h->tcz ? h->Az : nullptr, h->w));
     h->launches += 1;
   }
   if ((rc = mark(h, ev ? ev + 0 : nullptr))) return rc;
@@ -312,7 +323,7 @@ int run_hessian(mnl_handle *h, cudaEvent_t *ev = nullptr) {
                       h->wait_ns));
     h->launches += 1;
   } else if (S.f > 0) {
-    CK(launch_zblocks(S, h->fp64, h->X, h->Y, h->Z, h->P, h->zbar, h->z_split, h->z_part, h->st));
+    CK(launch_zblocks(S, h->fp64, h->X, h->Y, h->Z, h->P, h->zbar, h->z_split, h->z_part, h->st, h->w));
     h->launches += 1;
   }
   if ((rc = mark(h, ev ? ev + 3 : nullptr))) return rc;
@@ -530,6 +541,16 @@ int step_impl(mnl_handle *h, double *theta, mnl_step_info *info, double gtol, bo
   return MNL_OK;
 }
 
+// theta in the caller's order -> the order of the kernels (gamma_base = 1:
+// gamma_0 after alpha), in h->th_int; the caller's pointer otherwise.
+const double *theta_in(mnl_handle *h, const double *theta, int *rc) {
+  *rc = MNL_OK;
+  if (!h->gb1) return theta;
+  const cudaError_t e = launch_perm_to_internal(h->S.n, h->perm, theta, h->th_int, h->st);
+  if (e != cudaSuccess) *rc = cuda_fail(e);
+  return h->th_int;
+}
+
 int check_handle(const mnl_handle *h) {
   if (!h) return MNL_ERR_INVALID_ARG;
   if (!h->data_ready) return MNL_ERR_INVALID_ARG;
@@ -587,7 +608,10 @@ size_t mnl_workspace_bytes(const mnl_dims *d, int precision) {
   PassPlan pf, pl;
   int64_t ldn, mcp;
   int zts = 1;
-  Sizes z = plan_sizes(*d, precision, false, nsm, &ms, &bs, &zs, &pf, &pl, &ldn, &mcp, &nt1d, &nband, &zts);
+  mnl_dims di = *d;  // gamma_base = 1: the equivalent problem with d more generic columns
+  if (d->gamma_base == 1) { di.gamma_base = 0; di.f = d->f + d->d; }
+  Sizes z = plan_sizes(di, precision, false, nsm, &ms, &bs, &zs, &pf, &pl, &ldn, &mcp, &nt1d, &nband, &zts);
+  if (d->gamma_base == 1) z.owned += (size_t)d->N * d->K * di.f * 4 + 3 * (size_t)mnl_num_params(d) * 8;
   return z.total();
 }
 
@@ -595,7 +619,10 @@ int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *
   if (!out) return MNL_ERR_INVALID_ARG;
   *out = nullptr;
   if (!dims_ok(dims) || precision < 0 || precision > 2) return MNL_ERR_INVALID_ARG;
-  if (dims->gamma_base != 0) return MNL_ERR_UNSUPPORTED;
+  if (dims->gamma_base == 1 && dims->d == 0) return MNL_ERR_INVALID_ARG;  // no gamma_0 to estimate
+  // gamma_base = 1 is solved as gamma_base = 0 with the d columns of Y's base rows as generic columns
+  mnl_dims di = *dims;
+  if (dims->gamma_base == 1) { di.gamma_base = 0; di.f = dims->f + dims->d; }
   if (data) {
     if (!data->choice || (dims->p > 0 && !data->X) || (dims->d > 0 && !data->Y) || (dims->f > 0 && !data->Z))
       return MNL_ERR_INVALID_ARG;
@@ -603,7 +630,8 @@ int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *
   mnl_handle *h = new (std::nothrow) mnl_handle();
   if (!h) return MNL_ERR_OOM;
   h->dims = *dims;
-  h->S = make_shape(*dims);
+  h->S = make_shape(di);
+  h->gb1 = dims->gamma_base == 1;
   h->prec = precision;
   h->op = precision == MNL_FP64 ? OpType::F64 : precision == MNL_TF32 ? OpType::TF32 : OpType::BF16;
   // Too few observations for unbiased BF16 rounding to average out: TF32 operands.
@@ -619,7 +647,7 @@ int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *
   if (cudaGetDevice(&h->dev) != cudaSuccess) { cudaGetLastError(); return fail(MNL_ERR_CUDA); }
   cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev);
   int nband = 0;
-  Sizes z = plan_sizes(*dims, precision, data == nullptr, h->nsm, &h->main_split, &h->band_split, &h->z_split,
+  Sizes z = plan_sizes(di, precision, data == nullptr, h->nsm, &h->main_split, &h->band_split, &h->z_split,
                        &h->pfull, &h->pll, &h->ldn, &h->mc_pad, &h->nt1d, &nband, &h->zt_split);
   if (!h->pfull.ok || !h->pll.ok) return fail(MNL_ERR_UNSUPPORTED);
 
@@ -776,9 +804,23 @@ int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *
       return fail(MNL_ERR_CUDA);
     }
   }
-  // data
+  if (h->gb1) {  // augmented Z, theta permutation (user order <-> kernels' order), internal-order vectors
+    const int64_t nb = (int64_t)(S.K - 1) * S.p, dd = dims->d, nn = S.n;
+    std::vector<int64_t> perm((size_t)nn);
+    for (int64_t u = 0; u < nn; ++u)
+      perm[(size_t)u] = u < nb ? u : u < nb + dd ? nn - dd + (u - nb) : u - dd;
+    if ((rc = dalloc(h, &h->Zaug, (size_t)S.N * S.K * S.f * 4)) || (rc = dalloc(h, &h->perm, (size_t)nn * 8)) ||
+        (rc = dalloc(h, &h->th_int, (size_t)nn * 8)) || (rc = dalloc(h, &h->vec_int, (size_t)nn * 8)))
+      return fail(rc);
+    if (cudaMemcpy(h->perm, perm.data(), (size_t)nn * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MNL_ERR_CUDA);
+    }
+  }
+  // data (the caller's shapes: Z has dims->f columns)
   if (data) {
-    h->X = data->X; h->Y = data->Y; h->Z = data->Z; h->choice = data->choice;
+    h->X = data->X; h->Y = data->Y; h->Zu = data->Z; h->choice = data->choice;
+    h->Z = h->gb1 ? h->Zaug : h->Zu;
     h->owns_data = false;
     if ((rc = validate(h))) return fail(rc);
   } else {
@@ -786,9 +828,10 @@ int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *
     float *X = nullptr, *Y = nullptr, *Z = nullptr;
     int32_t *c = nullptr;
     if ((rc = dalloc(h, &X, (size_t)S.N * S.p * 4)) || (rc = dalloc(h, &Y, (size_t)S.N * S.K * S.d * 4)) ||
-        (rc = dalloc(h, &Z, (size_t)S.N * S.K * S.f * 4)) || (rc = dalloc(h, &c, (size_t)S.N * 4)))
+        (rc = dalloc(h, &Z, (size_t)S.N * S.K * dims->f * 4)) || (rc = dalloc(h, &c, (size_t)S.N * 4)))
       return fail(rc);
-    h->X = X; h->Y = Y; h->Z = Z; h->choice = c;
+    h->X = X; h->Y = Y; h->Zu = Z; h->choice = c;
+    h->Z = h->gb1 ? h->Zaug : h->Zu;
     h->data_ready = false;
   }
   if (cudaStreamSynchronize(h->st) != cudaSuccess) { cudaGetLastError(); return fail(MNL_ERR_CUDA); }
@@ -799,7 +842,8 @@ int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *
 int mnl_upload(mnl_handle *h, const mnl_data *hd) {
   if (!h || !hd || !h->owns_data) return MNL_ERR_INVALID_ARG;
   const Shape &S = h->S;
-  if (!hd->choice || (S.p > 0 && !hd->X) || (S.d > 0 && !hd->Y) || (S.f > 0 && !hd->Z)) return MNL_ERR_INVALID_ARG;
+  if (!hd->choice || (S.p > 0 && !hd->X) || (S.d > 0 && !hd->Y) || (h->dims.f > 0 && !hd->Z))
+    return MNL_ERR_INVALID_ARG;
   int rc = set_device(h);
   if (rc) return rc;
   if (!h->up_ready) {
@@ -826,7 +870,7 @@ int mnl_upload(mnl_handle *h, const mnl_data *hd) {
   };
   if (S.p) CK(copy(const_cast<float *>(h->X), hd->X, (size_t)S.N * S.p * 4));
   if (S.d) CK(copy(const_cast<float *>(h->Y), hd->Y, (size_t)S.N * S.K * S.d * 4));
-  if (S.f) CK(copy(const_cast<float *>(h->Z), hd->Z, (size_t)S.N * S.K * S.f * 4));
+  if (h->dims.f) CK(copy(const_cast<float *>(h->Zu), hd->Z, (size_t)S.N * S.K * h->dims.f * 4));
   CK(copy(const_cast<int32_t *>(h->choice), hd->choice, (size_t)S.N * 4));
   for (int i = 0; i < mnl_handle::kUp; ++i) {
     CK(cudaEventRecord(h->uev[i], h->ust[i]));
@@ -841,9 +885,12 @@ int mnl_loglik_grad(mnl_handle *h, const double *theta, double *loglik, double *
   if (!theta) return MNL_ERR_INVALID_ARG;
   if ((rc = set_device(h))) return rc;
   CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->st));
-  rc = run_pass(h, theta, grad != nullptr, nullptr, kL);
+  const double *th = theta_in(h, theta, &rc);
   if (rc) return rc;
-  if (grad) CK(cudaMemcpyAsync(grad, h->grad, h->S.n * 8, cudaMemcpyDeviceToDevice, h->st));
+  rc = run_pass(h, th, grad != nullptr, nullptr, kL);
+  if (rc) return rc;
+  if (grad && h->gb1) CK(launch_perm_to_user(h->S.n, h->perm, h->grad, grad, h->st));
+  else if (grad) CK(cudaMemcpyAsync(grad, h->grad, h->S.n * 8, cudaMemcpyDeviceToDevice, h->st));
   if (loglik) {
     CK(cudaMemcpyAsync(h->h_scal, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(h->h_flags + 1, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
@@ -860,9 +907,12 @@ int mnl_hessian(mnl_handle *h, const double *theta, double *H) {
   if (!theta || !H) return MNL_ERR_INVALID_ARG;
   if ((rc = set_device(h))) return rc;
   CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->st));
-  if ((rc = run_pass(h, theta, true, nullptr, kL))) return rc;
+  const double *th = theta_in(h, theta, &rc);
+  if (rc) return rc;
+  if ((rc = run_pass(h, th, true, nullptr, kL))) return rc;
   if ((rc = run_hessian(h))) return rc;
-  CK(launch_export_hessian(h->S.n, h->F, H, h->st));
+  if (h->gb1) CK(launch_export_hessian_perm(h->S.n, h->F, h->perm, H, h->st));
+  else CK(launch_export_hessian(h->S.n, h->F, H, h->st));
   return MNL_OK;
 }
 
@@ -871,7 +921,13 @@ int mnl_newton_step(mnl_handle *h, double *theta, mnl_step_info *info) {
   if (rc) return rc;
   if (!theta) return MNL_ERR_INVALID_ARG;
   if ((rc = set_device(h))) return rc;
-  return step_impl(h, theta, info, 0.0, nullptr, 30);
+  if (!h->gb1) return step_impl(h, theta, info, 0.0, nullptr, 30);
+  double *th = const_cast<double *>(theta_in(h, theta, &rc));
+  if (rc) return rc;
+  rc = step_impl(h, th, info, 0.0, nullptr, 30);
+  if (rc == MNL_OK) CK(launch_perm_to_user(h->S.n, h->perm, th, theta, h->st));
+  if (rc == MNL_OK) CK(cudaStreamSynchronize(h->st));
+  return rc;
 }
 
 int mnl_fit(mnl_handle *h, const mnl_fit_opts *opts, double *theta, mnl_fit_info *info) {
@@ -884,6 +940,9 @@ int mnl_fit(mnl_handle *h, const mnl_fit_opts *opts, double *theta, mnl_fit_info
   if (opts) o = *opts;
   if (o.maxiter < 0 || o.max_halvings < 0) return MNL_ERR_INVALID_ARG;
   const double steptol = o.steptol >= 0 ? o.steptol : (h->fp64 ? 1e-10 : 1e-7);
+  double *const theta_user = theta;
+  theta = const_cast<double *>(theta_in(h, theta_user, &rc));  // gamma_base = 1: the kernels' order
+  if (rc) return rc;
   mnl_fit_info fi{};
   const auto t0 = std::chrono::steady_clock::now();
   rc = MNL_MAXITER;
@@ -919,10 +978,74 @@ int mnl_fit(mnl_handle *h, const mnl_fit_opts *opts, double *theta, mnl_fit_info
     prev_step_rel = fi.step_rel;
   }
   if (rc == MNL_MAXITER) fi.stop_reason = MNL_STOP_MAXITER;
+  if (h->gb1) {
+    CK(launch_perm_to_user(h->S.n, h->perm, theta, theta_user, h->st));
+    CK(cudaStreamSynchronize(h->st));
+  }
   fi.status = rc;
   fi.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = fi;
   return rc;
+}
+
+int mnl_std_errors(mnl_handle *h, const double *theta, double *se) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!theta || !se) return MNL_ERR_INVALID_ARG;
+  if ((rc = set_device(h))) return rc;
+  const int64_t n = h->S.n;
+  if (!h->Binv && (rc = dalloc(h, &h->Binv, (size_t)n * n * 8))) return rc;
+  CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->st));
+  const double *th = theta_in(h, theta, &rc);
+  if (rc) return rc;
+  if ((rc = run_pass(h, th, true, nullptr, kL))) return rc;
+  if ((rc = run_hessian(h))) return rc;
+  CK(launch_std_errors(n, h->F, h->Binv, h->dinv, h->cwork, h->status, h->err, h->gb1 ? h->vec_int : se, h->st,
+                       h->wait_ns));
+  if (h->gb1) CK(launch_perm_to_user(n, h->perm, h->vec_int, se, h->st));
+  CK(cudaMemcpyAsync(h->h_flags, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(h->h_flags + 1, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (h->h_flags[1]) return MNL_ERR_TIMEOUT;
+  if (h->h_flags[0] & 4) return MNL_ERR_NOT_PD;
+  return MNL_OK;
+}
+
+int mnl_predict(mnl_handle *h, const double *theta, double *P, double *loglik) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!theta || !P) return MNL_ERR_INVALID_ARG;
+  if ((rc = set_device(h))) return rc;
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->st));
+  const double *th = theta_in(h, theta, &rc);
+  if (rc) return rc;
+  if ((rc = run_pass(h, th, true, nullptr, kL))) return rc;
+  CK(launch_export_probs(h->S.N * (int64_t)h->S.K, h->P, h->fp64, P, h->st));
+  if (loglik) {
+    CK(cudaMemcpyAsync(h->h_scal, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(h->h_flags + 1, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (h->h_flags[1]) return MNL_ERR_TIMEOUT;
+    *loglik = h->h_scal[0];
+  }
+  return MNL_OK;
+}
+
+int mnl_set_weights(mnl_handle *h, const float *w) {
+  if (!h) return MNL_ERR_INVALID_ARG;
+  if (!w) { h->w = nullptr; return MNL_OK; }
+  if ((reinterpret_cast<uintptr_t>(w) & 15) != 0) return MNL_ERR_INVALID_ARG;
+  int rc = set_device(h);
+  if (rc) return rc;
+  CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
+  CK(launch_validate_weights(h->S.N, w, h->status, h->st));
+  CK(cudaMemcpyAsync(h->h_flags, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (h->h_flags[0] & 2) return MNL_ERR_NONFINITE;
+  if (h->h_flags[0] & 1) return MNL_ERR_INVALID_ARG;
+  h->w = w;
+  return MNL_OK;
 }
 
 int mnl_set_wait_bound(mnl_handle *h, uint64_t ns) {

@@ -12,6 +12,8 @@
 // alpha-alpha derivation, with raw Z: a per-row shift of Z cancels).
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "mnl_internal.cuh"
 
 namespace mnl {
@@ -126,6 +128,7 @@ struct BuildDims {
   int f;   // Z operand (Az != nullptr): generic columns and its row-block offsets
   int64_t oY, oW, oZ;
   int64_t rpA, rpZ;  // padded row counts of At / Ad and of Az (K-blocked layout)
+  const float *w;    // [N] observation weights (every operand row scaled by sqrt(w_i)), or nullptr
 };
 
 // Element offset of operand row `row`, observation i.  float64 operands are
@@ -164,10 +167,17 @@ __device__ __forceinline__ void build_block(const BuildDims &D, const float *__r
   float *YsT = XsT + (size_t)p * kBs;
   CT *ZcT = reinterpret_cast<CT *>(YsT + (size_t)D.kc * d * kBs);
   CT *zbT = ZcT + (size_t)D.kc * f * kBs;
+  CT *swT = zbT + (size_t)f * kBs;  // sqrt(w_i) of the block's observations (weights only)
   const int64_t i0 = blk * kBob;
   const int nobs = (int)min((int64_t)kBob, D.N - i0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const FastDiv divK((uint32_t)K), divp((uint32_t)p), divq((uint32_t)q), divd((uint32_t)d), divf((uint32_t)f);
+  // Case weights: -H = sum_i w_i [...] is the SYRK of operand rows scaled by sqrt(w_i).
+  if (D.w) {
+    for (int r = tid; r < kBob; r += 256) swT[r] = r < nobs ? (CT)sqrt((double)D.w[i0 + r]) : (CT)0;
+    __syncthreads();
+  }
+  auto sw = [&](int r) { return D.w ? swT[r] : (CT)1; };
 
   // staging, kStage loads in flight per thread
   for (int e0 = 0; e0 < kBob * K; e0 += kStage * 256) {
@@ -182,9 +192,9 @@ __device__ __forceinline__ void build_block(const BuildDims &D, const float *__r
       const int e = e0 + tid + u * 256;
       if (e < kBob * K) {
         const int r = divK.div(e), k = e - r * K;
-        const CT pk = (CT)v[u], w = pk * ((CT)1 - pk);
-        PsT[k * kBs + r] = pk;
-        WsT[k * kBs + r] = w > (CT)0 ? sqrt(w) : (CT)0;
+        const CT pk = (CT)v[u], w = pk * ((CT)1 - pk), s = sw(r);
+        PsT[k * kBs + r] = pk * s;
+        WsT[k * kBs + r] = w > (CT)0 ? sqrt(w) * s : (CT)0;
       }
     }
   }
@@ -225,7 +235,7 @@ __device__ __forceinline__ void build_block(const BuildDims &D, const float *__r
       CT v[8];
       lds8(XsT + l * kBs + oc, m);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = (CT)m[u];
+      for (int u = 0; u < 8; ++u) v[u] = (CT)m[u] * sw(oc + u);
       put_z(l, v);
     }
   }
@@ -326,7 +336,7 @@ __device__ __forceinline__ void build_block(const BuildDims &D, const float *__r
           float m[8];
           lds8(YsT + (kk * d + l) * kBs + oc, m);
 #pragma unroll
-          for (int u = 0; u < 8; ++u) v[u] = (CT)m[u];
+          for (int u = 0; u < 8; ++u) v[u] = (CT)m[u] * sw(oc + u);
           row = D.oY + (int64_t)(ks + kq - 1) * d + l;
         } else if (c < ny + nwz) {
           const int c2 = c - ny, kk = divf.div(c2);
@@ -339,6 +349,8 @@ __device__ __forceinline__ void build_block(const BuildDims &D, const float *__r
         } else {
           const int c2 = c - ny - nwz;
           lds8(ZcT + c2 * kBs + oc, v);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] *= sw(oc + u);
           row = D.oZ + (int64_t)k0 * f + c2;
         }
         put_z(row, v);
@@ -373,6 +385,7 @@ __global__ void __launch_bounds__(256) grouped_build_kernel(const GroupProblem *
   D.N = g.N; D.ldn = g.ldn; D.K = g.K; D.p = g.p; D.d = g.d; D.q = g.p + g.d;
   D.ob = g.build_ob; D.kc = g.build_kc;
   D.rpA = g.mc_pad; D.rpZ = 0;
+  D.w = nullptr;
   build_block<OT, PT>(D, g.X, g.Y, reinterpret_cast<const PT *>(g.P), g.At, g.Ad, it.idx);
 }
 
@@ -526,6 +539,7 @@ struct ZDims {
   int nsplit;   // observation splits
   int64_t nzt;  // outputs per split
   ZPlan zp;
+  const float *w;  // [N] observation weights (they scale P_ik in W = P (z - zbar)), or nullptr
 };
 
 template <typename T>
@@ -573,7 +587,7 @@ __device__ __forceinline__ void zx_part(const ZDims &D, const float *__restrict_
       xv[s] = (in && xcol) ? __ldg(X + i * p + l0 + cc) : 0.f;
       if (in && zcol) {
         zv[s] = __ldg(Z + i * Kf + c);
-        pv[s] = P[i * K + k];
+        pv[s] = P[i * K + k] * (D.w ? (T)D.w[i] : (T)1);
         bv[s] = zbar[i * f + j];
       } else {
         zv[s] = 0.f; pv[s] = (T)0; bv[s] = (T)0;
@@ -683,7 +697,7 @@ __device__ __forceinline__ void zy_part(const ZDims &D, const float *__restrict_
           const int64_t i = rb + q0 + u;
           const bool in = q0 + u < nr;
           zv[u] = in ? __ldg(Z + i * Kf + (int64_t)kb * f + c) : 0.f;
-          pv[u] = in ? P[i * K + kb + kk] : (T)0;
+          pv[u] = in ? P[i * K + kb + kk] * (D.w ? (T)D.w[i] : (T)1) : (T)0;
           bv[u] = in ? zbar[i * f + j] : (T)0;
         }
 #pragma unroll
@@ -748,7 +762,7 @@ __device__ __forceinline__ void za_part(const ZDims &D, const float *__restrict_
             const int64_t i = rb + q0 + u;
             const bool in = jin && q0 + u < nr;
             zv[u] = in ? __ldg(Z + i * Kf + kk * f + j) : 0.f;
-            pv[u] = in ? P[i * K + kk] : (T)0;
+            pv[u] = in ? P[i * K + kk] * (D.w ? (T)D.w[i] : (T)1) : (T)0;
             bv[u] = in ? zbar[i * f + j] : (T)0;
           }
 #pragma unroll
@@ -826,6 +840,7 @@ __global__ void __launch_bounds__(kZThreads) grouped_zblocks_kernel(const GroupP
   D.N = g.N; D.K = g.K; D.p = g.p; D.d = g.d; D.f = g.f;
   D.nsplit = g.zsplit;
   D.nzt = (int64_t)g.p * g.K * g.f + (int64_t)g.K * g.d * g.f + (int64_t)g.f * g.f;
+  D.w = nullptr;
   D.zp = make_zplan(g.K, g.p, g.d, g.f, (int)sizeof(T));
   const int parts = D.zp.parts();
   const int split = it.idx / parts, part = it.idx % parts;
@@ -995,7 +1010,7 @@ size_t build_smem_bytes(const Shape &s, OpType t, int ob, int kc, bool with_z) {
   (void)ob;
   const size_t csz = t == OpType::F64 ? 8 : 4;
   return (size_t)2 * s.K * kBs * csz + ((size_t)s.p + (size_t)kc * s.d) * kBs * 4 +
-         (with_z ? ((size_t)kc * s.f + s.f) * kBs * csz : 0);
+         (with_z ? ((size_t)kc * s.f + s.f) * kBs * csz : 0) + (size_t)kBs * csz;  // + sqrt(w) of the block
 }
 
 // Classes per staging chunk: the most that keep three blocks on an SM (so that
@@ -1011,8 +1026,10 @@ void build_blocking(const Shape &s, OpType t, int *ob, int *kc, bool with_z) {
 }
 
 cudaError_t launch_build_operands(const Shape &s, OpType t, const float *X, const float *Y, const void *P, void *At,
-                                  void *Ad, int64_t ldn, cudaStream_t st, const float *Z, const void *zbar, void *Az) {
+                                  void *Ad, int64_t ldn, cudaStream_t st, const float *Z, const void *zbar, void *Az,
+                                  const float *w) {
   BuildDims D;
+  D.w = w;
   D.N = s.N; D.ldn = ldn; D.K = s.K; D.p = s.p; D.d = s.d; D.q = s.q;
   D.rpA = (s.mc + kTile - 1) / kTile * kTile;
   D.rpZ = 0;
@@ -1162,9 +1179,10 @@ cudaError_t launch_grouped_syrk_f64(const GroupProblem *probs, const SyrkUnit *u
 int f64_chunk_rows() { return kKc; }
 
 cudaError_t launch_zblocks(const Shape &s, bool fp64, const float *X, const float *Y, const float *Z, const void *P,
-                           const void *zbar, int nsplit, void *out, cudaStream_t st) {
+                           const void *zbar, int nsplit, void *out, cudaStream_t st, const float *w) {
   ZDims D;
   D.N = s.N; D.K = s.K; D.p = s.p; D.d = s.d; D.f = s.f;
+  D.w = w;
   D.nsplit = nsplit;
   D.nzt = zblocks_outputs(s);
   D.zp = make_zplan(s.K, s.p, s.d, s.f, fp64 ? 8 : 4);
@@ -1246,6 +1264,19 @@ ZTiles zop_tiles(const Shape &s, const ZopLayout &L) {
   return z;
 }
 
+
+namespace {
+__global__ void export_probs_kernel(int64_t count, const void *__restrict__ P, int fp64, double *__restrict__ out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = fp64 ? reinterpret_cast<const double *>(P)[e] : (double)reinterpret_cast<const float *>(P)[e];
+}
+}  // namespace
+
+cudaError_t launch_export_probs(int64_t count, const void *P, bool fp64, double *out, cudaStream_t st) {
+  const int64_t blocks = std::min<int64_t>((count + 255) / 256, 4096);
+  export_probs_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(count, P, fp64 ? 1 : 0, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_export_hessian(int64_t n, const double *F, double *H, cudaStream_t st) {
   dim3 grid, block;

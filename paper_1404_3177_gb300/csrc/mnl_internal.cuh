@@ -90,6 +90,7 @@ struct PassIO {
   double *partials;      // [grid][2 + n] (FULL) or [grid][2] (loglik only)
   int *err;              // error word (bit 16: a tile copy did not complete in time); tiled pass only
   uint64_t wait_ns;      // bound of the tile-copy waits (0: the default, 2 s)
+  const float *w;        // [N] observation weights, or nullptr (all ones)
 };
 
 // Bits of the device error word: which kernel's bounded wait gave up.
@@ -216,7 +217,7 @@ cudaError_t launch_validate(const Shape &s, const float *X, const float *Y, cons
 // Class operands At, Ad (and, when Az != nullptr, the rows of the Z-block operand from the same staged block).
 cudaError_t launch_build_operands(const Shape &s, OpType t, const float *X, const float *Y, const void *P, void *At,
                                   void *Ad, int64_t ldn, cudaStream_t st, const float *Z = nullptr,
-                                  const void *zbar = nullptr, void *Az = nullptr);
+                                  const void *zbar = nullptr, void *Az = nullptr, const float *w = nullptr);
 
 // Tile lists (pairs (ti, tj), ti >= tj) of the two contractions.
 struct TileLists {
@@ -258,7 +259,9 @@ cudaError_t launch_syrk_tc(OpType t, const CUtensorMap *maps, const SyrkUnit *un
 // out[s][zblocks_outputs()] = [C_X: p*K*f | C_Y: K*d*f | A: f*f] (see hessian.cu).
 int64_t zblocks_outputs(const Shape &s);
 cudaError_t launch_zblocks(const Shape &s, bool fp64, const float *X, const float *Y, const float *Z, const void *P,
-                           const void *zbar, int nsplit, void *out, cudaStream_t st);
+                           const void *zbar, int nsplit, void *out, cudaStream_t st, const float *w = nullptr);
+// Data validation of observation weights: status bits |= 1 (negative), 2 (non-finite).
+cudaError_t launch_validate_weights(int64_t N, const float *w, int *status, cudaStream_t st);
 
 // Assemble F = -H (n x n, column-major, both triangles) from the contraction
 // partials.  main/band partials are FP32 (tensor path) or FP64.
@@ -304,6 +307,13 @@ size_t chol_work_bytes(int64_t n);
 int cholesky_launches(int64_t n);
 cudaError_t launch_cholesky(int64_t n, double *F, double *dinv, void *work, int *status, int *err, cudaStream_t st,
                             uint64_t wait_ns = 0);
+// Standard errors sqrt(diag(F^{-1})): float64 factor of F (in place) with the
+// inverse of the factor Binv (n x n scratch), then the column norms of Binv.
+// status |= 4 when F is not positive definite (se is then NaN).
+cudaError_t launch_std_errors(int64_t n, double *F, double *Binv, double *dinv, void *work, int *status, int *err,
+                              double *se, cudaStream_t st, uint64_t wait_ns = 0);
+// Probabilities [N][K] in float64 from the pass's P (float32 or float64).
+cudaError_t launch_export_probs(int64_t count, const void *P, bool fp64, double *out, cudaStream_t st);
 // Solve L L^T x = b with the factor above (FP64; skipped when status & 4).
 cudaError_t launch_cholesky_solve(int64_t n, const double *L, const double *dinv, const double *b, double *x,
                                   const int *status, cudaStream_t st, int *launches);
@@ -368,6 +378,22 @@ cudaError_t tc_chol_prepare(int64_t n, void *ws, int num_sms, TcCholPlan *plan);
 cudaError_t launch_mixed_solve_tc(const TcCholPlan &plan, const double *F, float *F32, const double *g, double *delta,
                                   void *work, int *status, int *err, int iters, uint64_t wait_ns, cudaStream_t st,
                                   int *launches);
+
+// Paper-literal gamma_0 (gamma_base = 1): the model equals a gamma_base = 0
+// model with d more generic (Z-type) columns z'_ikj = (k == 0 ? y_i0j : 0),
+// whose coefficients are gamma_0 (only differences against alternative 0
+// enter: z'_ik - z'_i0 = -y_i0 for k >= 1, the paper's -Y_i0 gamma_0 term).
+// Zaug [N][K][f + d] = [Z | that block].
+cudaError_t launch_augment_z(int64_t N, int K, int d, int f, const float *Y, const float *Z, float *Zaug,
+                             cudaStream_t st);
+// theta orders: user (gamma_0 before gamma_1) and internal (gamma_0 after alpha);
+// perm[u] = internal index of user coefficient u.
+cudaError_t launch_perm_to_internal(int64_t n, const int64_t *perm, const double *user, double *internal,
+                                    cudaStream_t st);
+cudaError_t launch_perm_to_user(int64_t n, const int64_t *perm, const double *internal, double *user,
+                                cudaStream_t st);
+// H[u][v] = -F[perm[u]][perm[v]] (column-major, both triangles of F present).
+cudaError_t launch_export_hessian_perm(int64_t n, const double *F, const int64_t *perm, double *H, cudaStream_t st);
 
 // Small FP64 vector kernels.
 cudaError_t launch_axpy_theta(int64_t n, double *theta, const double *delta, const double *tscale, double *scal_out,

@@ -19,6 +19,7 @@
 //     alpha_k[j] += sum_rows r_ik Z_ikj   (summed over k at the end).
 // In float32 the per-tile sums are folded into Kahan-compensated running sums;
 // each CTA writes float64 partials that a second kernel adds in fixed order.
+#include <algorithm>
 #include <cfloat>
 
 #include "mnl_internal.cuh"
@@ -159,6 +160,7 @@ __device__ __forceinline__ void pass_segment(const PassDims &D, const PassIO &io
       const int64_t i = row0 + r;
       const float *x = Xs + (size_t)r * p;
       const int yi = __ldg(io.choice + i);
+      const T wi = io.w ? (T)__ldg(io.w + i) : (T)1;  // case weight (Sec. 2.3 "weights")
       T u[kMaxClassSlots];
       T umax = -(T)FLT_MAX, uy = 0;
 #pragma unroll
@@ -190,8 +192,8 @@ __device__ __forceinline__ void pass_segment(const PassDims &D, const PassIO &io
       const T lse = umax + flog(s);
       if (lane == 0) {
         const T li = uy - lse;
-        lsum.add(li);
-        labs.add(fabs(li));
+        lsum.add(wi * li);
+        labs.add(wi * fabs(li));
       }
       if (FULL) {
         T *pr = reinterpret_cast<T *>(io.P) + i * K;
@@ -202,7 +204,7 @@ __device__ __forceinline__ void pass_segment(const PassDims &D, const PassIO &io
             const T P = u[c] * inv;
             u[c] = P;
             pr[k] = P;
-            res[(size_t)r * K + k] = (k == yi ? (T)1 : (T)0) - P;
+            res[(size_t)r * K + k] = wi * ((k == yi ? (T)1 : (T)0) - P);
           }
         }
         for (int j = 0; j < f; ++j) {
@@ -518,6 +520,80 @@ cudaError_t launch_grouped_npt(const GroupedPassPlan &pl, const GroupProblem *pr
     case 32: return launch_grouped_t<T, FULL, 32>(pl, probs, segs, seg_start, active, partials, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+__global__ void validate_weights_kernel(int64_t N, const float *__restrict__ w, int *status) {
+  int bad = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = w[i];
+    if (!isfinite(v)) bad |= 2;
+    else if (v < 0.f) bad |= 1;
+  }
+  if (bad) atomicOr(status, bad);
+}
+
+__global__ void augment_z_kernel(int64_t N, int K, int d, int f, const float *__restrict__ Y,
+                                 const float *__restrict__ Z, float *__restrict__ Za) {
+  const int fa = f + d;
+  const int64_t total = N * K * fa;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ik = e / fa;
+    const int j = (int)(e - ik * fa);
+    const int64_t i = ik / K;
+    const int k = (int)(ik - i * K);
+    Za[e] = j < f ? Z[ik * f + j] : (k == 0 ? Y[i * K * d + (j - f)] : 0.f);
+  }
+}
+
+__global__ void perm_kernel(int64_t n, const int64_t *__restrict__ perm, const double *__restrict__ in,
+                            double *__restrict__ out, int to_user) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    if (to_user) out[u] = in[perm[u]];
+    else out[perm[u]] = in[u];
+  }
+}
+
+__global__ void export_hessian_perm_kernel(int64_t n, const double *__restrict__ F, const int64_t *__restrict__ perm,
+                                           double *__restrict__ H) {
+  const int64_t v = blockIdx.y + (int64_t)gridDim.y * blockIdx.z;
+  if (v >= n) return;
+  const int64_t pv = perm[v];
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+    H[v * n + u] = -F[pv * n + perm[u]];
+}
+
+cudaError_t launch_augment_z(int64_t N, int K, int d, int f, const float *Y, const float *Z, float *Zaug,
+                             cudaStream_t st) {
+  const int64_t total = N * K * (f + d);
+  const int64_t blocks = std::min<int64_t>((total + 255) / 256, 8192);
+  augment_z_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(N, K, d, f, Y, Z, Zaug);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_perm_to_internal(int64_t n, const int64_t *perm, const double *user, double *internal,
+                                    cudaStream_t st) {
+  perm_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 1024)), 256, 0, st>>>(
+      n, perm, user, internal, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_perm_to_user(int64_t n, const int64_t *perm, const double *internal, double *user,
+                                cudaStream_t st) {
+  perm_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 1024)), 256, 0, st>>>(
+      n, perm, internal, user, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_hessian_perm(int64_t n, const double *F, const int64_t *perm, double *H, cudaStream_t st) {
+  const dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)std::min<int64_t>(n, 65535),
+                  (unsigned)((n + 65534) / 65535));
+  export_hessian_perm_kernel<<<grid, 256, 0, st>>>(n, F, perm, H);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate_weights(int64_t N, const float *w, int *status, cudaStream_t st) {
+  validate_weights_kernel<<<1024, 256, 0, st>>>(N, w, status);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_validate(const Shape &s, const float *X, const float *Y, const float *Z, const int32_t *choice,

@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(kPT, kYZSlots == 4 ? 1 : 2) pass_tile_kernel(T
         const int rr = r0 + r;
         const bool vr = rr < nrows;
         const int yi = cs[rr];
+        const float wr = (io.w && vr) ? __ldg(io.w + row0 + rr) : 1.f;  // case weight
         float m = -FLT_MAX;
 #pragma unroll
         for (int c = 0; c < CS; ++c)
@@ -303,8 +304,8 @@ __global__ void __launch_bounds__(kPT, kYZSlots == 4 ? 1 : 2) pass_tile_kernel(T
         uy = wsum(uy);
         if (vr && lane == 0) {
           const float li = uy - (m + logf(sum));
-          lsum.add(li);
-          labs.add(fabsf(li));
+          lsum.add(wr * li);
+          labs.add(wr * fabsf(li));
         }
         if (FULL) {
           const float inv = 1.f / sum;
@@ -315,7 +316,7 @@ __global__ void __launch_bounds__(kPT, kYZSlots == 4 ? 1 : 2) pass_tile_kernel(T
             const float P = u[r][c] * inv;
             u[r][c] = P;
             if (k < K && vr) Pg[k] = P;
-            res[c][r] = (k < K && vr) ? ((k == yi ? 1.f : 0.f) - P) : 0.f;
+            res[c][r] = (k < K && vr) ? wr * ((k == yi ? 1.f : 0.f) - P) : 0.f;
           }
           for (int j = 0; j < f; ++j) {
             float zb = 0.f;
@@ -464,11 +465,11 @@ __global__ void __launch_bounds__(kPT, kYZSlots == 4 ? 1 : 2) pass_tile_kernel(T
 template <int JA, int KB>
 __global__ void __launch_bounds__(256, 1) grad_beta_kernel(int64_t N, int K, int p, int64_t n,
                                                            const float *__restrict__ X, const float *__restrict__ P,
-                                                           const int *__restrict__ choice, double *partials,
-                                                           int *err, uint64_t wait_ns) {
+                                                           const int *__restrict__ choice, const float *w,
+                                                           double *partials, int *err, uint64_t wait_ns) {
   extern __shared__ __align__(128) unsigned char sm[];
   const int sx = ((kGbRows * p * 4) + 127) & ~127, sp = ((kGbRows * K * 4) + 127) & ~127;
-  const int stage_bytes = sx + sp + 128;
+  const int stage_bytes = sx + sp + 256;
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kGbStages * stage_bytes);
   __shared__ int s_abort;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -480,7 +481,7 @@ __global__ void __launch_bounds__(256, 1) grad_beta_kernel(int64_t N, int K, int
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  const uint32_t tile_bytes = (uint32_t)(kGbRows * (p + K + 1) * 4);
+  const uint32_t tile_bytes = (uint32_t)(kGbRows * (p + K + 1 + (w ? 1 : 0)) * 4);
   auto full_tile = [&](int64_t tl) { return (tl + 1) * kGbRows <= N; };
   auto issue = [&](int64_t tl, int st) {
     const int64_t r0 = tl * kGbRows;
@@ -490,6 +491,7 @@ __global__ void __launch_bounds__(256, 1) grad_beta_kernel(int64_t N, int K, int
     bulk_copy(b, X + r0 * p, (uint32_t)(kGbRows * p * 4), &bar[st]);
     bulk_copy(b + sx, P + r0 * K, (uint32_t)(kGbRows * K * 4), &bar[st]);
     bulk_copy(b + sx + sp, choice + r0, (uint32_t)(kGbRows * 4), &bar[st]);
+    if (w) bulk_copy(b + sx + sp + 128, w + r0, (uint32_t)(kGbRows * 4), &bar[st]);
   };
   int pend[kGbStages];
   for (int st = 0; st < kGbStages; ++st) pend[st] = -1;
@@ -507,6 +509,7 @@ __global__ void __launch_bounds__(256, 1) grad_beta_kernel(int64_t N, int K, int
     float *Xs = reinterpret_cast<float *>(b);
     float *Ps = reinterpret_cast<float *>(b + sx);
     int *cs = reinterpret_cast<int *>(b + sx + sp);
+    float *ws = reinterpret_cast<float *>(b + sx + sp + 128);
     const int64_t r0 = tl * kGbRows;
     const int nrows = (int)(N - r0 < kGbRows ? N - r0 : kGbRows);
     if (nrows == kGbRows) {
@@ -516,6 +519,8 @@ __global__ void __launch_bounds__(256, 1) grad_beta_kernel(int64_t N, int K, int
       for (int e = tid; e < kGbRows * p; e += 256) Xs[e] = e < nrows * p ? X[r0 * p + e] : 0.f;
       for (int e = tid; e < kGbRows * K; e += 256) Ps[e] = e < nrows * K ? P[r0 * K + e] : 0.f;
       for (int e = tid; e < kGbRows; e += 256) cs[e] = e < nrows ? choice[r0 + e] : -1;
+      if (w)
+        for (int e = tid; e < kGbRows; e += 256) ws[e] = e < nrows ? w[r0 + e] : 0.f;
     }
     __syncthreads();
     if (s_abort) break;
@@ -527,6 +532,7 @@ __global__ void __launch_bounds__(256, 1) grad_beta_kernel(int64_t N, int K, int
 #pragma unroll 2
     for (int r = 0; r < kGbRows; ++r) {
       const int y = cs[r];
+      const float wr = w ? ws[r] : 1.f;
       float x[JA], rr[KB];
 #pragma unroll
       for (int a = 0; a < JA; ++a) {
@@ -536,7 +542,7 @@ __global__ void __launch_bounds__(256, 1) grad_beta_kernel(int64_t N, int K, int
 #pragma unroll
       for (int c = 0; c < KB; ++c) {
         const int k = ty + 16 * c;
-        rr[c] = k < K ? (k == y ? 1.f : 0.f) - Ps[r * K + k] : 0.f;
+        rr[c] = k < K ? wr * ((k == y ? 1.f : 0.f) - Ps[r * K + k]) : 0.f;
       }
 #pragma unroll
       for (int a = 0; a < JA; ++a)
@@ -574,7 +580,7 @@ __global__ void __launch_bounds__(256, 1) grad_beta_kernel(int64_t N, int K, int
 
 size_t grad_beta_smem(int K, int p) {
   const int sx = ((kGbRows * p * 4) + 127) & ~127, sp = ((kGbRows * K * 4) + 127) & ~127;
-  return (size_t)kGbStages * (sx + sp + 128) + kGbStages * 8;
+  return (size_t)kGbStages * (sx + sp + 256) + kGbStages * 8;
 }
 
 template <int JA, int KB>
@@ -583,7 +589,7 @@ cudaError_t launch_gb(const Shape &s, int grid, const PassIO &io, cudaStream_t s
   const size_t smem = grad_beta_smem(s.K, s.p);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, 256, smem, st>>>(s.N, s.K, s.p, s.n, io.X, reinterpret_cast<const float *>(io.P), io.choice,
+  kern<<<grid, 256, smem, st>>>(s.N, s.K, s.p, s.n, io.X, reinterpret_cast<const float *>(io.P), io.choice, io.w,
                                 io.partials, io.err, io.wait_ns);
   return cudaGetLastError();
 }
@@ -691,6 +697,7 @@ cudaError_t launch_pass_tiled(const Shape &s, const PassPlan &pl, bool full, con
   size_t smem = 0;
   if (!make_tile_dims(s, full, pl.rows / 8, D, smem) || smem != pl.smem || io.err == nullptr) return cudaErrorInvalidValue;
   const bool aligned = ((reinterpret_cast<uintptr_t>(io.X) | reinterpret_cast<uintptr_t>(io.choice) |
+                         reinterpret_cast<uintptr_t>(io.w) |
                          (s.d ? reinterpret_cast<uintptr_t>(io.Y) : 0) | (s.f ? reinterpret_cast<uintptr_t>(io.Z) : 0)) &
                         15) == 0;
   if (!aligned) return cudaErrorInvalidValue;

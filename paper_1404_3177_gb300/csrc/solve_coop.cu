@@ -1117,6 +1117,23 @@ MixedLayout mixed_layout(int64_t n) {
   return L;
 }
 
+// Standard errors: se_j = sqrt((F^{-1})_jj) = the norm of column j of L^{-1}
+// (F^{-1} = L^{-T} L^{-1}), one warp per column (contiguous, rows j .. n-1).
+__global__ void __launch_bounds__(256) column_norms_kernel(int64_t n, const double *__restrict__ B,
+                                                           const int *__restrict__ status, double *__restrict__ se) {
+  const int lane = threadIdx.x & 31;
+  const int64_t j = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (j >= n) return;
+  double s = 0.0;
+  for (int64_t i = j + lane; i < n; i += 32) {
+    const double b = B[j * n + i];
+    s = fma(b, b, s);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) se[j] = (*status & 4) ? nan("") : sqrt(s);
+}
+
 }  // namespace
 
 size_t chol_work_bytes(int64_t n) {
@@ -1131,6 +1148,19 @@ cudaError_t launch_cholesky(int64_t n, double *F, double *dinv, void *work, int 
   double *Dinv = reinterpret_cast<double *>(w);
   GridBarrier *bar = reinterpret_cast<GridBarrier *>(w + round256((size_t)panels(n) * kCb * kCb * 8));
   return launch_coop<double, false>(n, F, nullptr, Dinv, dinv, bar, status, 4, err, st, wait_ns);
+}
+
+cudaError_t launch_std_errors(int64_t n, double *F, double *Binv, double *dinv, void *work, int *status, int *err,
+                              double *se, cudaStream_t st, uint64_t wait_ns) {
+  unsigned char *w = static_cast<unsigned char *>(work);
+  double *Dinv = reinterpret_cast<double *>(w);
+  GridBarrier *bar = reinterpret_cast<GridBarrier *>(w + round256((size_t)panels(n) * kCb * kCb * 8));
+  cudaError_t e = cudaMemsetAsync(Binv, 0, (size_t)n * n * 8, st);
+  if (e != cudaSuccess) return e;
+  if ((e = launch_coop<double, true>(n, F, Binv, Dinv, dinv, bar, status, 4, err, st, wait_ns)) != cudaSuccess)
+    return e;
+  column_norms_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(n, Binv, status, se);
+  return cudaGetLastError();
 }
 
 size_t mixed_solve_bytes(int64_t n) { return mixed_layout(n).total; }
