@@ -20,9 +20,12 @@ then K steps bracketed by a barrier and torch.cuda.synchronize(); the inputs
 JSON line carries, measured after the timed region (rank 0, one GPU):
 the plain float64 mode on the same workload (one step), the batched workload
 (2048 uneven fits, BF16 and FP64) and the serving workload (Poisson arrivals;
-p50/p99 latency to convergence, fits/s).  With N > 1 GPUs (torchrun) every
-rank fits its own copy of the workload (replicas) and `value` is the sum over
-ranks at the slowest rank's time.
+p50/p99 latency to convergence, fits/s).  With N > 1 GPUs (torchrun) the
+observations are sharded: every rank holds a config-3-sized shard of its own
+rows of one large fit, the partial l, g and -H are added by one NCCL
+all-reduce per iteration and the line-search log-likelihoods by one all-reduce
+of two doubles per trial (paper_1404_3177_gb300.sharded); `value` counts each
+rank's shard as one unit (weak scaling) at the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -357,6 +360,92 @@ def rooflines_of(prob, precision, kern, infos, pk, alu, wname):
     return out
 
 
+def run_sharded(args, world, rank, local):
+    """N > 1 GPUs: one fit of the observations of all ranks (each rank holds a config-3-sized shard of its own
+    rows), one all-reduce of [l, sum|l_i|, g, lower(-H)] per iteration over NCCL and one of two doubles per
+    line-search trial (paper_1404_3177_gb300.sharded)."""
+    import torch
+
+    from paper_1404_3177_gb300 import _build, datagen
+    from paper_1404_3177_gb300.api import MNL
+    from paper_1404_3177_gb300.sharded import ShardEngine, ShardedNewton
+
+    _build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prob = datagen.config3_shard(rank) if args.workload == "c3" else datagen.config2()
+    Xh, Yh, Zh, ch = _host(prob)
+    X, Y, Z, c = (t.to(dev) if t is not None else None for t in (Xh, Yh, Zh, ch))
+    n = prob.n_theta
+    m = MNL(X, Y, Z, c, K=prob.K, precision=args.precision, solve=args.solve)
+    sn = ShardedNewton(ShardEngine(m))
+    theta0 = torch.zeros(n, dtype=torch.float64, device=dev)
+    theta = theta0.clone()
+
+    def step():
+        theta.copy_(theta0)
+        return sn.step(theta)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    infos = [step() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    barrier(world)
+    sec = allmax(world, time.perf_counter() - t0)
+    clocks = sampler.stop() if sampler else None
+    # e2e: each rank uploads its shard from pinned host memory every step
+    mh = MNL.with_host_upload(prob.N, prob.K, prob.p, prob.d, prob.f, precision=args.precision, solve=args.solve)
+    she = ShardedNewton(ShardEngine(mh))
+    out_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    e_steps = max(3, min(args.steps, 10))
+
+    def e2e_step():
+        mh.upload(Xh, Yh, Zh, ch)
+        th = torch.zeros(n, dtype=torch.float64, device=dev)
+        she.step(th)
+        out_h.copy_(th, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    e2e_step()
+    barrier(world)
+    te = time.perf_counter()
+    for _ in range(e_steps):
+        e2e_step()
+    t_e2e = allmax(world, time.perf_counter() - te)
+    mh.close()
+    m.close()
+    if rank != 0:
+        return
+    sums_bytes = 8 * (2 + n + n * (n + 1) // 2)
+    line = {
+        "metric": METRIC, "value": world * args.steps / sec, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * sec / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"bf16": "bf16+f32+f64", "tf32": "tf32+f32+f64", "fp64": "f64"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": f"{prob.name.split('_shard')[0] if '_shard' in prob.name else prob.name}"
+                               f"_x{world}_ranks_observation_sharded", "precision": args.precision, "n_theta": n,
+                   "note": CONFIG_NOTE, "per_rank_rows": prob.N,
+                   "exchange": f"NCCL all-reduce of {sums_bytes} bytes per iteration + 16 bytes per line-search trial"},
+        "value_units": "Newton iterations of the whole (all-rank) problem x ranks: each rank's shard is one "
+                       "config-3-sized problem",
+        "gpu_launches": None,
+        "e2e": {"value": world * e_steps / t_e2e, "unit": UNIT,
+                "h2d_bytes_per_step": int(prob.input_bytes()), "d2h_bytes_per_step": int(n * 8)},
+        "clocks": clocks,
+        "ls_evals_per_step": statistics.median(i.get("ls_evals", 1) for i in infos),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -647,6 +736,8 @@ def main():
     world, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif world > 1:
+        run_sharded(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

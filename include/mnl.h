@@ -268,6 +268,40 @@ MNL_API int mnl_predict(mnl_handle *h, const double *theta, double *P, double *l
 enum { MNL_SOLVE_AUTO = 0, MNL_SOLVE_FP64 = 1, MNL_SOLVE_MIXED = 2 };
 MNL_API int mnl_set_solve(mnl_handle *h, int mode);
 
+/* ------------------------------------------------------------------------
+ * Observation sharding (several GPUs, one process each).  l, g and -H are
+ * sums over the observations (eqs. "log-lik function", "loglik gradient",
+ * "hessian block"), so with the observations split over the GPUs one Newton
+ * step is: every rank forms its partial sums (mnl_shard_grad_hess), the sums
+ * are added across ranks (one all-reduce of mnl_shard_sums_size doubles),
+ * every rank solves the same system (mnl_shard_solve: identical inputs give
+ * identical steps), and each line-search trial adds the ranks' partial
+ * log-likelihoods (mnl_shard_loglik; an all-reduce of two doubles).  The
+ * exchange itself is the caller's (e.g. NCCL); gamma_base = 1 handles return
+ * MNL_ERR_UNSUPPORTED.
+ * ------------------------------------------------------------------------ */
+
+/* 2 + n + n (n + 1) / 2 for n = n_theta (-1 for invalid dims). */
+MNL_API int64_t mnl_shard_sums_size(const mnl_dims *dims);
+/* This handle's partial sums at theta (DEVICE [n_theta] float64) into sums
+ * (DEVICE float64 [mnl_shard_sums_size]): [0] l, [1] sum_i |l_i| (the line
+ * search's rounding allowance), [2 .. 2 + n) g, then the lower triangle of
+ * -H packed column by column (entry (r, c), r >= c, at 2 + n + c n - c (c - 1)
+ * / 2 + r - c).  Synchronises. */
+MNL_API int mnl_shard_grad_hess(mnl_handle *h, const double *theta, double *sums);
+/* delta (DEVICE [n_theta]) solving (-H) delta = g from summed sums (DEVICE),
+ * with the handle's solve mode (as mnl_newton_step).  info (HOST, may be
+ * NULL) receives solve_mode, factor_kind, refine_steps, fallback and
+ * t_factor_ms.  Synchronises.  MNL_ERR_NOT_PD for a singular -H. */
+MNL_API int mnl_shard_solve(mnl_handle *h, const double *sums, double *delta, mnl_step_info *info);
+/* This handle's partial [l, sum_i |l_i|] at theta + t delta (delta NULL:
+ * at theta) into l2 (DEVICE [2] float64).  Synchronises. */
+MNL_API int mnl_shard_loglik(mnl_handle *h, const double *theta, const double *delta, double t, double *l2);
+/* Unit roundoff of the arithmetic of this handle's log-likelihood (2^-53 in
+ * MNL_FP64, 2^-24 otherwise): a line search over summed l accepts a step when
+ * l_new >= l_old - 8 u sum_i |l_i|, as mnl_newton_step does. */
+MNL_API double mnl_loglik_roundoff(const mnl_handle *h);
+
 /* Observation weights (the `weights` argument of the package's mnlogit call,
  * Sec. 2.3), read as case weights: observation i counts w_i times in l, g and
  * H (l = sum_i w_i l_i; integer weights equal repeated rows).

@@ -33,7 +33,8 @@ MNL_STOP_GTOL, MNL_STOP_FTOL, MNL_STOP_STEPTOL, MNL_STOP_MAXITER, MNL_STOP_NOISE
 EXPORTS = (
     "mnl_num_params", "mnl_status_string", "mnl_workspace_bytes", "mnl_fit_opts_default", "mnl_create",
     "mnl_upload", "mnl_loglik_grad", "mnl_hessian", "mnl_newton_step", "mnl_fit", "mnl_destroy",
-    "mnl_loglik_grad_noalloc", "mnl_set_solve", "mnl_set_wait_bound", "mnl_set_weights", "mnl_std_errors", "mnl_predict", "mnl_batch_create", "mnl_batch_num_params", "mnl_batch_fit",
+    "mnl_loglik_grad_noalloc", "mnl_set_solve", "mnl_set_wait_bound", "mnl_set_weights",
+    "mnl_shard_sums_size", "mnl_shard_grad_hess", "mnl_shard_solve", "mnl_shard_loglik", "mnl_loglik_roundoff", "mnl_std_errors", "mnl_predict", "mnl_batch_create", "mnl_batch_num_params", "mnl_batch_fit",
     "mnl_batch_destroy", "mnl_server_opts_default", "mnl_server_create", "mnl_server_submit", "mnl_server_step",
     "mnl_server_poll", "mnl_server_finished", "mnl_server_memory_in_use", "mnl_server_destroy",
 )
@@ -147,6 +148,16 @@ def load() -> C.CDLL:
         lib.mnl_std_errors.argtypes = [vp, vp, vp]
         lib.mnl_predict.restype = i32
         lib.mnl_predict.argtypes = [vp, vp, vp, C.POINTER(C.c_double)]
+        lib.mnl_shard_sums_size.restype = i64
+        lib.mnl_shard_sums_size.argtypes = [C.POINTER(mnl_dims)]
+        lib.mnl_shard_grad_hess.restype = i32
+        lib.mnl_shard_grad_hess.argtypes = [vp, vp, vp]
+        lib.mnl_shard_solve.restype = i32
+        lib.mnl_shard_solve.argtypes = [vp, vp, vp, C.POINTER(mnl_step_info)]
+        lib.mnl_shard_loglik.restype = i32
+        lib.mnl_shard_loglik.argtypes = [vp, vp, vp, C.c_double, vp]
+        lib.mnl_loglik_roundoff.restype = C.c_double
+        lib.mnl_loglik_roundoff.argtypes = [vp]
         lib.mnl_set_weights.restype = i32
         lib.mnl_set_weights.argtypes = [vp, vp]
         lib.mnl_set_wait_bound.restype = i32
@@ -274,6 +285,32 @@ def mnl_predict(handle: int, theta_ptr: int, P_ptr: int, want_loglik: bool = Tru
     _check(load().mnl_predict(C.c_void_p(handle), C.c_void_p(theta_ptr), C.c_void_p(P_ptr),
                               C.byref(l) if want_loglik else None), "mnl_predict")
     return l.value if want_loglik else None
+
+
+def mnl_shard_sums_size(dims: mnl_dims) -> int:
+    return int(load().mnl_shard_sums_size(C.byref(dims)))
+
+
+def mnl_shard_grad_hess(handle: int, theta_ptr: int, sums_ptr: int) -> None:
+    _check(load().mnl_shard_grad_hess(C.c_void_p(handle), C.c_void_p(theta_ptr), C.c_void_p(sums_ptr)),
+           "mnl_shard_grad_hess")
+
+
+def mnl_shard_solve(handle: int, sums_ptr: int, delta_ptr: int) -> dict:
+    info = mnl_step_info()
+    _check(load().mnl_shard_solve(C.c_void_p(handle), C.c_void_p(sums_ptr), C.c_void_p(delta_ptr), C.byref(info)),
+           "mnl_shard_solve")
+    return struct_dict(info)
+
+
+def mnl_shard_loglik(handle: int, theta_ptr: int, delta_ptr: int | None, t: float, l2_ptr: int) -> None:
+    _check(load().mnl_shard_loglik(C.c_void_p(handle), C.c_void_p(theta_ptr),
+                                   C.c_void_p(delta_ptr) if delta_ptr else None, float(t), C.c_void_p(l2_ptr)),
+           "mnl_shard_loglik")
+
+
+def mnl_loglik_roundoff(handle: int) -> float:
+    return float(load().mnl_loglik_roundoff(C.c_void_p(handle)))
 
 
 def mnl_set_weights(handle: int, w_ptr: int | None) -> None:

@@ -551,6 +551,53 @@ const double *theta_in(mnl_handle *h, const double *theta, int *rc) {
   return h->th_int;
 }
 
+// (-H) delta = g from h->F (both triangles) and h->grad, synchronously, with the
+// handle's solve mode: refinement continued while it converges, the float64
+// factorisation when a mixed solve fails.  The sharded Newton step's solve.
+int solve_system(mnl_handle *h, mnl_step_info &loc) {
+  const int64_t n = h->S.n;
+  int nl = 0;
+  const bool mixed = h->solve_mode == MNL_SOLVE_MIXED;
+  CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->st));
+  CK(cudaMemsetAsync(h->ref, 0, 4 * sizeof(double), h->st));
+  if (mixed) {
+    if (h->tcp.ready) {
+      CK(launch_f64_to_f32_lower(n, h->F, h->F32, h->st));
+      CK(launch_mixed_solve_tc(h->tcp, h->F, h->F32, h->grad, h->delta, h->mwork, h->status, h->err, kRefineIters,
+                               h->wait_ns, h->st, &nl));
+    } else {
+      CK(launch_mixed_solve(n, h->F, h->F32, h->grad, h->delta, h->mwork, h->status, h->err, kRefineIters, h->st,
+                            &nl, false, h->wait_ns));
+    }
+    loc.factor_kind = h->tcp.ready ? MNL_FACTOR_TENSOR : MNL_FACTOR_COOP;
+    for (int done = 0;; done += kRefineIters) {
+      CK(cudaMemcpyAsync(h->h_flags, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+      CK(cudaMemcpyAsync(h->h_flags + 1, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+      CK(cudaMemcpyAsync(h->h_scal + 12, h->ref, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      CK(cudaStreamSynchronize(h->st));
+      if (h->h_flags[1]) { loc.wait_errors = h->h_flags[1]; return MNL_ERR_TIMEOUT; }
+      const bool cont = (h->h_flags[0] & 16) && !(h->h_flags[0] & 8) && h->h_scal[13] == 0.0 &&
+                        done + kRefineIters < kRefineMax;
+      if (!cont) break;
+      CK(launch_status_and(h->status, ~16, h->st));
+      CK(launch_mixed_refine(n, h->F, h->grad, h->delta, h->mwork, h->status, kRefineIters, h->st, &nl));
+    }
+    loc.refine_steps = (int)h->h_scal[14];
+    if (!(h->h_flags[0] & (8 | 16))) return MNL_OK;
+    loc.fallback = 1;
+    CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
+  }
+  CK(launch_cholesky(n, h->F, h->dinv, h->cwork, h->status, h->err, h->st, h->wait_ns));
+  CK(launch_cholesky_solve(n, h->F, h->dinv, h->grad, h->delta, h->status, h->st, &nl));
+  CK(cudaMemcpyAsync(h->h_flags, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(h->h_flags + 1, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (h->h_flags[1]) { loc.wait_errors = h->h_flags[1]; return MNL_ERR_TIMEOUT; }
+  if (!mixed) loc.factor_kind = MNL_FACTOR_COOP;
+  return (h->h_flags[0] & 4) ? MNL_ERR_NOT_PD : MNL_OK;
+}
+
 int check_handle(const mnl_handle *h) {
   if (!h) return MNL_ERR_INVALID_ARG;
   if (!h->data_ready) return MNL_ERR_INVALID_ARG;
@@ -1030,6 +1077,72 @@ int mnl_predict(mnl_handle *h, const double *theta, double *P, double *loglik) {
     *loglik = h->h_scal[0];
   }
   return MNL_OK;
+}
+
+int64_t mnl_shard_sums_size(const mnl_dims *d) {
+  const int64_t n = mnl_num_params(d);
+  return n < 0 ? -1 : 2 + n + n * (n + 1) / 2;
+}
+
+int mnl_shard_grad_hess(mnl_handle *h, const double *theta, double *sums) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!theta || !sums) return MNL_ERR_INVALID_ARG;
+  if (h->gb1) return MNL_ERR_UNSUPPORTED;
+  if ((rc = set_device(h))) return rc;
+  const int64_t n = h->S.n;
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->st));
+  if ((rc = run_pass(h, theta, true, nullptr, kL))) return rc;
+  if ((rc = run_hessian(h))) return rc;
+  CK(cudaMemcpyAsync(sums, h->scal + kL, 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemcpyAsync(sums + 2, h->grad, (size_t)n * 8, cudaMemcpyDeviceToDevice, h->st));
+  CK(launch_pack_lower(n, h->F, sums + 2 + n, h->st));
+  CK(cudaMemcpyAsync(h->h_flags + 1, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return h->h_flags[1] ? MNL_ERR_TIMEOUT : MNL_OK;
+}
+
+int mnl_shard_solve(mnl_handle *h, const double *sums, double *delta, mnl_step_info *info) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!sums || !delta) return MNL_ERR_INVALID_ARG;
+  if (h->gb1) return MNL_ERR_UNSUPPORTED;
+  if ((rc = set_device(h))) return rc;
+  const int64_t n = h->S.n;
+  mnl_step_info loc{};
+  CK(cudaEventRecord(h->ev[2], h->st));
+  CK(cudaMemcpyAsync(h->grad, sums + 2, (size_t)n * 8, cudaMemcpyDeviceToDevice, h->st));
+  CK(launch_unpack_lower(n, sums + 2 + n, h->F, h->st));
+  rc = solve_system(h, loc);
+  CK(cudaEventRecord(h->ev[3], h->st));
+  if (rc == MNL_OK) CK(cudaMemcpyAsync(delta, h->delta, (size_t)n * 8, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  loc.solve_mode = h->solve_mode;
+  loc.t_chol_ms = loc.t_factor_ms = elapsed(h->ev[2], h->ev[3]);
+  if (info) *info = loc;
+  return rc;
+}
+
+int mnl_shard_loglik(mnl_handle *h, const double *theta, const double *delta, double t, double *l2) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!theta || !l2) return MNL_ERR_INVALID_ARG;
+  if (h->gb1) return MNL_ERR_UNSUPPORTED;
+  if ((rc = set_device(h))) return rc;
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->st));
+  if (delta) {
+    h->h_scal[8] = t;
+    CK(cudaMemcpyAsync(h->tscale, h->h_scal + 8, sizeof(double), cudaMemcpyHostToDevice, h->st));
+  }
+  if ((rc = run_pass(h, theta, false, delta, kLt))) return rc;
+  CK(cudaMemcpyAsync(l2, h->scal + kLt, 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemcpyAsync(h->h_flags + 1, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return h->h_flags[1] ? MNL_ERR_TIMEOUT : MNL_OK;
+}
+
+double mnl_loglik_roundoff(const mnl_handle *h) {
+  return h ? (h->fp64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24)) : 0.0;
 }
 
 int mnl_set_weights(mnl_handle *h, const float *w) {

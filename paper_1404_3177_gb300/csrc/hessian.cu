@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(256) grouped_build_kernel(const GroupProblem *
   const GroupItem it = items[blockIdx.x];
   if (active[it.problem] == 0) return;
   const GroupProblem &g = probs[it.problem];
-  BuildDims D;
+  BuildDims D{};
   D.N = g.N; D.ldn = g.ldn; D.K = g.K; D.p = g.p; D.d = g.d; D.q = g.p + g.d;
   D.ob = g.build_ob; D.kc = g.build_kc;
   D.rpA = g.mc_pad; D.rpZ = 0;
@@ -836,7 +836,7 @@ __global__ void __launch_bounds__(kZThreads) grouped_zblocks_kernel(const GroupP
   const GroupItem it = items[blockIdx.x];
   if (active[it.problem] == 0) return;
   const GroupProblem &g = probs[it.problem];
-  ZDims D;
+  ZDims D{};
   D.N = g.N; D.K = g.K; D.p = g.p; D.d = g.d; D.f = g.f;
   D.nsplit = g.zsplit;
   D.nzt = (int64_t)g.p * g.K * g.f + (int64_t)g.K * g.d * g.f + (int64_t)g.f * g.f;
@@ -1028,7 +1028,7 @@ void build_blocking(const Shape &s, OpType t, int *ob, int *kc, bool with_z) {
 cudaError_t launch_build_operands(const Shape &s, OpType t, const float *X, const float *Y, const void *P, void *At,
                                   void *Ad, int64_t ldn, cudaStream_t st, const float *Z, const void *zbar, void *Az,
                                   const float *w) {
-  BuildDims D;
+  BuildDims D{};
   D.w = w;
   D.N = s.N; D.ldn = ldn; D.K = s.K; D.p = s.p; D.d = s.d; D.q = s.q;
   D.rpA = (s.mc + kTile - 1) / kTile * kTile;
@@ -1180,7 +1180,7 @@ int f64_chunk_rows() { return kKc; }
 
 cudaError_t launch_zblocks(const Shape &s, bool fp64, const float *X, const float *Y, const float *Z, const void *P,
                            const void *zbar, int nsplit, void *out, cudaStream_t st, const float *w) {
-  ZDims D;
+  ZDims D{};
   D.N = s.N; D.K = s.K; D.p = s.p; D.d = s.d; D.f = s.f;
   D.w = w;
   D.nsplit = nsplit;
@@ -1271,6 +1271,42 @@ __global__ void export_probs_kernel(int64_t count, const void *__restrict__ P, i
     out[e] = fp64 ? reinterpret_cast<const double *>(P)[e] : (double)reinterpret_cast<const float *>(P)[e];
 }
 }  // namespace
+
+namespace {
+// Packed lower triangle, column by column: entry (r, c), r >= c, at c n - c (c - 1) / 2 + (r - c).
+__device__ __forceinline__ int64_t packed_index(int64_t n, int64_t r, int64_t c) { return c * n - c * (c - 1) / 2 + (r - c); }
+
+__global__ void pack_lower_kernel(int64_t n, const double *__restrict__ F, double *__restrict__ out) {
+  const int64_t c = blockIdx.y + (int64_t)gridDim.y * blockIdx.z;
+  if (c >= n) return;
+  for (int64_t r = c + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+    out[packed_index(n, r, c)] = F[c * n + r];
+}
+
+__global__ void unpack_lower_kernel(int64_t n, const double *__restrict__ in, double *__restrict__ F) {
+  const int64_t c = blockIdx.y + (int64_t)gridDim.y * blockIdx.z;
+  if (c >= n) return;
+  for (int64_t r = c + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    const double v = in[packed_index(n, r, c)];
+    F[c * n + r] = v;
+    F[r * n + c] = v;
+  }
+}
+}  // namespace
+
+cudaError_t launch_pack_lower(int64_t n, const double *F, double *out, cudaStream_t st) {
+  const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 32)),
+                  (unsigned)std::min<int64_t>(n, 65535), (unsigned)((n + 65534) / 65535));
+  pack_lower_kernel<<<grid, 256, 0, st>>>(n, F, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_lower(int64_t n, const double *in, double *F, cudaStream_t st) {
+  const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 32)),
+                  (unsigned)std::min<int64_t>(n, 65535), (unsigned)((n + 65534) / 65535));
+  unpack_lower_kernel<<<grid, 256, 0, st>>>(n, in, F);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_export_probs(int64_t count, const void *P, bool fp64, double *out, cudaStream_t st) {
   const int64_t blocks = std::min<int64_t>((count + 255) / 256, 4096);

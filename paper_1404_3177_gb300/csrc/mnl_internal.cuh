@@ -395,6 +395,12 @@ cudaError_t launch_perm_to_user(int64_t n, const int64_t *perm, const double *in
 // H[u][v] = -F[perm[u]][perm[v]] (column-major, both triangles of F present).
 cudaError_t launch_export_hessian_perm(int64_t n, const double *F, const int64_t *perm, double *H, cudaStream_t st);
 
+// Observation sharding: -H's lower triangle packed column by column
+// (n (n + 1) / 2 doubles) and back into both triangles of F.
+cudaError_t launch_pack_lower(int64_t n, const double *F, double *out, cudaStream_t st);
+cudaError_t launch_unpack_lower(int64_t n, const double *in, double *F, cudaStream_t st);
+cudaError_t launch_f64_to_f32_lower(int64_t n, const double *F, float *F32, cudaStream_t st);
+
 // Small FP64 vector kernels.
 cudaError_t launch_axpy_theta(int64_t n, double *theta, const double *delta, const double *tscale, double *scal_out,
                               cudaStream_t st);

@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(512) grouped_pass_kernel(const GroupProblem *_
     D.nout = D.mc + (int64_t)gp.K * gp.f;
     D.rows = rows;
     D.ntiles = (gp.N + rows - 1) / rows;
-    PassIO io;
+    PassIO io{};
     io.X = gp.X; io.Y = gp.Y; io.Z = gp.Z; io.choice = gp.choice;
     io.theta = gp.theta;
     io.delta = FULL ? nullptr : gp.delta;

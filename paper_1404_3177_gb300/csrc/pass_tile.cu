@@ -675,7 +675,7 @@ cudaError_t launch_cs(const TileDims &D, int grid, size_t smem, const PassIO &io
 }  // namespace
 
 bool plan_pass_tiled(const Shape &s, bool full, int num_sms, PassPlan &pl) {
-  TileDims D;
+  TileDims D{};
   size_t smem = 0;
   for (int rpw : {2}) {
     if (!make_tile_dims(s, full, rpw, D, smem)) continue;
@@ -693,7 +693,7 @@ bool plan_pass_tiled(const Shape &s, bool full, int num_sms, PassPlan &pl) {
 }
 
 cudaError_t launch_pass_tiled(const Shape &s, const PassPlan &pl, bool full, const PassIO &io, cudaStream_t st) {
-  TileDims D;
+  TileDims D{};
   size_t smem = 0;
   if (!make_tile_dims(s, full, pl.rows / 8, D, smem) || smem != pl.smem || io.err == nullptr) return cudaErrorInvalidValue;
   const bool aligned = ((reinterpret_cast<uintptr_t>(io.X) | reinterpret_cast<uintptr_t>(io.choice) |

@@ -1089,7 +1089,7 @@ cudaError_t launch_coop(int64_t n, T *A, T *Li, T *Dinv, T *dinv, GridBarrier *b
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int grid = std::min(nsm * std::min(per_sm, 2), kMaxCoopGrid);
   if ((e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st)) != cudaSuccess) return e;
-  CoopArgs<T> a;
+  CoopArgs<T> a{};
   a.A = A; a.Li = Li; a.Dinv = Dinv; a.dinv = dinv; a.n = n; a.bar = bar;
   a.status = status; a.bad_bit = bad_bit; a.err = err;
   a.wait_ns = wait_ns ? wait_ns : kWaitNs;
@@ -1160,6 +1160,12 @@ cudaError_t launch_std_errors(int64_t n, double *F, double *Binv, double *dinv, 
   if ((e = launch_coop<double, true>(n, F, Binv, Dinv, dinv, bar, status, 4, err, st, wait_ns)) != cudaSuccess)
     return e;
   column_norms_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(n, Binv, status, se);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f64_to_f32_lower(int64_t n, const double *F, float *F32, cudaStream_t st) {
+  dim3 grid((unsigned)((n + 255) / 256), (unsigned)std::min<int64_t>(n, 65535), (unsigned)((n + 65534) / 65535));
+  f64_to_f32_lower_kernel<<<grid, 256, 0, st>>>(n, F, F32);
   return cudaGetLastError();
 }
 

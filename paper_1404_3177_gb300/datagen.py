@@ -155,6 +155,16 @@ def config3(N: int = 500_000) -> Problem:
                         sparse_cols=(70, 100), name=f"c3_N{N}_K100_p100_d0_f10")
 
 
+def config3_shard(rank: int, N: int = 500_000) -> Problem:
+    """Rank `rank`'s observations of the observation-sharded workload: the config-3 shape and true coefficients,
+    rank 0's rows are config3() itself and every other rank draws its own rows (seed offset by the rank)."""
+    if rank == 0:
+        return config3(N)
+    theta = make_problem(0, 100, 100, 0, 10, SEED_BASE + 3, intercept=False, theta_sd=0.2 / math.sqrt(100)).theta_true
+    return make_problem(N, 100, 100, 0, 10, SEED_BASE + 3 + 7919 * rank, intercept=False, sparse_cols=(70, 100),
+                        theta_true=theta, name=f"c3_shard{rank}_N{N}_K100_p100_d0_f10")
+
+
 def config4_shapes(count: int = 2048, seed: int = SEED_BASE + 4) -> list[tuple[int, int, int, int]]:
     """(N, K, p, f) of the batched workload: N log-uniform in [500, 50000], K in 3..30, p in 2..40, f in 0..4, d=0."""
     rng = np.random.Generator(np.random.Philox(np.random.SeedSequence([seed, 1 << 20])))

@@ -281,8 +281,11 @@ def test_unsupported_requests(MNL):
     with pytest.raises(nat.MnlError) as e:
         nat.mnl_create(nat.mnl_dims(10, 300, 2, 0, 0, 0), None, nat.MNL_BF16, 0)
     assert e.value.status == nat.MNL_ERR_UNSUPPORTED
-    with pytest.raises(nat.MnlError) as e:
-        nat.mnl_create(nat.mnl_dims(10, 4, 2, 1, 0, 1), None, nat.MNL_BF16, 0)
+    with pytest.raises(nat.MnlError) as e:  # gamma_base = 1 needs Y columns (a gamma_0 to estimate)
+        nat.mnl_create(nat.mnl_dims(10, 4, 2, 0, 1, 1), None, nat.MNL_BF16, 0)
+    assert e.value.status == nat.MNL_ERR_INVALID_ARG
+    with pytest.raises(nat.MnlError) as e:  # the batched calls keep gamma_0 = 0
+        nat.mnl_batch_create([nat.mnl_dims(10, 4, 2, 1, 0, 1)], [nat.mnl_data(16, 16, None, 16)], nat.MNL_BF16, 0)
     assert e.value.status == nat.MNL_ERR_UNSUPPORTED
 
 

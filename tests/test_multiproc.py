@@ -1,9 +1,10 @@
 """The multi-process host path of bench.py on CPU (gloo, world size 2).
 
-Every GPU runs an independent replica of the workload, so the only exchange
-between ranks is the bench's own bookkeeping: the barrier around the timed
-region, the maximum of the per-rank times, and one JSON line printed by rank 0.
-These tests run that logic as two gloo ranks on 127.0.0.1, without a GPU.
+The bench's own bookkeeping between ranks: the barrier around the timed
+region, the maximum of the per-rank times, and one JSON line printed by rank 0
+(the data exchange of the sharded fit is tested in test_sharded_cpu.py and, on
+a GPU, in test_gpu_sharded.py).  These tests run that logic as two gloo ranks
+on 127.0.0.1, without a GPU.
 """
 import json
 import os
