@@ -125,6 +125,7 @@ typedef struct mnl_step_info {
   int32_t fallback;    /* 1 when a mixed solve fell back to float64          */
   int32_t factor_kind; /* factorisation of the (first) solve: MNL_FACTOR_*   */
   int32_t wait_errors; /* after MNL_ERR_TIMEOUT: MNL_WAIT_* bits of the kernels whose waits gave up */
+  int32_t cg_iters;    /* truncated Newton (MNL_CREATE_TRUNCATED): conjugate-gradient iterations */
 } mnl_step_info;
 
 /* mnl_step_info.wait_errors: which kernels' bounded device waits gave up
@@ -180,6 +181,18 @@ MNL_API const char *mnl_status_string(int status);
 /* Device bytes mnl_create would allocate for these dims and precision (0 on error). */
 MNL_API size_t mnl_workspace_bytes(const mnl_dims *dims, int precision);
 
+/* mnl_create_ex flags.  MNL_CREATE_TRUNCATED: a Hessian-free handle for
+ * problems whose n_theta^2 Hessian does not fit (the paper's closing
+ * discussion of inexact Newton for larger problems): every Newton step solves
+ * (-H) delta = g approximately by conjugate gradients whose products -H v come
+ * from a pass over the data (mnl_hessian_vec), stopped at a relative residual
+ * eta = min(0.1, ||g||^(1/2)) (tending to 0 with g, so convergence stays fast
+ * near the optimum), then the step halving of mnl_newton_step.  The handle
+ * holds the data pass's buffers and a few n_theta vectors, no Hessian,
+ * operand or factor workspaces; mnl_hessian, mnl_std_errors, mnl_shard_* and
+ * mnl_set_solve (other than AUTO) return MNL_ERR_UNSUPPORTED on it. */
+enum { MNL_CREATE_TRUNCATED = 1 };
+
 /* Create a handle for one problem.
  *   dims      sizes (copied).
  *   data      DEVICE pointers to the caller's arrays, which must stay valid
@@ -194,6 +207,19 @@ MNL_API size_t mnl_workspace_bytes(const mnl_dims *dims, int precision);
  * MNL_ERR_INVALID_ARG, a NaN/Inf in X, Y or Z returns MNL_ERR_NONFINITE.
  * Synchronises the stream. */
 MNL_API int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *stream, mnl_handle **out);
+/* mnl_create with flags (0 or MNL_CREATE_TRUNCATED). */
+MNL_API int mnl_create_ex(const mnl_dims *dims, const mnl_data *data, int precision, int flags, void *stream,
+                          mnl_handle **out);
+
+/* Hessian-vector product at theta (paper sign: H v, H negative definite),
+ * without forming H: with u_ik = j_ik . v (j_ik the derivative of alternative
+ * k's utility with respect to theta) and P the probabilities at theta,
+ * -H v = sum_i sum_k P_ik (u_ik - sum_m P_im u_im) j_ik (App. A's Hessian
+ * applied to v), one pass over the data.  theta, v, Hv: DEVICE [n_theta]
+ * float64.  Synchronises.  Any handle. */
+MNL_API int mnl_hessian_vec(mnl_handle *h, const double *theta, const double *v, double *Hv);
+/* Conjugate-gradient iterations per truncated Newton step at most (default 500). */
+MNL_API int mnl_set_cg_max(mnl_handle *h, int32_t iters);
 
 /* Copy HOST arrays into the handle's own device buffers (handles created with
  * data = NULL only; otherwise MNL_ERR_INVALID_ARG), then validate them as

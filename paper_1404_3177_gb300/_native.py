@@ -34,7 +34,7 @@ EXPORTS = (
     "mnl_num_params", "mnl_status_string", "mnl_workspace_bytes", "mnl_fit_opts_default", "mnl_create",
     "mnl_upload", "mnl_loglik_grad", "mnl_hessian", "mnl_newton_step", "mnl_fit", "mnl_destroy",
     "mnl_loglik_grad_noalloc", "mnl_set_solve", "mnl_set_wait_bound", "mnl_set_weights",
-    "mnl_shard_sums_size", "mnl_shard_grad_hess", "mnl_shard_solve", "mnl_shard_loglik", "mnl_loglik_roundoff", "mnl_std_errors", "mnl_predict", "mnl_batch_create", "mnl_batch_num_params", "mnl_batch_fit",
+    "mnl_create_ex", "mnl_hessian_vec", "mnl_set_cg_max", "mnl_shard_sums_size", "mnl_shard_grad_hess", "mnl_shard_solve", "mnl_shard_loglik", "mnl_loglik_roundoff", "mnl_std_errors", "mnl_predict", "mnl_batch_create", "mnl_batch_num_params", "mnl_batch_fit",
     "mnl_batch_destroy", "mnl_server_opts_default", "mnl_server_create", "mnl_server_submit", "mnl_server_step",
     "mnl_server_poll", "mnl_server_finished", "mnl_server_memory_in_use", "mnl_server_destroy",
 )
@@ -63,7 +63,8 @@ class mnl_step_info(C.Structure):
                 ("t_band_ms", C.c_float), ("t_zblk_ms", C.c_float), ("t_asm_ms", C.c_float),
                 ("t_factor_ms", C.c_float), ("t_solve_ms", C.c_float), ("t_fallback_ms", C.c_float),
                 ("launches", C.c_int32), ("solve_mode", C.c_int32), ("refine_steps", C.c_int32),
-                ("fallback", C.c_int32), ("factor_kind", C.c_int32), ("wait_errors", C.c_int32)]
+                ("fallback", C.c_int32), ("factor_kind", C.c_int32), ("wait_errors", C.c_int32),
+                ("cg_iters", C.c_int32)]
 
 
 class mnl_fit_opts(C.Structure):
@@ -148,6 +149,12 @@ def load() -> C.CDLL:
         lib.mnl_std_errors.argtypes = [vp, vp, vp]
         lib.mnl_predict.restype = i32
         lib.mnl_predict.argtypes = [vp, vp, vp, C.POINTER(C.c_double)]
+        lib.mnl_create_ex.restype = i32
+        lib.mnl_create_ex.argtypes = [C.POINTER(mnl_dims), C.POINTER(mnl_data), i32, i32, vp, C.POINTER(vp)]
+        lib.mnl_hessian_vec.restype = i32
+        lib.mnl_hessian_vec.argtypes = [vp, vp, vp, vp]
+        lib.mnl_set_cg_max.restype = i32
+        lib.mnl_set_cg_max.argtypes = [vp, C.c_int32]
         lib.mnl_shard_sums_size.restype = i64
         lib.mnl_shard_sums_size.argtypes = [C.POINTER(mnl_dims)]
         lib.mnl_shard_grad_hess.restype = i32
@@ -285,6 +292,25 @@ def mnl_predict(handle: int, theta_ptr: int, P_ptr: int, want_loglik: bool = Tru
     _check(load().mnl_predict(C.c_void_p(handle), C.c_void_p(theta_ptr), C.c_void_p(P_ptr),
                               C.byref(l) if want_loglik else None), "mnl_predict")
     return l.value if want_loglik else None
+
+
+MNL_CREATE_TRUNCATED = 1
+
+
+def mnl_create_ex(dims: mnl_dims, data: mnl_data | None, precision: int, flags: int, stream: int | None) -> int:
+    h = C.c_void_p()
+    _check(load().mnl_create_ex(C.byref(dims), C.byref(data) if data is not None else None, precision, flags,
+                                C.c_void_p(stream or 0), C.byref(h)), "mnl_create_ex")
+    return h.value
+
+
+def mnl_hessian_vec(handle: int, theta_ptr: int, v_ptr: int, Hv_ptr: int) -> None:
+    _check(load().mnl_hessian_vec(C.c_void_p(handle), C.c_void_p(theta_ptr), C.c_void_p(v_ptr), C.c_void_p(Hv_ptr)),
+           "mnl_hessian_vec")
+
+
+def mnl_set_cg_max(handle: int, iters: int) -> None:
+    _check(load().mnl_set_cg_max(C.c_void_p(handle), int(iters)), "mnl_set_cg_max")
 
 
 def mnl_shard_sums_size(dims: mnl_dims) -> int:

@@ -20,7 +20,7 @@ class MNL:
     """
 
     def __init__(self, X=None, Y=None, Z=None, choice=None, *, K=None, precision="bf16", stream=None,
-                 host_owned_dims=None, solve="auto", gamma_base=0, weights=None):
+                 host_owned_dims=None, solve="auto", gamma_base=0, weights=None, truncated=False):
         self.precision = nat.PRECISIONS[precision]
         self._stream = (stream or torch.cuda.current_stream()).cuda_stream
         if host_owned_dims is not None:
@@ -48,7 +48,8 @@ class MNL:
         self._keep = (X, Y, Z, choice)
         self.dims = nat.mnl_dims(N, K, p, d, f, gamma_base)
         data = nat.mnl_data(_ptr(X), _ptr(Y), _ptr(Z), _ptr(choice))
-        self.h = nat.mnl_create(self.dims, data, self.precision, self._stream)
+        self.h = nat.mnl_create_ex(self.dims, data, self.precision, nat.MNL_CREATE_TRUNCATED if truncated else 0,
+                                   self._stream)
         nat.mnl_set_solve(self.h, nat.SOLVES[solve])
         if weights is not None:
             self.set_weights(weights)
@@ -94,6 +95,14 @@ class MNL:
         H = torch.empty(self.n_theta, self.n_theta, dtype=torch.float64, device=th.device)
         nat.mnl_hessian(self.h, th.data_ptr(), H.data_ptr())
         return H
+
+    def hessian_vec(self, theta, v):
+        """H v at theta (paper sign), float64 [n_theta] (CUDA), without forming H."""
+        th = self._theta(theta)
+        vv = self._theta(v)
+        out = torch.empty(self.n_theta, dtype=torch.float64, device=th.device)
+        nat.mnl_hessian_vec(self.h, th.data_ptr(), vv.data_ptr(), out.data_ptr())
+        return out
 
     def std_errors(self, theta):
         """Standard errors sqrt(diag((-H)^-1)) at theta, float64 [n_theta] (CUDA)."""

@@ -71,6 +71,11 @@ struct mnl_handle {
   double *Binv;         // inverse of the float64 factor (standard errors; allocated at the first call)
   TcCholPlan tcp;
   uint64_t wait_ns;     // bound of the kernels' device waits (0: their defaults)
+  // Hessian-free handle (truncated Newton): no Hessian, factor or solve workspaces
+  bool hfree;
+  int cg_max;           // conjugate-gradient iterations per Newton step at most
+  double *cg;           // [3 n]: CG residual, direction, product (also scratch of mnl_hessian_vec)
+  float *wbuf;          // [N][K] Hessian-vector residuals for the separate beta kernel (wide shapes)
   // host mirrors (pinned)
   double *h_scal;
   int *h_flags;
@@ -160,7 +165,8 @@ int simt_split(int ntiles, int64_t nchunks, int nsm) {
 }
 
 Sizes plan_sizes(const mnl_dims &d, int prec_in, bool owned, int nsm, int *main_split, int *band_split, int *z_split,
-                 PassPlan *pf, PassPlan *pl, int64_t *ldn, int64_t *mc_pad, int *nt1d, int *nband, int *zt_split) {
+                 PassPlan *pf, PassPlan *pl, int64_t *ldn, int64_t *mc_pad, int *nt1d, int *nband, int *zt_split,
+                 bool hfree = false) {
   const Shape S = make_shape(d);
   const int prec = (prec_in == MNL_BF16 && d.N < kBf16MinRows) ? MNL_TF32 : prec_in;
   const bool fp64 = prec == MNL_FP64;
@@ -220,6 +226,11 @@ Sizes plan_sizes(const mnl_dims &d, int prec_in, bool owned, int nsm, int *main_
   z.solve = (size_t)S.n * 8 + (size_t)S.n * S.n * 4 + mixed_solve_bytes(S.n) + chol_work_bytes(S.n) +
             (S.n >= tc_chol_min_n() ? tc_chol_bytes(S.n) : 0);
   z.owned = owned ? ((size_t)S.N * S.p + (size_t)S.N * S.K * (S.d + S.f)) * 4 + (size_t)S.N * 4 : 0;
+  if (hfree)  // truncated Newton: no Hessian operands, partials, F or factor workspaces; CG vectors instead
+  {
+    z.ops = z.main_part = z.band_part = z.z_part = z.zop = z.zt_part = z.F = 0;
+    z.solve = (size_t)3 * S.n * 8;
+  }
   return z;
 }
 
@@ -551,6 +562,128 @@ const double *theta_in(mnl_handle *h, const double *theta, int *rc) {
   return h->th_int;
 }
 
+// F v = -H v at the theta of the last full pass (whose P it reuses), into out:
+// the pass with v as its coefficients and the residuals P_ik (u_ik - ubar_i).
+int hv_pass(mnl_handle *h, const double *v, double *out) {
+  PassIO io{};
+  io.X = h->X; io.Y = h->Y; io.Z = h->Z; io.choice = h->choice;
+  io.theta = v;
+  io.P = h->P; io.zbar = h->zbar;
+  io.partials = h->part_full;
+  io.err = h->err;
+  io.wait_ns = h->wait_ns;
+  io.w = h->w;
+  io.Pin = h->P;
+  io.Wout = h->wbuf;
+  CK(launch_pass(h->S, h->pfull, h->fp64, true, io, h->st));
+  CK(launch_pass_reduce(h->S, h->pfull.grid, true, io.partials, h->scal + 10, out, h->st));
+  h->launches += 2;
+  return MNL_OK;
+}
+
+// Truncated (inexact) Newton iteration (Sec. 3.1 eq. "NR update" with the
+// Newton system solved only approximately): conjugate gradients on
+// F delta = g with products F v from hv_pass (no Hessian is formed or stored),
+// stopped when ||r|| <= eta ||g||, eta = min(0.1, sqrt(||g||)) (a forcing
+// sequence that tends to 0 as g does, so convergence stays superlinear), then
+// the same step halving as the exact step.
+int step_truncated(mnl_handle *h, double *theta, mnl_step_info *info, double gtol, bool *converged,
+                   int max_halvings) {
+  const int64_t n = h->S.n;
+  mnl_step_info loc{};
+  if (converged) *converged = false;
+  h->launches = 0;
+  double *r = h->cg, *pv = h->cg + n, *ap = h->cg + 2 * n;
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->st));
+  CK(cudaMemsetAsync(h->scal, 0, kNscal * sizeof(double), h->st));
+  CK(cudaEventRecord(h->ev[0], h->st));
+  int rc = run_pass(h, theta, true, nullptr, kL);
+  if (rc) return rc;
+  CK(launch_vec_absmax(n, h->grad, h->scal + kGinf, h->st));
+  CK(launch_dot(n, h->grad, h->grad, h->scal + 3, h->st));
+  CK(cudaEventRecord(h->ev[1], h->st));
+  CK(cudaMemcpyAsync(h->h_scal, h->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(h->h_flags + 1, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (h->h_flags[1]) { loc.wait_errors = h->h_flags[1]; if (info) *info = loc; return MNL_ERR_TIMEOUT; }
+  const double l0 = h->h_scal[kL], labs = h->h_scal[kLabs], ginf = h->h_scal[kGinf], gg = h->h_scal[3];
+  if (!std::isfinite(l0) || !std::isfinite(ginf)) return MNL_ERR_NONFINITE;
+  loc.loglik_old = loc.loglik_new = l0;
+  loc.grad_inf = ginf;
+  loc.factor_kind = MNL_FACTOR_NONE;
+  if (gtol > 0 && ginf < gtol) {
+    if (converged) *converged = true;
+    if (info) *info = loc;
+    return MNL_OK;
+  }
+  // conjugate gradients, delta_0 = 0
+  const double eta = std::min(0.1, std::sqrt(std::sqrt(gg)));
+  const double target = eta * eta * gg;
+  CK(cudaMemsetAsync(h->delta, 0, (size_t)n * 8, h->st));
+  CK(cudaMemcpyAsync(r, h->grad, (size_t)n * 8, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemcpyAsync(pv, h->grad, (size_t)n * 8, cudaMemcpyDeviceToDevice, h->st));
+  double rs = gg;
+  int it = 0;
+  for (; it < h->cg_max && rs > target; ++it) {
+    if ((rc = hv_pass(h, pv, ap))) return rc;
+    CK(launch_dot(n, pv, ap, h->scal + 13, h->st));
+    CK(cudaMemcpyAsync(h->h_scal + 13, h->scal + 13, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    const double pap = h->h_scal[13];
+    if (!(pap > 0.0) || !std::isfinite(pap)) {
+      if (it == 0) return MNL_ERR_NOT_PD;  // a direction of zero or negative curvature: -H is singular
+      break;
+    }
+    const double alpha = rs / pap;
+    CK(launch_axpby(n, alpha, pv, 1.0, h->delta, h->st));
+    CK(launch_axpby(n, -alpha, ap, 1.0, r, h->st));
+    CK(launch_dot(n, r, r, h->scal + 14, h->st));
+    CK(cudaMemcpyAsync(h->h_scal + 14, h->scal + 14, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    const double rs_new = h->h_scal[14];
+    CK(launch_axpby(n, 1.0, r, rs_new / rs, pv, h->st));
+    rs = rs_new;
+    h->launches += 6;
+  }
+  CK(cudaEventRecord(h->ev[3], h->st));
+  loc.cg_iters = it;
+  // step halving (Sec. 3.1)
+  const double tau = noise_tol(h, labs);
+  double t = 1.0, lt = 0.0;
+  int j = 0;
+  bool accepted = false;
+  for (j = 0; j <= max_halvings; ++j) {
+    h->h_scal[8] = t;
+    CK(cudaMemcpyAsync(h->tscale, h->h_scal + 8, sizeof(double), cudaMemcpyHostToDevice, h->st));
+    if ((rc = run_pass(h, theta, false, h->delta, kLt))) return rc;
+    CK(cudaMemcpyAsync(h->h_scal + kLt, h->scal + kLt, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(h->h_flags + 1, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (h->h_flags[1]) { loc.wait_errors = h->h_flags[1]; if (info) *info = loc; return MNL_ERR_TIMEOUT; }
+    lt = h->h_scal[kLt];
+    if (std::isfinite(lt) && lt >= l0 - tau) { accepted = true; break; }
+    t *= 0.5;
+  }
+  CK(cudaEventRecord(h->ev[4], h->st));
+  if (!accepted) return MNL_ERR_LINESEARCH;
+  CK(launch_axpy_theta(n, theta, h->delta, h->tscale, h->scal + kStepInf, h->st));
+  CK(cudaMemcpyAsync(h->h_scal + kStepInf, h->scal + kStepInf, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  loc.loglik_new = lt;
+  loc.step_inf = h->h_scal[kStepInf];
+  loc.theta_inf = h->h_scal[kThetaInf];
+  loc.step_scale = t;
+  loc.ls_noise = tau;
+  loc.halvings = j;
+  loc.ls_evals = j + 1;
+  loc.t_pass_ms = elapsed(h->ev[0], h->ev[1]);
+  loc.t_chol_ms = loc.t_solve_ms = elapsed(h->ev[1], h->ev[3]);
+  loc.t_ls_ms = elapsed(h->ev[3], h->ev[4]);
+  loc.launches = h->launches;
+  if (info) *info = loc;
+  return MNL_OK;
+}
+
 // (-H) delta = g from h->F (both triangles) and h->grad, synchronously, with the
 // handle's solve mode: refinement continued while it converges, the float64
 // factorisation when a mixed solve fails.  The sharded Newton step's solve.
@@ -596,6 +729,11 @@ int solve_system(mnl_handle *h, mnl_step_info &loc) {
   if (h->h_flags[1]) { loc.wait_errors = h->h_flags[1]; return MNL_ERR_TIMEOUT; }
   if (!mixed) loc.factor_kind = MNL_FACTOR_COOP;
   return (h->h_flags[0] & 4) ? MNL_ERR_NOT_PD : MNL_OK;
+}
+
+int step_any(mnl_handle *h, double *theta, mnl_step_info *info, double gtol, bool *converged, int max_halvings) {
+  return h->hfree ? step_truncated(h, theta, info, gtol, converged, max_halvings)
+                  : step_impl(h, theta, info, gtol, converged, max_halvings);
 }
 
 int check_handle(const mnl_handle *h) {
@@ -663,9 +801,15 @@ size_t mnl_workspace_bytes(const mnl_dims *d, int precision) {
 }
 
 int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *stream, mnl_handle **out) {
+  return mnl_create_ex(dims, data, precision, 0, stream, out);
+}
+
+int mnl_create_ex(const mnl_dims *dims, const mnl_data *data, int precision, int flags, void *stream,
+                  mnl_handle **out) {
   if (!out) return MNL_ERR_INVALID_ARG;
   *out = nullptr;
-  if (!dims_ok(dims) || precision < 0 || precision > 2) return MNL_ERR_INVALID_ARG;
+  if (!dims_ok(dims) || precision < 0 || precision > 2 || (flags & ~MNL_CREATE_TRUNCATED)) return MNL_ERR_INVALID_ARG;
+  const bool hfree = (flags & MNL_CREATE_TRUNCATED) != 0;
   if (dims->gamma_base == 1 && dims->d == 0) return MNL_ERR_INVALID_ARG;  // no gamma_0 to estimate
   // gamma_base = 1 is solved as gamma_base = 0 with the d columns of Y's base rows as generic columns
   mnl_dims di = *dims;
@@ -684,6 +828,8 @@ int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *
   // Too few observations for unbiased BF16 rounding to average out: TF32 operands.
   if (h->op == OpType::BF16 && dims->N < kBf16MinRows) h->op = OpType::TF32;
   h->fp64 = precision == MNL_FP64;
+  h->hfree = hfree;
+  h->cg_max = 500;
   h->st = reinterpret_cast<cudaStream_t>(stream);
   int rc = MNL_OK;
   auto fail = [&](int code) {
@@ -695,7 +841,7 @@ int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *
   cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev);
   int nband = 0;
   Sizes z = plan_sizes(di, precision, data == nullptr, h->nsm, &h->main_split, &h->band_split, &h->z_split,
-                       &h->pfull, &h->pll, &h->ldn, &h->mc_pad, &h->nt1d, &nband, &h->zt_split);
+                       &h->pfull, &h->pll, &h->ldn, &h->mc_pad, &h->nt1d, &nband, &h->zt_split, hfree);
   if (!h->pfull.ok || !h->pll.ok) return fail(MNL_ERR_UNSUPPORTED);
 
   for (auto &e : h->ev)
@@ -714,12 +860,16 @@ int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *
       (rc = dalloc(h, &h->status, 16)) || (rc = dalloc(h, &h->err, 16)) || (rc = dalloc(h, &h->At, z.ops)) ||
       (rc = dalloc(h, &h->Ad, z.ops)) || (rc = dalloc(h, &h->main_part, z.main_part)) ||
       (rc = dalloc(h, &h->band_part, z.band_part)) || (rc = dalloc(h, &h->z_part, z.z_part)) ||
-      (rc = dalloc(h, &h->F, z.F)) || (rc = dalloc(h, &h->dinv, S.n * 8)) ||
-      (rc = dalloc(h, &h->F32, (size_t)S.n * S.n * 4)) || (rc = dalloc(h, &h->mwork, mixed_solve_bytes(S.n))) ||
-      (rc = dalloc(h, &h->cwork, chol_work_bytes(S.n))))
+      (rc = dalloc(h, &h->F, z.F)) || (rc = dalloc(h, &h->dinv, hfree ? 0 : S.n * 8)) ||
+      (rc = dalloc(h, &h->F32, hfree ? 0 : (size_t)S.n * S.n * 4)) ||
+      (rc = dalloc(h, &h->mwork, hfree ? 0 : mixed_solve_bytes(S.n))) ||
+      (rc = dalloc(h, &h->cwork, hfree ? 0 : chol_work_bytes(S.n))) || (rc = dalloc(h, &h->cg, (size_t)3 * S.n * 8)))
     return fail(rc);
-  h->ref = mixed_solve_ref(h->mwork, S.n);
-  if (S.n >= tc_chol_min_n()) {
+  // Hessian-vector residuals for the separate beta kernel of the wide tiled pass
+  if (!h->fp64 && h->pfull.tiled && plan_pass_beta_ext(S) && (rc = dalloc(h, &h->wbuf, (size_t)S.N * S.K * 4)))
+    return fail(rc);
+  h->ref = hfree ? nullptr : mixed_solve_ref(h->mwork, S.n);
+  if (!hfree && S.n >= tc_chol_min_n()) {
     if ((rc = dalloc(h, &h->tcwork, tc_chol_bytes(S.n)))) return fail(rc);
     const cudaError_t e = tc_chol_prepare(S.n, h->tcwork, h->nsm, &h->tcp);
     if (e != cudaSuccess) { cudaGetLastError(); return fail(cuda_fail(e)); }
@@ -753,8 +903,8 @@ int mnl_create(const mnl_dims *dims, const mnl_data *data, int precision, void *
     cudaGetLastError();
     return fail(MNL_ERR_CUDA);
   }
-  h->tcz = !h->fp64 && S.f > 0;
-  if (!h->fp64 && (S.mc > 0 || h->tcz)) {
+  h->tcz = !h->fp64 && S.f > 0 && !hfree;
+  if (!h->fp64 && !hfree && (S.mc > 0 || h->tcz)) {
     CUtensorMap hm[3];
     std::memset(hm, 0, sizeof(hm));
     cudaError_t e = cudaSuccess;
@@ -952,6 +1102,7 @@ int mnl_hessian(mnl_handle *h, const double *theta, double *H) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (!theta || !H) return MNL_ERR_INVALID_ARG;
+  if (h->hfree) return MNL_ERR_UNSUPPORTED;
   if ((rc = set_device(h))) return rc;
   CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->st));
   const double *th = theta_in(h, theta, &rc);
@@ -968,10 +1119,10 @@ int mnl_newton_step(mnl_handle *h, double *theta, mnl_step_info *info) {
   if (rc) return rc;
   if (!theta) return MNL_ERR_INVALID_ARG;
   if ((rc = set_device(h))) return rc;
-  if (!h->gb1) return step_impl(h, theta, info, 0.0, nullptr, 30);
+  if (!h->gb1) return step_any(h, theta, info, 0.0, nullptr, 30);
   double *th = const_cast<double *>(theta_in(h, theta, &rc));
   if (rc) return rc;
-  rc = step_impl(h, th, info, 0.0, nullptr, 30);
+  rc = step_any(h, th, info, 0.0, nullptr, 30);
   if (rc == MNL_OK) CK(launch_perm_to_user(h->S.n, h->perm, th, theta, h->st));
   if (rc == MNL_OK) CK(cudaStreamSynchronize(h->st));
   return rc;
@@ -997,7 +1148,7 @@ int mnl_fit(mnl_handle *h, const mnl_fit_opts *opts, double *theta, mnl_fit_info
   for (int it = 0; it < o.maxiter; ++it) {
     mnl_step_info si{};
     bool conv = false;
-    int s = step_impl(h, theta, &si, o.gtol, &conv, o.max_halvings);
+    int s = step_any(h, theta, &si, o.gtol, &conv, o.max_halvings);
     fi.t_pass_ms += si.t_pass_ms;
     fi.t_hess_ms += si.t_hess_ms;
     fi.t_chol_ms += si.t_chol_ms;
@@ -1035,10 +1186,44 @@ int mnl_fit(mnl_handle *h, const mnl_fit_opts *opts, double *theta, mnl_fit_info
   return rc;
 }
 
+int mnl_hessian_vec(mnl_handle *h, const double *theta, const double *v, double *Hv) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!theta || !v || !Hv) return MNL_ERR_INVALID_ARG;
+  if ((rc = set_device(h))) return rc;
+  const int64_t n = h->S.n;
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->st));
+  const double *th = theta_in(h, theta, &rc);
+  if (rc) return rc;
+  if ((rc = run_pass(h, th, true, nullptr, kL))) return rc;  // P at theta
+  const double *vi = v;
+  if (h->gb1) {
+    CK(launch_perm_to_internal(n, h->perm, v, h->cg, h->st));
+    vi = h->cg;
+  }
+  if ((rc = hv_pass(h, vi, h->cg + n))) return rc;
+  if (h->gb1) {
+    CK(launch_axpby(n, -1.0, h->cg + n, 0.0, h->cg + 2 * n, h->st));  // H v = -(F v)
+    CK(launch_perm_to_user(n, h->perm, h->cg + 2 * n, Hv, h->st));
+  } else {
+    CK(launch_axpby(n, -1.0, h->cg + n, 0.0, Hv, h->st));
+  }
+  CK(cudaMemcpyAsync(h->h_flags + 1, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return h->h_flags[1] ? MNL_ERR_TIMEOUT : MNL_OK;
+}
+
+int mnl_set_cg_max(mnl_handle *h, int32_t iters) {
+  if (!h || iters < 1) return MNL_ERR_INVALID_ARG;
+  h->cg_max = iters;
+  return MNL_OK;
+}
+
 int mnl_std_errors(mnl_handle *h, const double *theta, double *se) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (!theta || !se) return MNL_ERR_INVALID_ARG;
+  if (h->hfree) return MNL_ERR_UNSUPPORTED;
   if ((rc = set_device(h))) return rc;
   const int64_t n = h->S.n;
   if (!h->Binv && (rc = dalloc(h, &h->Binv, (size_t)n * n * 8))) return rc;
@@ -1088,7 +1273,7 @@ int mnl_shard_grad_hess(mnl_handle *h, const double *theta, double *sums) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (!theta || !sums) return MNL_ERR_INVALID_ARG;
-  if (h->gb1) return MNL_ERR_UNSUPPORTED;
+  if (h->gb1 || h->hfree) return MNL_ERR_UNSUPPORTED;
   if ((rc = set_device(h))) return rc;
   const int64_t n = h->S.n;
   CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->st));
@@ -1106,7 +1291,7 @@ int mnl_shard_solve(mnl_handle *h, const double *sums, double *delta, mnl_step_i
   int rc = check_handle(h);
   if (rc) return rc;
   if (!sums || !delta) return MNL_ERR_INVALID_ARG;
-  if (h->gb1) return MNL_ERR_UNSUPPORTED;
+  if (h->gb1 || h->hfree) return MNL_ERR_UNSUPPORTED;
   if ((rc = set_device(h))) return rc;
   const int64_t n = h->S.n;
   mnl_step_info loc{};
@@ -1169,6 +1354,7 @@ int mnl_set_wait_bound(mnl_handle *h, uint64_t ns) {
 
 int mnl_set_solve(mnl_handle *h, int mode) {
   if (!h || mode < MNL_SOLVE_AUTO || mode > MNL_SOLVE_MIXED) return MNL_ERR_INVALID_ARG;
+  if (h->hfree) return mode == MNL_SOLVE_AUTO ? MNL_OK : MNL_ERR_UNSUPPORTED;
   h->solve_mode = mode == MNL_SOLVE_AUTO ? (h->fp64 ? MNL_SOLVE_FP64 : MNL_SOLVE_MIXED) : mode;
   return MNL_OK;
 }

@@ -488,6 +488,40 @@ cudaError_t launch_try_full_step(int64_t n, double *theta, const double *delta, 
   return cudaGetLastError();
 }
 
+namespace {
+// out[0] = a . b in a fixed order (one CTA: strided partial sums, then a tree over the threads).
+__global__ void __launch_bounds__(1024) dot_kernel(int64_t n, const double *__restrict__ a,
+                                                   const double *__restrict__ b, double *__restrict__ out) {
+  __shared__ double red[1024];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s = fma(a[i], b[i], s);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+
+// y = a x + b y
+__global__ void axpby_kernel(int64_t n, double a, const double *__restrict__ x, double b, double *__restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = b == 0.0 ? a * x[i] : fma(a, x[i], b * y[i]);  // b = 0: y's old value is not read
+}
+}  // namespace
+
+cudaError_t launch_dot(int64_t n, const double *a, const double *b, double *out, cudaStream_t st) {
+  dot_kernel<<<1, 1024, 0, st>>>(n, a, b, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(int64_t n, double a, const double *x, double b, double *y, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>(256, (n + 255) / 256);
+  axpby_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, st>>>(n, a, x, b, y);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_vec_absmax(int64_t n, const double *v, double *out, cudaStream_t st) {
   const int blocks = (int)std::min<int64_t>(64, (n + 255) / 256);
   vec_absmax_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, st>>>(n, v, out);

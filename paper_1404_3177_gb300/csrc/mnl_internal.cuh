@@ -91,6 +91,13 @@ struct PassIO {
   int *err;              // error word (bit 16: a tile copy did not complete in time); tiled pass only
   uint64_t wait_ns;      // bound of the tile-copy waits (0: the default, 2 s)
   const float *w;        // [N] observation weights, or nullptr (all ones)
+  // Hessian-vector mode (FULL pass only): theta holds v, Pin the probabilities
+  // of the last full pass ([N][K], T); the residual r_ik becomes
+  // w_i P_ik (u_ik - sum_k P_ik u_ik) with u = J v, so the gradient slots
+  // accumulate F v = -H v.  Wout ([N][K] float32, tiled pass with the
+  // separate beta kernel only) receives those residuals.
+  const void *Pin;
+  float *Wout;
 };
 
 // Bits of the device error word: which kernel's bounded wait gave up.
@@ -110,6 +117,8 @@ struct PassPlan {
 // 16-byte aligned X, Y, Z, choice).
 PassPlan plan_pass(const Shape &s, bool fp64, bool full, int num_sms, bool allow_tiled = true);
 bool plan_pass_tiled(const Shape &s, bool full, int num_sms, PassPlan &pl);
+// The tiled full pass leaves the beta gradient to its separate kernel (wide shapes).
+bool plan_pass_beta_ext(const Shape &s);
 cudaError_t launch_pass_tiled(const Shape &s, const PassPlan &pl, bool full, const PassIO &io, cudaStream_t st);
 cudaError_t launch_pass(const Shape &s, const PassPlan &pl, bool fp64, bool full, const PassIO &io, cudaStream_t st);
 
@@ -402,6 +411,8 @@ cudaError_t launch_unpack_lower(int64_t n, const double *in, double *F, cudaStre
 cudaError_t launch_f64_to_f32_lower(int64_t n, const double *F, float *F32, cudaStream_t st);
 
 // Small FP64 vector kernels.
+cudaError_t launch_dot(int64_t n, const double *a, const double *b, double *out, cudaStream_t st);  // out = a.b
+cudaError_t launch_axpby(int64_t n, double a, const double *x, double b, double *y, cudaStream_t st);  // y = ax+by
 cudaError_t launch_axpy_theta(int64_t n, double *theta, const double *delta, const double *tscale, double *scal_out,
                               cudaStream_t st);
 cudaError_t launch_vec_absmax(int64_t n, const double *v, double *out, cudaStream_t st);

@@ -179,6 +179,23 @@ __device__ __forceinline__ void pass_segment(const PassDims &D, const PassIO &io
           if (k == yi) uy = v;
         }
       }
+      if (FULL && io.Pin) {  // Hessian-vector product: r_ik = w_i P_ik (u_ik - ubar_i)
+        const T *Pr = reinterpret_cast<const T *>(io.Pin) + i * K;
+        T pk[kMaxClassSlots], ub = 0;
+#pragma unroll
+        for (int c = 0; c < kMaxClassSlots; ++c) {
+          const int k = lane + 32 * c;
+          pk[c] = k < K ? Pr[k] : (T)0;
+          if (k < K) ub = fma(pk[c], u[c], ub);
+        }
+        ub = warp_sum(ub);
+#pragma unroll
+        for (int c = 0; c < kMaxClassSlots; ++c) {
+          const int k = lane + 32 * c;
+          if (k < K) res[(size_t)r * K + k] = wi * pk[c] * (u[c] - ub);
+        }
+        continue;
+      }
       umax = warp_max(umax);
       T s = 0;
 #pragma unroll

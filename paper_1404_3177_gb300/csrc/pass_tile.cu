@@ -283,6 +283,24 @@ __global__ void __launch_bounds__(kPT, kYZSlots == 4 ? 1 : 2) pass_tile_kernel(T
         const bool vr = rr < nrows;
         const int yi = cs[rr];
         const float wr = (io.w && vr) ? __ldg(io.w + row0 + rr) : 1.f;  // case weight
+        if (FULL && io.Pin) {  // Hessian-vector product: r_ik = w_i P_ik (u_ik - ubar_i)
+          const float *Pr = reinterpret_cast<const float *>(io.Pin) + (row0 + rr) * K;
+          float pk[CS], ub = 0.f;
+#pragma unroll
+          for (int c = 0; c < CS; ++c) {
+            const int k = lane + 32 * c;
+            pk[c] = (k < K && vr) ? __ldg(Pr + k) : 0.f;
+            ub = fmaf(pk[c], u[r][c], ub);
+          }
+          ub = wsum(ub);
+#pragma unroll
+          for (int c = 0; c < CS; ++c) {
+            const int k = lane + 32 * c;
+            res[c][r] = wr * pk[c] * (u[r][c] - ub);
+            if (io.Wout && k < K && vr) io.Wout[(row0 + rr) * K + k] = res[c][r];
+          }
+          continue;
+        }
         float m = -FLT_MAX;
 #pragma unroll
         for (int c = 0; c < CS; ++c)
@@ -466,7 +484,8 @@ template <int JA, int KB>
 __global__ void __launch_bounds__(256, 1) grad_beta_kernel(int64_t N, int K, int p, int64_t n,
                                                            const float *__restrict__ X, const float *__restrict__ P,
                                                            const int *__restrict__ choice, const float *w,
-                                                           double *partials, int *err, uint64_t wait_ns) {
+                                                           double *partials, int *err, uint64_t wait_ns,
+                                                           int p_is_residual) {
   extern __shared__ __align__(128) unsigned char sm[];
   const int sx = ((kGbRows * p * 4) + 127) & ~127, sp = ((kGbRows * K * 4) + 127) & ~127;
   const int stage_bytes = sx + sp + 256;
@@ -542,7 +561,7 @@ __global__ void __launch_bounds__(256, 1) grad_beta_kernel(int64_t N, int K, int
 #pragma unroll
       for (int c = 0; c < KB; ++c) {
         const int k = ty + 16 * c;
-        rr[c] = k < K ? wr * ((k == y ? 1.f : 0.f) - Ps[r * K + k]) : 0.f;
+        rr[c] = k < K ? (p_is_residual ? Ps[r * K + k] : wr * ((k == y ? 1.f : 0.f) - Ps[r * K + k])) : 0.f;
       }
 #pragma unroll
       for (int a = 0; a < JA; ++a)
@@ -589,8 +608,10 @@ cudaError_t launch_gb(const Shape &s, int grid, const PassIO &io, cudaStream_t s
   const size_t smem = grad_beta_smem(s.K, s.p);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, 256, smem, st>>>(s.N, s.K, s.p, s.n, io.X, reinterpret_cast<const float *>(io.P), io.choice, io.w,
-                                io.partials, io.err, io.wait_ns);
+  // Hessian-vector mode: the residuals w_i P_ik (u_ik - ubar_i) written by the pass stand in for P
+  const bool hv = io.Pin != nullptr;
+  kern<<<grid, 256, smem, st>>>(s.N, s.K, s.p, s.n, io.X, hv ? io.Wout : reinterpret_cast<const float *>(io.P),
+                                io.choice, hv ? nullptr : io.w, io.partials, io.err, io.wait_ns, hv ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -674,6 +695,12 @@ cudaError_t launch_cs(const TileDims &D, int grid, size_t smem, const PassIO &io
 
 }  // namespace
 
+bool plan_pass_beta_ext(const Shape &s) {
+  TileDims D{};
+  size_t smem = 0;
+  return make_tile_dims(s, true, 2, D, smem) && D.beta_ext;
+}
+
 bool plan_pass_tiled(const Shape &s, bool full, int num_sms, PassPlan &pl) {
   TileDims D{};
   size_t smem = 0;
@@ -703,6 +730,7 @@ cudaError_t launch_pass_tiled(const Shape &s, const PassPlan &pl, bool full, con
   if (!aligned) return cudaErrorInvalidValue;
   if (pl.rows != 16) return cudaErrorInvalidValue;
   if (!full) return launch_cs<2, false>(D, pl.grid, smem, io, st);
+  if (io.Pin && D.beta_ext && !io.Wout) return cudaErrorInvalidValue;
   cudaError_t e = launch_cs<2, true>(D, pl.grid, smem, io, st);
   if (e == cudaSuccess && D.beta_ext) e = launch_grad_beta(s, pl.grid, io, st);
   return e;
