@@ -281,6 +281,43 @@ MNL_API int mnl_std_errors(mnl_handle *h, const double *theta, double *se);
  * modes, float64 in MNL_FP64). */
 MNL_API int mnl_predict(mnl_handle *h, const double *theta, double *P, double *loglik);
 
+/* Collinearity check of the data (the `linDepTol` argument of the package's
+ * mnlogit call, Sec. 2.3; App. B's necessary conditions for a non-singular
+ * Hessian): X and every Y_k need linearly independent columns, and so do the
+ * generic variables' normalized columns (the N (K-1) rows Z_ik - Z_i0, k >= 1,
+ * stacked).  Within each block the columns are taken in order and column j is
+ * flagged when the part of it orthogonal to the unflagged earlier columns has
+ * a norm of at most tol * ||column j|| - a rank-revealing factorisation that
+ * drops the later columns of a collinear set one by one.  Computed on the
+ * device in float64: the blocks' Gram matrices from one pass over the data
+ * (float32 products are exact in float64), then per block an in-order Cholesky
+ * factorisation that flags column j when its pivot is at most tol^2 times the
+ * column's squared norm.  Observation weights play no part.
+ *   tol       > 0 (the package's default linDepTol is 1e-6).
+ *   flags     HOST int32 [p + K d + f]: X column j at j; column j of Y_k at
+ *             p + k d + j (Y_0's entries are 0 unless gamma_base = 1); Z column
+ *             j at p + K d + j.  1: dependent, 0: kept.
+ *   ndropped  HOST, or NULL: the number of flags set.
+ * Synchronises.  Allocates (and frees before returning) scratch for the Gram
+ * matrices (the sum of the blocks' cols^2 doubles) and their partial tiles.
+ * MNL_ERR_INVALID_ARG for tol <= 0 or NULL flags. */
+MNL_API int mnl_check_collinear(mnl_handle *h, double tol, int32_t *flags, int32_t *ndropped);
+
+/* Remove flagged columns from the model, as the package does with collinear
+ * columns before it fits.  Their coefficients - beta_k[j] for every k when X
+ * column j is flagged, gamma_k[j] for column j of Y_k, alpha[j] for Z column j
+ * - are held at their current values (zero in a fit from theta = 0, which is
+ * the fit of the model without those columns) by mnl_newton_step, mnl_fit,
+ * mnl_shard_solve and mnl_std_errors (whose entries for them are NaN): their
+ * gradient entries count as zero and their rows and columns of -H are those
+ * of the identity in the Newton system.  mnl_loglik_grad, mnl_hessian,
+ * mnl_hessian_vec and mnl_predict still describe the full model.
+ *   flags  HOST int32 [p + K d + f] in the layout of mnl_check_collinear (Y_0
+ *          entries are ignored when gamma_base = 0), or NULL to restore the
+ *          full model.
+ * MNL_ERR_INVALID_ARG for a flag other than 0 or 1.  Synchronises. */
+MNL_API int mnl_drop_columns(mnl_handle *h, const int32_t *flags);
+
 /* How mnl_newton_step / mnl_fit solve (-H) delta = g.
  *   MNL_SOLVE_FP64:  blocked float64 Cholesky and float64 triangular solves.
  *   MNL_SOLVE_MIXED: float32 Cholesky of -H and float64 iterative refinement

@@ -37,18 +37,20 @@ def dependent_columns(M: np.ndarray, tol: float) -> np.ndarray:
     A = np.asarray(M, dtype=np.float64)
     ncol = A.shape[1]
     flags = np.zeros(ncol, dtype=np.int32)
-    Q = np.zeros((A.shape[0], 0))
+    Q = np.empty((A.shape[0], ncol))  # orthonormal basis of the kept columns: Q[:, :kept]
+    kept = 0
     for j in range(ncol):
         a = A[:, j]
         norm_a = np.sqrt(a @ a)
         r = a.copy()
         for _ in range(2):
-            r = r - Q @ (Q.T @ r)
+            r = r - Q[:, :kept] @ (Q[:, :kept].T @ r)
         norm_r = np.sqrt(r @ r)
         if norm_a == 0.0 or norm_r <= tol * norm_a:
             flags[j] = 1
             continue
-        Q = np.column_stack([Q, r / norm_r])
+        Q[:, kept] = r / norm_r
+        kept += 1
     return flags
 
 

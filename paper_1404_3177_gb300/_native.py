@@ -34,7 +34,8 @@ EXPORTS = (
     "mnl_num_params", "mnl_status_string", "mnl_workspace_bytes", "mnl_fit_opts_default", "mnl_create",
     "mnl_upload", "mnl_loglik_grad", "mnl_hessian", "mnl_newton_step", "mnl_fit", "mnl_destroy",
     "mnl_loglik_grad_noalloc", "mnl_set_solve", "mnl_set_wait_bound", "mnl_set_weights",
-    "mnl_create_ex", "mnl_hessian_vec", "mnl_set_cg_max", "mnl_shard_sums_size", "mnl_shard_grad_hess", "mnl_shard_solve", "mnl_shard_loglik", "mnl_loglik_roundoff", "mnl_std_errors", "mnl_predict", "mnl_batch_create", "mnl_batch_num_params", "mnl_batch_fit",
+    "mnl_create_ex", "mnl_hessian_vec", "mnl_set_cg_max", "mnl_shard_sums_size", "mnl_shard_grad_hess", "mnl_shard_solve", "mnl_shard_loglik", "mnl_loglik_roundoff", "mnl_std_errors", "mnl_predict",
+    "mnl_check_collinear", "mnl_drop_columns", "mnl_batch_create", "mnl_batch_num_params", "mnl_batch_fit",
     "mnl_batch_destroy", "mnl_server_opts_default", "mnl_server_create", "mnl_server_submit", "mnl_server_step",
     "mnl_server_poll", "mnl_server_finished", "mnl_server_memory_in_use", "mnl_server_destroy",
 )
@@ -150,6 +151,10 @@ def load() -> C.CDLL:
         lib.mnl_predict.restype = i32
         lib.mnl_predict.argtypes = [vp, vp, vp, C.POINTER(C.c_double)]
         lib.mnl_create_ex.restype = i32
+        lib.mnl_check_collinear.argtypes = [vp, C.c_double, vp, C.POINTER(C.c_int32)]
+        lib.mnl_check_collinear.restype = i32
+        lib.mnl_drop_columns.argtypes = [vp, vp]
+        lib.mnl_drop_columns.restype = i32
         lib.mnl_create_ex.argtypes = [C.POINTER(mnl_dims), C.POINTER(mnl_data), i32, i32, vp, C.POINTER(vp)]
         lib.mnl_hessian_vec.restype = i32
         lib.mnl_hessian_vec.argtypes = [vp, vp, vp, vp]
@@ -292,6 +297,23 @@ def mnl_predict(handle: int, theta_ptr: int, P_ptr: int, want_loglik: bool = Tru
     _check(load().mnl_predict(C.c_void_p(handle), C.c_void_p(theta_ptr), C.c_void_p(P_ptr),
                               C.byref(l) if want_loglik else None), "mnl_predict")
     return l.value if want_loglik else None
+
+
+def mnl_check_collinear(handle: int, tol: float, nflags: int):
+    """(flags, ndropped): flags is a list of nflags ints (0 kept, 1 dependent)."""
+    flags = (C.c_int32 * max(nflags, 1))()
+    nd = C.c_int32()
+    _check(load().mnl_check_collinear(C.c_void_p(handle), C.c_double(tol), flags, C.byref(nd)),
+           "mnl_check_collinear")
+    return list(flags)[:nflags], nd.value
+
+
+def mnl_drop_columns(handle: int, flags) -> None:
+    if flags is None:
+        _check(load().mnl_drop_columns(C.c_void_p(handle), None), "mnl_drop_columns")
+        return
+    arr = (C.c_int32 * max(len(flags), 1))(*[int(x) for x in flags])
+    _check(load().mnl_drop_columns(C.c_void_p(handle), arr), "mnl_drop_columns")
 
 
 MNL_CREATE_TRUNCATED = 1

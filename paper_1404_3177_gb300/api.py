@@ -1,6 +1,7 @@
 """torch-facing wrapper around the C ABI (marshalling only; no arithmetic here)."""
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 from . import _native as nat
@@ -118,6 +119,17 @@ class MNL:
         l = nat.mnl_predict(self.h, th.data_ptr(), P.data_ptr())
         return P, l
 
+    def check_collinear(self, tol=1e-6):
+        """Flags (numpy int32 [p + K d + f]: X | Y_0..Y_{K-1} | Z) of the data columns that depend on earlier
+        ones (Sec. 2.3 linDepTol, App. B); see mnl_check_collinear."""
+        d = self.dims
+        flags, _ = nat.mnl_check_collinear(self.h, tol, d.p + d.K * d.d + d.f)
+        return np.asarray(flags, dtype=np.int32)
+
+    def drop_columns(self, flags):
+        """Hold the coefficients of the flagged columns at their current values (None: the full model)."""
+        nat.mnl_drop_columns(self.h, None if flags is None else [int(x) for x in flags])
+
     def newton_step(self, theta):
         """One Newton-Raphson iteration; theta (float64 CUDA) is updated in place."""
         info = nat.mnl_newton_step(self.h, self._theta(theta).data_ptr())
@@ -220,7 +232,6 @@ class MNLServer:
 
     def submit(self, X=None, Y=None, Z=None, choice=None, K=None, theta0=None):
         """X, Y, Z, choice: numpy arrays (float32 / int32) on the host; returns a ticket."""
-        import numpy as np
         N = choice.shape[0]
         if Y is not None and Y.size:
             K = Y.shape[1]
@@ -244,7 +255,6 @@ class MNLServer:
 
     def poll(self, ticket):
         """(theta numpy array, result dict) once finished, else None."""
-        import numpy as np
         out = np.empty(self._sizes[ticket])
         done, res = nat.mnl_server_poll(self.h, ticket, out.ctypes.data)
         if not done:

@@ -76,6 +76,9 @@ struct mnl_handle {
   int cg_max;           // conjugate-gradient iterations per Newton step at most
   double *cg;           // [3 n]: CG residual, direction, product (also scratch of mnl_hessian_vec)
   float *wbuf;          // [N][K] Hessian-vector residuals for the separate beta kernel (wide shapes)
+  // coefficients of dropped data columns (mnl_drop_columns), in the kernels' order
+  int nmask;
+  int64_t *mask_idx;    // device [n_theta] (the first nmask entries are used)
   // host mirrors (pinned)
   double *h_scal;
   int *h_flags;
@@ -402,6 +405,7 @@ int step_impl(mnl_handle *h, double *theta, mnl_step_info *info, double gtol, bo
   CK(cudaEventRecord(h->ev[0], h->st));
   int rc = run_pass(h, theta, true, nullptr, kL);
   if (rc) return rc;
+  CK(launch_mask_vec(h->nmask, h->mask_idx, h->grad, 0.0, h->st));
   CK(launch_vec_absmax(n, h->grad, h->scal + kGinf, h->st));
   h->launches += 1;
   CK(cudaEventRecord(h->ev[1], h->st));
@@ -420,9 +424,10 @@ int step_impl(mnl_handle *h, double *theta, mnl_step_info *info, double gtol, bo
   }
   rc = run_hessian(h, h->ev + 5);
   if (rc) return rc;
+  const bool mixed = h->solve_mode == MNL_SOLVE_MIXED;
+  CK(launch_mask_matrix(n, h->nmask, h->mask_idx, h->F, mixed ? h->F32 : nullptr, h->st));
   CK(cudaEventRecord(h->ev[2], h->st));
   int nl = 0;
-  const bool mixed = h->solve_mode == MNL_SOLVE_MIXED;
   if (mixed && h->tcp.ready) {
     CK(launch_mixed_solve_tc(h->tcp, h->F, h->F32, h->grad, h->delta, h->mwork, h->status, h->err, kRefineIters,
                              h->wait_ns, h->st, &nl));
@@ -599,6 +604,7 @@ int step_truncated(mnl_handle *h, double *theta, mnl_step_info *info, double gto
   CK(cudaEventRecord(h->ev[0], h->st));
   int rc = run_pass(h, theta, true, nullptr, kL);
   if (rc) return rc;
+  CK(launch_mask_vec(h->nmask, h->mask_idx, h->grad, 0.0, h->st));
   CK(launch_vec_absmax(n, h->grad, h->scal + kGinf, h->st));
   CK(launch_dot(n, h->grad, h->grad, h->scal + 3, h->st));
   CK(cudaEventRecord(h->ev[1], h->st));
@@ -626,6 +632,7 @@ int step_truncated(mnl_handle *h, double *theta, mnl_step_info *info, double gto
   int it = 0;
   for (; it < h->cg_max && rs > target; ++it) {
     if ((rc = hv_pass(h, pv, ap))) return rc;
+    CK(launch_mask_vec(h->nmask, h->mask_idx, ap, 0.0, h->st));  // CG stays in the free coefficients
     CK(launch_dot(n, pv, ap, h->scal + 13, h->st));
     CK(cudaMemcpyAsync(h->h_scal + 13, h->scal + 13, sizeof(double), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
@@ -1233,8 +1240,10 @@ int mnl_std_errors(mnl_handle *h, const double *theta, double *se) {
   if (rc) return rc;
   if ((rc = run_pass(h, th, true, nullptr, kL))) return rc;
   if ((rc = run_hessian(h))) return rc;
+  CK(launch_mask_matrix(n, h->nmask, h->mask_idx, h->F, nullptr, h->st));
   CK(launch_std_errors(n, h->F, h->Binv, h->dinv, h->cwork, h->status, h->err, h->gb1 ? h->vec_int : se, h->st,
                        h->wait_ns));
+  CK(launch_mask_vec(h->nmask, h->mask_idx, h->gb1 ? h->vec_int : se, std::nan(""), h->st));
   if (h->gb1) CK(launch_perm_to_user(n, h->perm, h->vec_int, se, h->st));
   CK(cudaMemcpyAsync(h->h_flags, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   CK(cudaMemcpyAsync(h->h_flags + 1, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
@@ -1298,6 +1307,8 @@ int mnl_shard_solve(mnl_handle *h, const double *sums, double *delta, mnl_step_i
   CK(cudaEventRecord(h->ev[2], h->st));
   CK(cudaMemcpyAsync(h->grad, sums + 2, (size_t)n * 8, cudaMemcpyDeviceToDevice, h->st));
   CK(launch_unpack_lower(n, sums + 2 + n, h->F, h->st));
+  CK(launch_mask_vec(h->nmask, h->mask_idx, h->grad, 0.0, h->st));
+  CK(launch_mask_matrix(n, h->nmask, h->mask_idx, h->F, nullptr, h->st));
   rc = solve_system(h, loc);
   CK(cudaEventRecord(h->ev[3], h->st));
   if (rc == MNL_OK) CK(cudaMemcpyAsync(delta, h->delta, (size_t)n * 8, cudaMemcpyDeviceToDevice, h->st));
@@ -1343,6 +1354,52 @@ int mnl_set_weights(mnl_handle *h, const float *w) {
   if (h->h_flags[0] & 2) return MNL_ERR_NONFINITE;
   if (h->h_flags[0] & 1) return MNL_ERR_INVALID_ARG;
   h->w = w;
+  return MNL_OK;
+}
+
+int mnl_check_collinear(mnl_handle *h, double tol, int32_t *flags, int32_t *ndropped) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!flags || !(tol > 0.0) || !std::isfinite(tol)) return MNL_ERR_INVALID_ARG;
+  if ((rc = set_device(h))) return rc;
+  CK(collinear_check(h->dims, h->X, h->Y, h->Zu, tol, h->nsm, h->st, flags, nullptr));
+  if (ndropped) {
+    int32_t c = 0;
+    for (int i = 0; i < collinear_flags_size(h->dims); ++i) c += flags[i] != 0;
+    *ndropped = c;
+  }
+  return MNL_OK;
+}
+
+int mnl_drop_columns(mnl_handle *h, const int32_t *flags) {
+  if (!h) return MNL_ERR_INVALID_ARG;
+  if (!flags) { h->nmask = 0; return MNL_OK; }
+  const mnl_dims &d = h->dims;
+  const int nf = collinear_flags_size(d);
+  for (int i = 0; i < nf; ++i)
+    if (flags[i] != 0 && flags[i] != 1) return MNL_ERR_INVALID_ARG;
+  // The coefficients of the flagged columns in the caller's order (eq. "theta vec"), then in the kernels'.
+  const int64_t n = h->S.n, nb = (int64_t)(d.K - 1) * d.p, dd = d.d;
+  std::vector<int64_t> idx;
+  auto internal = [&](int64_t u) { return !h->gb1 ? u : u < nb ? u : u < nb + dd ? n - dd + (u - nb) : u - dd; };
+  for (int k = 1; k < d.K; ++k)
+    for (int j = 0; j < d.p; ++j)
+      if (flags[j]) idx.push_back(internal((int64_t)(k - 1) * d.p + j));
+  int64_t u = nb;
+  for (int k = h->gb1 ? 0 : 1; k < d.K; ++k)
+    for (int j = 0; j < d.d; ++j, ++u)
+      if (flags[d.p + k * d.d + j]) idx.push_back(internal(u));
+  for (int j = 0; j < d.f; ++j, ++u)
+    if (flags[d.p + d.K * d.d + j]) idx.push_back(internal(u));
+  if (u != n) return MNL_ERR_INVALID_ARG;
+  int rc = set_device(h);
+  if (rc) return rc;
+  if (!h->mask_idx && (rc = dalloc(h, &h->mask_idx, (size_t)n * sizeof(int64_t)))) return rc;
+  if (!idx.empty()) {
+    CK(cudaMemcpyAsync(h->mask_idx, idx.data(), idx.size() * sizeof(int64_t), cudaMemcpyHostToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));
+  }
+  h->nmask = (int)idx.size();
   return MNL_OK;
 }
 

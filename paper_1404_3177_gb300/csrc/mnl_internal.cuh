@@ -410,6 +410,24 @@ cudaError_t launch_pack_lower(int64_t n, const double *F, double *out, cudaStrea
 cudaError_t launch_unpack_lower(int64_t n, const double *in, double *F, cudaStream_t st);
 cudaError_t launch_f64_to_f32_lower(int64_t n, const double *F, float *F32, cudaStream_t st);
 
+// Collinearity check (collinear.cu): flags of the dependent data columns in the
+// layout [X (p) | Y_0 .. Y_{K-1} (K d) | Z (f)] (Y_0 only with gamma_base = 1),
+// written to flags_host; synchronous, allocates and frees its own scratch.
+struct CollinearStats {
+  float ms;          // device time of the Gram pass and the decisions
+  int groups, jobs, tile;
+  double gram_fma;   // sum over the blocks of rows x cols (cols + 1) / 2
+  double bytes;      // sum over the blocks of rows x cols x 4 (data read once per block pair at least)
+};
+int collinear_flags_size(const mnl_dims &d);
+cudaError_t collinear_check(const mnl_dims &d, const float *X, const float *Y, const float *Z, double tol, int nsm,
+                            cudaStream_t st, int32_t *flags_host, CollinearStats *stats);
+// v[idx[t]] = val for t < m.
+cudaError_t launch_mask_vec(int m, const int64_t *idx, double *v, double val, cudaStream_t st);
+// Rows and columns idx[0 .. m) of F (n x n, both triangles) and of F32's lower
+// triangle (when not NULL) set to those of the identity.
+cudaError_t launch_mask_matrix(int64_t n, int m, const int64_t *idx, double *F, float *F32, cudaStream_t st);
+
 // Small FP64 vector kernels.
 cudaError_t launch_dot(int64_t n, const double *a, const double *b, double *out, cudaStream_t st);  // out = a.b
 cudaError_t launch_axpby(int64_t n, double a, const double *x, double b, double *y, cudaStream_t st);  // y = ax+by
