@@ -250,6 +250,7 @@ int dalloc(mnl_handle *h, T **p, size_t bytes) {
 }
 
 void free_all(mnl_handle *h) {
+  tc_chol_release(&h->tcp);
   for (void *p : h->allocs) cudaFree(p);
   h->allocs.clear();
   if (h->h_scal) cudaFreeHost(h->h_scal);

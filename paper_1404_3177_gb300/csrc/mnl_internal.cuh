@@ -369,14 +369,21 @@ cudaError_t launch_chol_update_tc(const CUtensorMap *maps, const CholUnit *units
 struct TcCholPlan {
   int64_t n = 0, n_pad = 0;
   int np = 0, grid = 0;
+  int reserve = 0;                    // SMs left to the side stream while the rest of an update runs
   void *ws = nullptr;                 // tc_chol_bytes(n) bytes of device memory
-  CUtensorMap *maps = nullptr;        // device: Ph, Pl, Rh, Rl
+  CUtensorMap *maps = nullptr;        // device: two sets (panel parity) of Ph, Pl, Rh, Rl
   CholUnit *units = nullptr;          // device: all panels' units
-  std::vector<int> unit_off;          // host: panel k's units are [unit_off[k], unit_off[k + 1])
-  float *Ph = nullptr, *Pl = nullptr, *Rh = nullptr, *Rl = nullptr;  // [n_pad][128] hi / lo
+  // host: panel k's units are [unit_off[k], unit_off[k + 1]); those that the next
+  // panel's diagonal and panel steps wait for come first, [unit_off[k], unit_mid[k])
+  std::vector<int> unit_off, unit_mid;
+  float *Ph[2] = {}, *Pl[2] = {}, *Rh[2] = {}, *Rl[2] = {};  // [n_pad][128] hi / lo, per panel parity
   float *InvT = nullptr;             // [np][128][128]: inverse of each diagonal block, transposed
+  cudaStream_t side = nullptr;       // the diagonal and panel steps of the next panel (look-ahead)
+  cudaEvent_t ev_start = nullptr, ev_next = nullptr, ev_panel = nullptr;
   bool ready = false;
 };
+// Destroys the plan's stream and events (the device memory belongs to the caller).
+void tc_chol_release(TcCholPlan *plan);
 // Use the tensor-core factorisation for n_theta at or above this.
 constexpr int64_t kTcCholMinN = 4096;
 size_t tc_chol_bytes(int64_t n);

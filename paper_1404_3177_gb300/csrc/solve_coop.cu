@@ -35,6 +35,9 @@
 // conditioning of F); otherwise (or if the float32 factor fails) the caller
 // falls back to the float64 factorisation, which is the same kernel without
 // the inverse.
+#include <algorithm>
+#include <cstdlib>
+
 #include "mnl_internal.cuh"
 
 namespace mnl {
@@ -781,8 +784,14 @@ __global__ void status_and_kernel(int *status, int mask) { atomicAnd(status, mas
 //     B_ij -= L_ik B_kj (i > k, j <= k).
 // B is the block forward substitution L B = I carried along with the
 // factorisation, as in the cooperative kernel above.
+// Look-ahead: panel k's update is two launches, first the tiles that panel
+// k + 1's diagonal and panel steps read (tile column k + 1 of the factor, tile
+// row k + 1 of the inverse), then the rest on all but a few SMs, while a
+// second stream runs panel k + 1's diagonal and panel steps beside it.  The
+// panel buffers (Ph, Pl, Rh, Rl) come in two sets, by panel parity.
 // ---------------------------------------------------------------------------
 constexpr int kDp = kCholPanel;  // panel width = diagonal block edge
+constexpr int kCholReserve = 8;  // SMs kept free for the look-ahead's diagonal and panel steps
 constexpr int kDd = kDp + 4;     // shared stride of the diagonal step's arrays
 constexpr size_t kDiag128Smem = (size_t)(2 * kDp * kDd + 32 * kLts + kDp) * sizeof(float);
 constexpr int kPr = 64;          // panel step: rows (or inverse columns) per item
@@ -1203,8 +1212,17 @@ size_t tc_chol_bytes(int64_t n) {
     const int64_t m = np - 1 - k;
     units += m * (m + 1) / 2 + m * (k + 1);
   }
-  return round256(4 * sizeof(CUtensorMap)) + 4 * round256((size_t)n_pad * kDp * 4) +
+  return round256(8 * sizeof(CUtensorMap)) + 8 * round256((size_t)n_pad * kDp * 4) +
          round256((size_t)np * kDp * kDp * 4) + round256((size_t)units * sizeof(CholUnit));
+}
+
+void tc_chol_release(TcCholPlan *P) {
+  if (P->side) cudaStreamDestroy(P->side);
+  for (cudaEvent_t *e : {&P->ev_start, &P->ev_next, &P->ev_panel})
+    if (*e) cudaEventDestroy(*e);
+  P->side = nullptr;
+  P->ev_start = P->ev_next = P->ev_panel = nullptr;
+  P->ready = false;
 }
 
 cudaError_t tc_chol_prepare(int64_t n, void *ws, int num_sms, TcCholPlan *P) {
@@ -1215,23 +1233,30 @@ cudaError_t tc_chol_prepare(int64_t n, void *ws, int num_sms, TcCholPlan *P) {
   P->ws = ws;
   unsigned char *w = static_cast<unsigned char *>(ws);
   size_t o = 0;
-  P->maps = reinterpret_cast<CUtensorMap *>(w + o); o += round256(4 * sizeof(CUtensorMap));
-  float **bufs[4] = {&P->Ph, &P->Pl, &P->Rh, &P->Rl};
+  P->maps = reinterpret_cast<CUtensorMap *>(w + o); o += round256(8 * sizeof(CUtensorMap));
+  float **bufs[8] = {&P->Ph[0], &P->Pl[0], &P->Rh[0], &P->Rl[0], &P->Ph[1], &P->Pl[1], &P->Rh[1], &P->Rl[1]};
   for (float **b : bufs) { *b = reinterpret_cast<float *>(w + o); o += round256((size_t)P->n_pad * kDp * 4); }
   P->InvT = reinterpret_cast<float *>(w + o); o += round256((size_t)P->np * kDp * kDp * 4);
   P->units = reinterpret_cast<CholUnit *>(w + o);
+  // Per panel k: first the units that the diagonal and panel steps of panel k + 1
+  // read (tile column k + 1 of the factor, tile row k + 1 of the inverse), then the rest.
   std::vector<CholUnit> u;
   P->unit_off.assign(1, 0);
+  P->unit_mid.clear();
   for (int k = 0; k + 1 < P->np; ++k) {
-    for (int ti = k + 1; ti < P->np; ++ti)
-      for (int tj = k + 1; tj <= ti; ++tj) u.push_back(CholUnit{ti, tj, 0, 0, ti == tj ? 1 : 0, 0});
-    for (int ti = k + 1; ti < P->np; ++ti)
+    const int k1 = k + 1;
+    for (int ti = k1; ti < P->np; ++ti) u.push_back(CholUnit{ti, k1, 0, 0, ti == k1 ? 1 : 0, 0});
+    for (int tj = 0; tj <= k; ++tj) u.push_back(CholUnit{k1, tj, 1, 1, 0, 0});
+    P->unit_mid.push_back((int)u.size());
+    for (int ti = k1 + 1; ti < P->np; ++ti)
+      for (int tj = k1 + 1; tj <= ti; ++tj) u.push_back(CholUnit{ti, tj, 0, 0, ti == tj ? 1 : 0, 0});
+    for (int ti = k1 + 1; ti < P->np; ++ti)
       for (int tj = 0; tj <= k; ++tj) u.push_back(CholUnit{ti, tj, 1, 1, 0, 0});
     P->unit_off.push_back((int)u.size());
   }
-  CUtensorMap hm[4];
+  CUtensorMap hm[8];
   cudaError_t e;
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 8; ++i)
     if ((e = encode_rows_map(*bufs[i], P->n_pad, kDp, &hm[i])) != cudaSuccess) return e;
   if ((e = cudaMemcpy(P->maps, hm, sizeof(hm), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
   if (!u.empty() && (e = cudaMemcpy(P->units, u.data(), u.size() * sizeof(CholUnit), cudaMemcpyHostToDevice)) !=
@@ -1244,7 +1269,11 @@ cudaError_t tc_chol_prepare(int64_t n, void *ws, int num_sms, TcCholPlan *P) {
                                 (int)kPanelSmem)) != cudaSuccess)
     return e;
   if ((e = chol_update_tc_setup()) != cudaSuccess) return e;
+  if ((e = cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  for (cudaEvent_t *ev : {&P->ev_start, &P->ev_next, &P->ev_panel})
+    if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) return e;
   P->grid = num_sms;
+  P->reserve = std::min(kCholReserve, num_sms / 4);
   P->ready = true;
   return cudaSuccess;
 }
@@ -1262,22 +1291,46 @@ cudaError_t launch_mixed_solve_tc(const TcCholPlan &P, const double *F, float *F
   cudaError_t e;
   if ((e = cudaMemsetAsync(Li, 0, (size_t)n * n * 4, st)) != cudaSuccess) return e;
   int cnt = 0;
-  for (int k = 0; k < P.np; ++k) {
-    chol_diag128_kernel<<<1, 256, kDiag128Smem, st>>>(F32, n, n, k, Li, P.InvT, P.Rh, P.Rl, status, 8);
+  // Diagonal and panel steps of panel k on stream s, into the buffers of parity k & 1.
+  auto diag_panel = [&](int k, cudaStream_t s) {
+    const int b = k & 1;
+    chol_diag128_kernel<<<1, 256, kDiag128Smem, s>>>(F32, n, n, k, Li, P.InvT, P.Rh[b], P.Rl[b], status, 8);
     const int64_t j0 = (int64_t)k * kDp;
     const int items = (int)((P.n_pad - j0 - kDp) / kPr + j0 / kPr);
     if (items > 0)
-      chol_panel_kernel<<<std::min(items, 2 * P.grid), 256, kPanelSmem, st>>>(F32, n, n, P.n_pad, k, Li, P.InvT, P.Ph,
-                                                                            P.Pl, P.Rh, P.Rl);
+      chol_panel_kernel<<<std::min(items, 2 * P.grid), 256, kPanelSmem, s>>>(F32, n, n, P.n_pad, k, Li, P.InvT,
+                                                                            P.Ph[b], P.Pl[b], P.Rh[b], P.Rl[b]);
     cnt += items > 0 ? 2 : 1;
-    if (k + 1 < P.np) {
-      const int u0 = P.unit_off[(size_t)k], nu = P.unit_off[(size_t)k + 1] - u0;
-      if ((e = launch_chol_update_tc(P.maps, P.units + u0, nu, std::min(nu, P.grid), F32, Li, n, n, err, wait_ns,
-                                     st)) != cudaSuccess)
+  };
+  // Look-ahead: while the bulk of panel k's trailing update runs on st (on all
+  // but `reserve` SMs), the side stream factors the diagonal block of panel
+  // k + 1 and forms its panel, as soon as the few update tiles they read are
+  // done.  The panel buffers alternate between two sets so that panel k + 1's
+  // are written while panel k's are still read.
+  if ((e = cudaEventRecord(P.ev_start, st)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(P.side, P.ev_start, 0)) != cudaSuccess) return e;
+  diag_panel(0, P.side);
+  if ((e = cudaEventRecord(P.ev_panel, P.side)) != cudaSuccess) return e;
+  for (int k = 0; k + 1 < P.np; ++k) {
+    const CUtensorMap *maps = P.maps + 4 * (k & 1);
+    const int u0 = P.unit_off[(size_t)k], um = P.unit_mid[(size_t)k], u1 = P.unit_off[(size_t)k + 1];
+    if ((e = cudaStreamWaitEvent(st, P.ev_panel, 0)) != cudaSuccess) return e;
+    if ((e = launch_chol_update_tc(maps, P.units + u0, um - u0, std::min(um - u0, P.grid), F32, Li, n, n, err,
+                                   wait_ns, st)) != cudaSuccess)
+      return e;
+    if ((e = cudaEventRecord(P.ev_next, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(P.side, P.ev_next, 0)) != cudaSuccess) return e;
+    diag_panel(k + 1, P.side);
+    if ((e = cudaEventRecord(P.ev_panel, P.side)) != cudaSuccess) return e;
+    if (u1 > um) {
+      if ((e = launch_chol_update_tc(maps, P.units + um, u1 - um, std::max(1, std::min(u1 - um, P.grid - P.reserve)),
+                                     F32, Li, n, n, err, wait_ns, st)) != cudaSuccess)
         return e;
       ++cnt;
     }
+    ++cnt;
   }
+  if ((e = cudaStreamWaitEvent(st, P.ev_panel, 0)) != cudaSuccess) return e;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   cnt += refine_with_inverse(n, F, Li, g, delta, y, z, r, ref, status, iters, st);
   if (launches) *launches = cnt;

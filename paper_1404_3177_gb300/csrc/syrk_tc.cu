@@ -474,11 +474,65 @@ __global__ void __launch_bounds__(192, 1) chol_update_tc_kernel(const CUtensorMa
       wait_bounded(drain, 0u, abort_flag, err, kWaitPanel, false);
     }
   } else {
+    // Epilogue: C -= accumulator, 32 columns (one chunk) at a time.  While a
+    // chunk is written back the old C values of the next chunk (of this unit or
+    // of the CTA's next unit) are already in flight, in the other of two
+    // register buffers: the loads, not the tensor cores, set the pace of this
+    // kernel.  Whole tiles strictly below the diagonal and inside the matrix
+    // (all but the diagonal and last tiles) take a path without per-element
+    // checks and with 32-bit offsets.
     const int quarter = warp & 3;
     uint32_t acc_ph[2] = {0u, 0u};
     int local = 0;
-    for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
-      const CholUnit w = units[u];
+    const int ldi = (int)ld;
+    auto interior = [&](const CholUnit &w) {
+      return !w.tri && (int64_t)(w.ti + 1) * kTile <= n && (int64_t)(w.tj + 1) * kTile <= n;
+    };
+    auto load_chunk = [&](const CholUnit &w, int c, float(&dst)[32]) {
+      const float *C = w.cbuf ? C1 : C0;
+      const int64_t row = (int64_t)w.ti * kTile + quarter * 32 + lane;
+      const int64_t col0 = (int64_t)w.tj * kTile + 32 * c;
+      const float *src = C + col0 * ld + row;
+      if (interior(w)) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) dst[j] = src[j * ldi];
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int64_t col = col0 + j;
+          dst[j] = (row < n && col < n && (!w.tri || col <= row)) ? src[(int64_t)j * ld] : 0.f;
+        }
+      }
+    };
+    auto store_chunk = [&](const CholUnit &w, int b, int c, const float(&old)[32]) {
+      uint32_t v[32];
+      tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kTile + 32 * c), v);
+      float *C = w.cbuf ? C1 : C0;
+      const int64_t row = (int64_t)w.ti * kTile + quarter * 32 + lane;
+      const int64_t col0 = (int64_t)w.tj * kTile + 32 * c;
+      float *dst = C + col0 * ld + row;
+      if (interior(w)) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) dst[j * ldi] = old[j] - __uint_as_float(v[j]);
+      } else if (row < n) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int64_t col = col0 + j;
+          if (col < n && (!w.tri || col <= row)) dst[(int64_t)j * ld] = old[j] - __uint_as_float(v[j]);
+        }
+      }
+    };
+    float bufA[32], bufB[32];
+    int u = blockIdx.x;
+    CholUnit wc{};
+    if (u < nunits) {
+      wc = units[u];
+      load_chunk(wc, 0, bufA);
+    }
+    for (; u < nunits; u += gridDim.x) {
+      const int un = u + gridDim.x;
+      CholUnit wn{};
+      if (un < nunits) wn = units[un];
       const int b = local & 1;
       ++local;
       int ok = 0;
@@ -487,30 +541,18 @@ __global__ void __launch_bounds__(192, 1) chol_update_tc_kernel(const CUtensorMa
       if (!ok) break;
       acc_ph[b] ^= 1u;
       tc_fence_after();
-      float *C = w.cbuf ? C1 : C0;
-      const int64_t row = (int64_t)w.ti * kTile + quarter * 32 + lane;
-#pragma unroll 1
-      for (int c0 = 0; c0 < kTile; c0 += 32) {
-        uint32_t v[32];
-        tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kTile + c0), v);
-        const int64_t col0 = (int64_t)w.tj * kTile + c0;
-        if (row >= n) continue;
-        float *dst = C + col0 * ld + row;
-        float prev[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int64_t col = col0 + j;
-          prev[j] = (col < n && (!w.tri || col <= row)) ? dst[(int64_t)j * ld] : 0.f;
-        }
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int64_t col = col0 + j;
-          if (col < n && (!w.tri || col <= row)) dst[(int64_t)j * ld] = prev[j] - __uint_as_float(v[j]);
-        }
-      }
+      load_chunk(wc, 1, bufB);
+      store_chunk(wc, b, 0, bufA);
+      load_chunk(wc, 2, bufA);
+      store_chunk(wc, b, 1, bufB);
+      load_chunk(wc, 3, bufB);
+      store_chunk(wc, b, 2, bufA);
+      if (un < nunits) load_chunk(wn, 0, bufA);
+      store_chunk(wc, b, 3, bufB);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[b]);
+      wc = wn;
     }
   }
 
