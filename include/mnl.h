@@ -481,7 +481,10 @@ MNL_API int mnl_server_create(const mnl_server_opts *opts, void *stream, mnl_ser
 /* Queue a request.  host: HOST arrays (copied before the call returns);
  * theta0: HOST [n_theta] start values or NULL (zeros).  MNL_ERR_OOM when the
  * request could never fit the budget; MNL_ERR_INVALID_ARG for a choice out of
- * range; MNL_ERR_UNSUPPORTED beyond n_theta 1400 or K 256. */
+ * range; MNL_ERR_UNSUPPORTED for gamma_base = 1, K > 256 or more than 16384
+ * raw gradient sums ((K-1)(p+d) + K f).  Requests with n_theta up to 1400 are
+ * solved by one CTA each inside the grouped launches; larger ones by the
+ * multi-CTA mixed (or, in MNL_FP64, float64) factorisation, one at a time. */
 MNL_API int mnl_server_submit(mnl_server *s, const mnl_dims *dims, const mnl_data *host, const double *theta0,
                               uint64_t *ticket);
 /* One tick: admit, iterate, retire.  Returns the numbers still admitted and queued. */

@@ -76,6 +76,7 @@ struct mnl_handle {
   int cg_max;           // conjugate-gradient iterations per Newton step at most
   double *cg;           // [3 n]: CG residual, direction, product (also scratch of mnl_hessian_vec)
   float *wbuf;          // [N][K] Hessian-vector residuals for the separate beta kernel (wide shapes)
+  float *ux, *bf;       // wide shapes: X-block utilities [N][K] and float32 coefficients of their GEMM
   // coefficients of dropped data columns (mnl_drop_columns), in the kernels' order
   int nmask;
   int64_t *mask_idx;    // device [n_theta] (the first nmask entries are used)
@@ -138,9 +139,9 @@ bool dims_ok(const mnl_dims *d) {
 }
 
 struct Sizes {
-  size_t P, zbar, part_full, part_ll, ops, main_part, band_part, z_part, F, owned, solve, zop, zt_part;
+  size_t P, zbar, part_full, part_ll, ops, main_part, band_part, z_part, F, owned, solve, zop, zt_part, ux;
   size_t total() const {
-    return P + zbar + part_full + part_ll + 2 * ops + main_part + band_part + z_part + F + owned + solve + zop +
+    return P + zbar + part_full + part_ll + ux + 2 * ops + main_part + band_part + z_part + F + owned + solve + zop +
            zt_part;
   }
 };
@@ -182,6 +183,8 @@ Sizes plan_sizes(const mnl_dims &d, int prec_in, bool owned, int nsm, int *main_
   z.zbar = (size_t)S.N * S.f * tsz;
   z.part_full = (size_t)pf->grid * (2 + S.n) * 8;
   z.part_ll = (size_t)pl->grid * 2 * 8;
+  // wide shapes: utilities of the X block ([N][K] float32) and float32 coefficients ([p][ux_ldb(K)])
+  z.ux = (pf->ux || pl->ux) ? (size_t)S.N * S.K * 4 + (size_t)S.p * ux_ldb(S.K) * 4 : 0;
   *ldn = round_up(S.N, 64);
   *mc_pad = round_up(S.mc, kTile);
   *nt1d = (int)(*mc_pad / kTile);
@@ -289,6 +292,8 @@ int run_pass(mnl_handle *h, const double *theta, bool full, const double *delta,
   io.err = h->err;
   io.wait_ns = h->wait_ns;
   io.w = h->w;
+  io.ux = h->ux;
+  io.bf = h->bf;
   CK(launch_pass(h->S, pl, h->fp64, full, io, h->st));
   CK(launch_pass_reduce(h->S, pl.grid, full, io.partials, h->scal + base, full ? h->grad : nullptr, h->st));
   h->launches += 2;
@@ -581,6 +586,8 @@ int hv_pass(mnl_handle *h, const double *v, double *out) {
   io.w = h->w;
   io.Pin = h->P;
   io.Wout = h->wbuf;
+  io.ux = h->ux;
+  io.bf = h->bf;
   CK(launch_pass(h->S, h->pfull, h->fp64, true, io, h->st));
   CK(launch_pass_reduce(h->S, h->pfull.grid, true, io.partials, h->scal + 10, out, h->st));
   h->launches += 2;
@@ -875,6 +882,9 @@ int mnl_create_ex(const mnl_dims *dims, const mnl_data *data, int precision, int
     return fail(rc);
   // Hessian-vector residuals for the separate beta kernel of the wide tiled pass
   if (!h->fp64 && h->pfull.tiled && plan_pass_beta_ext(S) && (rc = dalloc(h, &h->wbuf, (size_t)S.N * S.K * 4)))
+    return fail(rc);
+  if ((h->pfull.ux || h->pll.ux) && ((rc = dalloc(h, &h->ux, (size_t)S.N * S.K * 4)) ||
+                                     (rc = dalloc(h, &h->bf, (size_t)S.p * ux_ldb(S.K) * 4))))
     return fail(rc);
   h->ref = hfree ? nullptr : mixed_solve_ref(h->mwork, S.n);
   if (!hfree && S.n >= tc_chol_min_n()) {

@@ -98,7 +98,14 @@ struct PassIO {
   // separate beta kernel only) receives those residuals.
   const void *Pin;
   float *Wout;
+  // Wide shapes (PassPlan::ux): the utilities of the X block, U_x = X B, come
+  // from a float32 GEMM into ux ([N][K] float32) before the pass, with the
+  // coefficients as float32 in bf ([p][ux_ldb(K)]); both are scratch of the caller.
+  float *ux;
+  float *bf;
 };
+// Leading dimension of the float32 coefficient matrix of the utility GEMM.
+inline int ux_ldb(int K) { return (K + 127) / 128 * 128; }
 
 // Bits of the device error word: which kernel's bounded wait gave up.
 constexpr int kWaitSyrk = 1 | 2 | 4 | 8;  // tensor-core contraction (producer, MMA, epilogue, drain)
@@ -112,6 +119,7 @@ struct PassPlan {
   size_t smem;
   bool ok;
   bool tiled;                   // float32 pass with asynchronous tile copies (pass_tile.cu)
+  bool ux;                      // tiled, with the X-block utilities from a separate GEMM (wide shapes)
 };
 // allow_tiled: the float32 path may use the tiled pass (needs io.err and
 // 16-byte aligned X, Y, Z, choice).

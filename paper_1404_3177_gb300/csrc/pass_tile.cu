@@ -49,6 +49,7 @@ struct TileDims {
   int off_bt, off_gt, off_al, off_xt, off_rt, off_red, off_bar, off_stage;
   int kp2, lq, wk, wl, nyz;                                          // gradient work
   int beta_ext;  // the beta gradient is left to grad_beta_kernel (too many outputs for the register tiles)
+  int ux;        // the X-block utilities come precomputed (io.ux): the stage holds their rows instead of X's
 };
 
 struct KahanF {
@@ -144,16 +145,18 @@ __global__ void __launch_bounds__(kPT, kYZSlots == 4 ? 1 : 2) pass_tile_kernel(T
   // coefficients theta (+ t delta), zero for the base alternative and the padding
   const double tsc = io.delta ? *io.tscale : 0.0;
   auto coef = [&](int64_t a) { return io.theta[a] + (io.delta ? tsc * io.delta[a] : 0.0); };
-  for (int e = tid; e < p * Kpad; e += kPT) {
-    const int j = e / Kpad, k = e - j * Kpad;
-    Bt[e] = (k >= 1 && k < K) ? (float)coef((int64_t)(k - 1) * p + j) : 0.f;
-  }
+  if (!D.ux)
+    for (int e = tid; e < p * Kpad; e += kPT) {
+      const int j = e / Kpad, k = e - j * Kpad;
+      Bt[e] = (k >= 1 && k < K) ? (float)coef((int64_t)(k - 1) * p + j) : 0.f;
+    }
   for (int e = tid; e < d * Kpad; e += kPT) {
     const int j = e / Kpad, k = e - j * Kpad;
     Gt[e] = (k >= 1 && k < K) ? (float)coef(D.nb + (int64_t)(k - 1) * d + j) : 0.f;
   }
   for (int j = tid; j < f; j += kPT) al[j] = (float)coef(D.mc + j);
-  for (int e = p * R4 + tid; e < D.pp * R4; e += kPT) Xt[xcol(e / R4) + e % R4] = 0.f;  // padding columns
+  if (!D.ux)
+    for (int e = p * R4 + tid; e < D.pp * R4; e += kPT) Xt[xcol(e / R4) + e % R4] = 0.f;  // padding columns
   if (FULL)
     for (int e = tid; e < R4; e += kPT) Rt[Kpad * R4 + e] = 0.f;       // row read by the last class pair
   if (tid == 0) {
@@ -164,14 +167,16 @@ __global__ void __launch_bounds__(kPT, kYZSlots == 4 ? 1 : 2) pass_tile_kernel(T
   }
   __syncthreads();
 
-  const uint32_t tile_bytes = (uint32_t)(R * (p + K * d + K * f + 1) * 4);
+  const int px = D.ux ? K : p;  // floats per observation in the stage's first block (U_x or X)
+  const float *xsrc = D.ux ? io.ux : io.X;
+  const uint32_t tile_bytes = (uint32_t)(R * (px + K * d + K * f + 1) * 4);
   auto full_tile = [&](int64_t tl) { return (tl + 1) * R <= N; };
   auto issue = [&](int64_t tl, int s) {  // one thread
     const int64_t row0 = tl * R;
     unsigned char *st = sm + D.off_stage + s * D.stage_bytes;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(&bar[s])), "r"(tile_bytes)
                  : "memory");
-    bulk_copy(st + D.off_x, io.X + row0 * p, (uint32_t)(R * p * 4), &bar[s]);
+    bulk_copy(st + D.off_x, xsrc + row0 * px, (uint32_t)(R * px * 4), &bar[s]);
     if (d) bulk_copy(st + D.off_y, io.Y + row0 * K * d, (uint32_t)(R * K * d * 4), &bar[s]);
     if (f) bulk_copy(st + D.off_z, io.Z + row0 * K * f, (uint32_t)(R * K * f * 4), &bar[s]);
     bulk_copy(st + D.off_c, io.choice + row0, (uint32_t)(R * 4), &bar[s]);
@@ -224,18 +229,20 @@ __global__ void __launch_bounds__(kPT, kYZSlots == 4 ? 1 : 2) pass_tile_kernel(T
       if (!stage_wait(&bar[s], par, io.wait_ns)) s_abort = 1;
       else if (tid == 0) pend[s] = -1;
     } else {  // the partial last tile: plain loads, zero padding
-      for (int e = tid; e < R * p; e += kPT) Xs[e] = e < nrows * p ? io.X[row0 * p + e] : 0.f;
+      for (int e = tid; e < R * px; e += kPT) Xs[e] = e < nrows * px ? xsrc[row0 * px + e] : 0.f;
       for (int e = tid; e < R * K * d; e += kPT) Ys[e] = e < nrows * K * d ? io.Y[row0 * K * d + e] : 0.f;
       for (int e = tid; e < R * K * f; e += kPT) Zs[e] = e < nrows * K * f ? io.Z[row0 * K * f + e] : 0.f;
       for (int e = tid; e < R; e += kPT) cs[e] = e < nrows ? io.choice[row0 + e] : -1;
     }
     __syncthreads();
     if (s_abort) break;
-    for (int e = tid; e < kR * p; e += kPT) {  // lanes over rows: no division, conflict-free
-      const int r = e & (kR - 1), l = e >> kRsh;
-      Xt[xcol(l) + r] = Xs[r * p + l];
+    if (!D.ux) {
+      for (int e = tid; e < kR * p; e += kPT) {  // lanes over rows: no division, conflict-free
+        const int r = e & (kR - 1), l = e >> kRsh;
+        Xt[xcol(l) + r] = Xs[r * p + l];
+      }
+      __syncthreads();
     }
-    __syncthreads();
 
     // ---- utilities, softmax, l (and P, residuals, zbar) ----
     {
@@ -245,15 +252,24 @@ __global__ void __launch_bounds__(kPT, kYZSlots == 4 ? 1 : 2) pass_tile_kernel(T
       for (int r = 0; r < RPW; ++r)
 #pragma unroll
         for (int c = 0; c < CS; ++c) u[r][c] = 0.f;
-#pragma unroll 2
-      for (int j = 0; j < p; ++j) {
-        float xv[RPW];
-        load_rows<RPW>(Xt + xcol(j) + r0, xv);
+      if (D.ux) {  // precomputed x_i . beta_k
 #pragma unroll
         for (int c = 0; c < CS; ++c) {
-          const float b = Bt[j * Kpad + lane + 32 * c];
+          const int k = lane + 32 * c;
 #pragma unroll
-          for (int r = 0; r < RPW; ++r) u[r][c] = fmaf(xv[r], b, u[r][c]);
+          for (int r = 0; r < RPW; ++r) u[r][c] = k < K ? Xs[(r0 + r) * K + k] : 0.f;
+        }
+      } else {
+#pragma unroll 2
+        for (int j = 0; j < p; ++j) {
+          float xv[RPW];
+          load_rows<RPW>(Xt + xcol(j) + r0, xv);
+#pragma unroll
+          for (int c = 0; c < CS; ++c) {
+            const float b = Bt[j * Kpad + lane + 32 * c];
+#pragma unroll
+            for (int r = 0; r < RPW; ++r) u[r][c] = fmaf(xv[r], b, u[r][c]);
+          }
         }
       }
 #pragma unroll
@@ -626,9 +642,100 @@ cudaError_t launch_grad_beta(const Shape &s, int grid, const PassIO &io, cudaStr
   return cudaErrorInvalidValue;
 }
 
+// ---------------------------------------------------------------------------
+// Utilities of the individual-specific block for wide shapes (eq. "unormalized
+// utility"): U_x[i][k] = x_i . beta_k (beta_0 = 0) as the float32 product
+// U_x = X B, B[l][k] = beta_k[l] rounded to float32 as in the fused pass.
+// For these shapes the product is most of the pass's arithmetic; as a
+// register-tiled GEMM (CTA tile 128 observations x 128 classes, 16 columns of
+// X per step through shared memory, 8 x 8 outputs per thread) it runs at the
+// FMA rate instead of the shared-memory load rate of the fused loop.
+// ---------------------------------------------------------------------------
+constexpr int kUgM = 128, kUgN = 128, kUgK = 16;
+
+__global__ void __launch_bounds__(256) ux_coef_kernel(int p, int K, int ldb, const double *__restrict__ theta,
+                                                      const double *__restrict__ delta,
+                                                      const double *__restrict__ tscale, float *__restrict__ Bf) {
+  const double t = delta ? *tscale : 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p * ldb; e += gridDim.x * blockDim.x) {
+    const int l = e / ldb, k = e - l * ldb;
+    float v = 0.f;
+    if (k >= 1 && k < K) {
+      const int64_t a = (int64_t)(k - 1) * p + l;
+      v = (float)(theta[a] + (delta ? t * delta[a] : 0.0));
+    }
+    Bf[e] = v;
+  }
+}
+
+__global__ void __launch_bounds__(256, 2) ux_gemm_kernel(int64_t N, int p, int K, int ldb,
+                                                         const float *__restrict__ X, const float *__restrict__ Bf,
+                                                         float *__restrict__ U) {
+  __shared__ __align__(16) float As[kUgK][kUgM + 4];  // As[l][r] = X[row0 + r][l0 + l]
+  __shared__ __align__(16) float Bs[kUgK][kUgN];      // Bs[l][c] = B[l0 + l][col0 + c]
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t row0 = (int64_t)blockIdx.x * kUgM;
+  const int col0 = blockIdx.y * kUgN;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  for (int l0 = 0; l0 < p; l0 += kUgK) {
+    float xa[8], xb[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = tid + 256 * u, r = e >> 4, l = e & 15;
+      xa[u] = (row0 + r < N && l0 + l < p) ? X[(row0 + r) * p + l0 + l] : 0.f;
+      const int lb = e >> 7, c = e & 127;
+      xb[u] = (l0 + lb < p) ? Bf[(int64_t)(l0 + lb) * ldb + col0 + c] : 0.f;
+    }
+    __syncthreads();  // the previous step is done with As, Bs
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = tid + 256 * u;
+      As[e & 15][e >> 4] = xa[u];
+      Bs[e >> 7][e & 127] = xb[u];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < kUgK; ++l) {
+      const float4 a0 = *reinterpret_cast<const float4 *>(&As[l][4 * ty]);
+      const float4 a1 = *reinterpret_cast<const float4 *>(&As[l][64 + 4 * ty]);
+      const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[l][4 * tx]);
+      const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[l][64 + 4 * tx]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int64_t r = row0 + (i < 4 ? 4 * ty + i : 64 + 4 * ty + i - 4);
+    if (r >= N) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = col0 + (j < 4 ? 4 * tx + j : 64 + 4 * tx + j - 4);
+      if (c < K) U[r * K + c] = acc[i][j];
+    }
+  }
+}
+
+cudaError_t launch_ux(const Shape &s, const PassIO &io, cudaStream_t st) {
+  const int ldb = ux_ldb(s.K);
+  ux_coef_kernel<<<(unsigned)std::min((s.p * ldb + 255) / 256, 1024), 256, 0, st>>>(s.p, s.K, ldb, io.theta, io.delta,
+                                                                                   io.tscale, io.bf);
+  const dim3 grid((unsigned)((s.N + kUgM - 1) / kUgM), (unsigned)((s.K + kUgN - 1) / kUgN));
+  ux_gemm_kernel<<<grid, 256, 0, st>>>(s.N, s.p, s.K, ldb, io.X, io.bf, io.ux);
+  return cudaGetLastError();
+}
+
 int round_up_int(int v, int m) { return (v + m - 1) / m * m; }
 
-bool make_tile_dims(const Shape &s, bool full, int rpw, TileDims &D, size_t &smem) {
+bool make_tile_dims(const Shape &s, bool full, int rpw, TileDims &D, size_t &smem, bool ux = false) {
   if (s.K < 2 || s.K > 256) return false;
   const int cs = (s.K + 31) / 32;
   D.N = s.N; D.K = s.K; D.p = s.p; D.d = s.d; D.f = s.f;
@@ -640,16 +747,17 @@ bool make_tile_dims(const Shape &s, bool full, int rpw, TileDims &D, size_t &sme
   D.nb = (int)s.nb; D.mc = (int)s.mc; D.n = (int)s.n;
   D.ntiles = (s.N + D.R - 1) / D.R;
   int o = 0;
-  D.off_x = o; o += round_up_int(D.R * s.p * 4, 128);
+  D.ux = ux ? 1 : 0;
+  D.off_x = o; o += round_up_int(D.R * (ux ? s.K : s.p) * 4, 128);
   D.off_y = o; o += round_up_int(D.R * s.K * s.d * 4, 128);
   D.off_z = o; o += round_up_int(D.R * s.K * s.f * 4, 128);
   D.off_c = o; o += round_up_int(D.R * 4, 128);
   D.stage_bytes = o;
   o = 0;
-  D.off_bt = o; o += round_up_int(s.p * D.Kpad * 4, 128);
+  D.off_bt = o; o += ux ? 0 : round_up_int(s.p * D.Kpad * 4, 128);
   D.off_gt = o; o += round_up_int(s.d * D.Kpad * 4, 128);
   D.off_al = o; o += round_up_int(std::max(s.f, 1) * 4, 128);
-  D.off_xt = o; o += round_up_int(D.pp / 4 * D.xq * 4, 128);
+  D.off_xt = o; o += ux ? 0 : round_up_int(D.pp / 4 * D.xq * 4, 128);
   D.off_rt = o; o += full ? round_up_int((D.Kpad + 1) * D.R4 * 4, 128) : 0;
   D.off_red = o; o += round_up_int(std::max(2 * kPT / 32, s.K * s.f) * 8, 128);
   D.off_bar = o; o += 128;
@@ -660,7 +768,7 @@ bool make_tile_dims(const Shape &s, bool full, int rpw, TileDims &D, size_t &sme
   D.wk = (D.kp2 + 3) / 4;
   D.wl = (D.lq + 7) / 8;
   D.nyz = (s.K - 1) * s.d + s.K * s.f;
-  D.beta_ext = full && D.wk * D.wl > 8 * kBetaItems;
+  D.beta_ext = full && (ux || D.wk * D.wl > 8 * kBetaItems);
   if (D.beta_ext && (s.p > 16 * kGbMaxJ || s.K > 16 * kGbMaxK)) return false;
   if (full && D.nyz > kPT * 4) return false;
   // two CTAs per SM when a 2-stage ring fits in half of the shared memory, else one
@@ -704,9 +812,13 @@ bool plan_pass_beta_ext(const Shape &s) {
 bool plan_pass_tiled(const Shape &s, bool full, int num_sms, PassPlan &pl) {
   TileDims D{};
   size_t smem = 0;
+  // Wide shapes (the full pass's beta gradient does not fit its register
+  // tiles): the X-block utilities from the separate GEMM, in both passes.
+  const bool ux = plan_pass_beta_ext(s);
   for (int rpw : {2}) {
-    if (!make_tile_dims(s, full, rpw, D, smem)) continue;
+    if (!make_tile_dims(s, full, rpw, D, smem, ux)) continue;
     pl.tiled = true;
+    pl.ux = ux;
     pl.rows = D.R;
     pl.block = kPT;
     pl.npt = 0;
@@ -722,13 +834,19 @@ bool plan_pass_tiled(const Shape &s, bool full, int num_sms, PassPlan &pl) {
 cudaError_t launch_pass_tiled(const Shape &s, const PassPlan &pl, bool full, const PassIO &io, cudaStream_t st) {
   TileDims D{};
   size_t smem = 0;
-  if (!make_tile_dims(s, full, pl.rows / 8, D, smem) || smem != pl.smem || io.err == nullptr) return cudaErrorInvalidValue;
+  if (!make_tile_dims(s, full, pl.rows / 8, D, smem, pl.ux) || smem != pl.smem || io.err == nullptr)
+    return cudaErrorInvalidValue;
+  if (pl.ux && (!io.ux || !io.bf || (reinterpret_cast<uintptr_t>(io.ux) & 15))) return cudaErrorInvalidValue;
   const bool aligned = ((reinterpret_cast<uintptr_t>(io.X) | reinterpret_cast<uintptr_t>(io.choice) |
                          reinterpret_cast<uintptr_t>(io.w) |
                          (s.d ? reinterpret_cast<uintptr_t>(io.Y) : 0) | (s.f ? reinterpret_cast<uintptr_t>(io.Z) : 0)) &
                         15) == 0;
   if (!aligned) return cudaErrorInvalidValue;
   if (pl.rows != 16) return cudaErrorInvalidValue;
+  if (pl.ux) {
+    cudaError_t e = launch_ux(s, io, st);
+    if (e != cudaSuccess) return e;
+  }
   if (!full) return launch_cs<2, false>(D, pl.grid, smem, io, st);
   if (io.Pin && D.beta_ext && !io.Wout) return cudaErrorInvalidValue;
   cudaError_t e = launch_cs<2, true>(D, pl.grid, smem, io, st);
