@@ -11,7 +11,7 @@ Newton solve, step-halving line search, coefficient update), so every step
 does the same work.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|tf32|fp64]
-                    [--workload c3|c2] [--extras all|none]
+                    [--workload c3|c2] [--extras all|none] [--rows N]
     python bench.py --impl reference ...     # the FP64 CPU oracle on the host cores
 
 Timing: CUDA events on the stream the library uses, W untimed warm-up steps,
@@ -257,9 +257,13 @@ def allmax(world, v):
     return float(t.item())
 
 
-def workload_problem(name):
+def workload_problem(name, rows=None):
+    """The workload's problem; rows (optional) replaces its number of observations (same shape and seed)."""
     from paper_1404_3177_gb300 import datagen
-    prob = datagen.config3() if name == "c3" else datagen.config2()
+    if name == "c3":
+        prob = datagen.config3(rows) if rows else datagen.config3()
+    else:
+        prob = datagen.config2(rows) if rows else datagen.config2()
     return prob, prob.name
 
 
@@ -271,7 +275,7 @@ def run_reference(args, world, rank):
     """The FP64 CPU oracle as it stands, one bounded (extrapolated) sample per step, rank 0 only."""
     if rank != 0:
         return
-    prob, wname = workload_problem(args.workload)
+    prob, wname = workload_problem(args.workload, args.rows)
     for _ in range(args.warmup):
         oracle_iteration_seconds(prob, args.ref_rows, args.ref_hess_rows, args.ref_chol_n)
     times, desc = [], ""
@@ -456,7 +460,7 @@ def run_ours(args, world, rank, local):
     _build.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    prob, wname = workload_problem(args.workload)
+    prob, wname = workload_problem(args.workload, args.rows)
     Xh, Yh, Zh, ch = _host(prob)
     X, Y, Z, c = (t.to(dev) if t is not None else None for t in (Xh, Yh, Zh, ch))
     n = prob.n_theta
@@ -716,6 +720,9 @@ def main():
     ap.add_argument("--workload", default="c3", choices=["c3", "c2"],
                     help="c3: N=500000 K=100 p=100 f=10 (default); c2: N=200000 K=50 p=50 d=5 f=5")
     ap.add_argument("--precision", default="bf16", choices=["bf16", "tf32", "fp64"])
+    ap.add_argument("--rows", type=int, default=None,
+                    help="observations of the workload's shape (default: the workload's N); smaller values size "
+                         "profiler captures and are not the workload's bench line")
     ap.add_argument("--solve", default="auto", choices=["auto", "fp64", "mixed"],
                     help="Newton solve: float64 Cholesky, or float32 factor + float64 refinement")
     ap.add_argument("--extras", default="all", choices=["all", "none"],
