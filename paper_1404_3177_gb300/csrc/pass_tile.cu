@@ -559,6 +559,14 @@ __global__ void __launch_bounds__(256, 1) grad_beta_kernel(int64_t N, int K, int
     }
     __syncthreads();
     if (s_abort) break;
+    if (!p_is_residual) {  // residuals w_i (I(y_i = k) - P_ik) of the tile, in place of P (once per tile)
+      for (int e = tid; e < kGbRows * K; e += 256) {
+        const int r = e / K, k = e - r * K;
+        const float wr = w ? ws[r] : 1.f;
+        Ps[e] = wr * ((k == cs[r] ? 1.f : 0.f) - Ps[e]);
+      }
+      __syncthreads();
+    }
     float acc[JA][KB];
 #pragma unroll
     for (int a = 0; a < JA; ++a)
@@ -566,8 +574,6 @@ __global__ void __launch_bounds__(256, 1) grad_beta_kernel(int64_t N, int K, int
       for (int c = 0; c < KB; ++c) acc[a][c] = 0.f;
 #pragma unroll 2
     for (int r = 0; r < kGbRows; ++r) {
-      const int y = cs[r];
-      const float wr = w ? ws[r] : 1.f;
       float x[JA], rr[KB];
 #pragma unroll
       for (int a = 0; a < JA; ++a) {
@@ -577,7 +583,7 @@ __global__ void __launch_bounds__(256, 1) grad_beta_kernel(int64_t N, int K, int
 #pragma unroll
       for (int c = 0; c < KB; ++c) {
         const int k = ty + 16 * c;
-        rr[c] = k < K ? (p_is_residual ? Ps[r * K + k] : wr * ((k == y ? 1.f : 0.f) - Ps[r * K + k])) : 0.f;
+        rr[c] = k < K ? Ps[r * K + k] : 0.f;
       }
 #pragma unroll
       for (int a = 0; a < JA; ++a)
@@ -681,8 +687,8 @@ __global__ void __launch_bounds__(256, 2) ux_gemm_kernel(int64_t N, int p, int K
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-  for (int l0 = 0; l0 < p; l0 += kUgK) {
-    float xa[8], xb[8];
+  float xa[8], xb[8];
+  auto load = [&](int l0) {
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int e = tid + 256 * u, r = e >> 4, l = e & 15;
@@ -690,6 +696,9 @@ __global__ void __launch_bounds__(256, 2) ux_gemm_kernel(int64_t N, int p, int K
       const int lb = e >> 7, c = e & 127;
       xb[u] = (l0 + lb < p) ? Bf[(int64_t)(l0 + lb) * ldb + col0 + c] : 0.f;
     }
+  };
+  load(0);
+  for (int l0 = 0; l0 < p; l0 += kUgK) {
     __syncthreads();  // the previous step is done with As, Bs
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
@@ -698,6 +707,7 @@ __global__ void __launch_bounds__(256, 2) ux_gemm_kernel(int64_t N, int p, int K
       Bs[e >> 7][e & 127] = xb[u];
     }
     __syncthreads();
+    if (l0 + kUgK < p) load(l0 + kUgK);  // in flight during the products below
 #pragma unroll
     for (int l = 0; l < kUgK; ++l) {
       const float4 a0 = *reinterpret_cast<const float4 *>(&As[l][4 * ty]);
