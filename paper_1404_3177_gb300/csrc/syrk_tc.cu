@@ -360,14 +360,18 @@ __global__ void __launch_bounds__(192, 1) syrk_tc_kernel(const CUtensorMap *__re
 // ld), A = rows ti of maps (0, 1), B = rows tj of maps (2 bmap, 2 bmap + 1);
 // tri: only entries on or below the diagonal of the tile are written.
 // Roles as in the SYRK kernel: warp 0 TMA producer, warp 1 MMA issuer (one
-// lane) and TMEM owner, warps 2-5 the epilogue (read C, subtract, write C,
-// 128 contiguous bytes per store instruction across the warp).
+// lane) and TMEM owner, warps 2-9 the epilogue (read C, subtract, write C,
+// 128 contiguous bytes per store instruction across the warp): two warps per
+// TMEM lane quarter, each taking half of the tile's columns, so that twice as
+// many C loads are in flight (the epilogue's load latency sets the pace).
 // ---------------------------------------------------------------------------
 constexpr int kCuStages = 3;
+constexpr int kCuEpiWarps = 8;                    // epilogue warps: two per TMEM lane quarter
+constexpr int kCuThreads = 64 + 32 * kCuEpiWarps;  // + the producer and MMA warps
 constexpr int kCuStageBytes = 4 * kOpBytes;  // Ah, Al, Bh, Bl
 constexpr int kCuSmemBytes = kCuStages * kCuStageBytes + 256 + 1024;
 
-__global__ void __launch_bounds__(192, 1) chol_update_tc_kernel(const CUtensorMap *__restrict__ maps,
+__global__ void __launch_bounds__(kCuThreads, 1) chol_update_tc_kernel(const CUtensorMap *__restrict__ maps,
                                                                 const CholUnit *__restrict__ units, int nunits,
                                                                 float *__restrict__ C0, float *__restrict__ C1,
                                                                 int64_t ld, int64_t n, int *__restrict__ err,
@@ -387,7 +391,7 @@ __global__ void __launch_bounds__(192, 1) chol_update_tc_kernel(const CUtensorMa
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kCuStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 4); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], kCuEpiWarps); }
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -481,7 +485,8 @@ __global__ void __launch_bounds__(192, 1) chol_update_tc_kernel(const CUtensorMa
     // kernel.  Whole tiles strictly below the diagonal and inside the matrix
     // (all but the diagonal and last tiles) take a path without per-element
     // checks and with 32-bit offsets.
-    const int quarter = warp & 3;
+    const int quarter = warp & 3;          // TMEM lanes 32 quarter .. + 31 (the rows of this warp)
+    const int cbase = 2 * ((warp - 2) >> 2);  // two warps per quarter: chunks cbase, cbase + 1 of each tile
     uint32_t acc_ph[2] = {0u, 0u};
     int local = 0;
     const int ldi = (int)ld;
@@ -527,7 +532,7 @@ __global__ void __launch_bounds__(192, 1) chol_update_tc_kernel(const CUtensorMa
     CholUnit wc{};
     if (u < nunits) {
       wc = units[u];
-      load_chunk(wc, 0, bufA);
+      load_chunk(wc, cbase, bufA);
     }
     for (; u < nunits; u += gridDim.x) {
       const int un = u + gridDim.x;
@@ -541,14 +546,10 @@ __global__ void __launch_bounds__(192, 1) chol_update_tc_kernel(const CUtensorMa
       if (!ok) break;
       acc_ph[b] ^= 1u;
       tc_fence_after();
-      load_chunk(wc, 1, bufB);
-      store_chunk(wc, b, 0, bufA);
-      load_chunk(wc, 2, bufA);
-      store_chunk(wc, b, 1, bufB);
-      load_chunk(wc, 3, bufB);
-      store_chunk(wc, b, 2, bufA);
-      if (un < nunits) load_chunk(wn, 0, bufA);
-      store_chunk(wc, b, 3, bufB);
+      load_chunk(wc, cbase + 1, bufB);
+      store_chunk(wc, b, cbase, bufA);
+      if (un < nunits) load_chunk(wn, cbase, bufA);
+      store_chunk(wc, b, cbase + 1, bufB);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[b]);
@@ -726,7 +727,7 @@ cudaError_t chol_update_tc_setup() {
 cudaError_t launch_chol_update_tc(const CUtensorMap *maps, const CholUnit *units, int nunits, int grid, float *C0,
                                   float *C1, int64_t ld, int64_t n, int *err, uint64_t wait_ns, cudaStream_t st) {
   if (nunits <= 0) return cudaSuccess;
-  chol_update_tc_kernel<<<grid, 192, kCuSmemBytes, st>>>(maps, units, nunits, C0, C1, ld, n, err,
+  chol_update_tc_kernel<<<grid, kCuThreads, kCuSmemBytes, st>>>(maps, units, nunits, C0, C1, ld, n, err,
                                                          wait_ns ? wait_ns : kTimeoutNs);
   return cudaGetLastError();
 }
