@@ -54,8 +54,8 @@ CONFIG_NOTE = "inputs larger than L2 (no flush)"
 # smaller N of the same shape, the figure is scaled to the full N (the traffic grows in proportion).
 MEASURED_TRAFFIC: dict = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass) on
-    # `python bench.py --extras none --steps 1 --warmup 1 --no-cpu-baseline`: 67.62 GB read + 7.08 GB written
-    ("c3_N500000_K100_p100_d0_f10", "syrk_AtA"): {"bytes": 74.70e9, "sources": "97fa32a9bb83e3a2"},
+    # `python bench.py --extras none --steps 1 --warmup 1 --no-cpu-baseline`: 68.13 GB read + 7.08 GB written
+    ("c3_N500000_K100_p100_d0_f10", "syrk_AtA"): {"bytes": 75.21e9, "sources": "dfc565d9cd2d8e19"},
 }
 KERNEL_SOURCES = {
     "syrk_AtA": ["paper_1404_3177_gb300/csrc/syrk_tc.cu", "paper_1404_3177_gb300/csrc/hessian.cu"],
