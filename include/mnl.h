@@ -138,7 +138,10 @@ enum { MNL_WAIT_SYRK = 15, MNL_WAIT_PASS = 16, MNL_WAIT_COOP = 32, MNL_WAIT_PANE
  * cores (float32 in a mixed solve, float64 otherwise), or the panel
  * factorisation whose trailing updates run on the tensor cores (mixed solves
  * with n_theta >= 4096; environment variable MNL_TC_CHOL_MIN_N, read by
- * mnl_create, moves that threshold). */
+ * mnl_create, moves that threshold).  The panel factorisation runs the next
+ * panel's diagonal and panel steps on a second stream that the handle owns,
+ * ordered by events after the work already on the handle's stream and before
+ * anything enqueued there later, so the stream semantics above still hold. */
 enum { MNL_FACTOR_NONE = 0, MNL_FACTOR_COOP = 1, MNL_FACTOR_TENSOR = 2 };
 
 typedef struct mnl_fit_opts {
