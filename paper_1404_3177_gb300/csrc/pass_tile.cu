@@ -825,7 +825,9 @@ bool plan_pass_tiled(const Shape &s, bool full, int num_sms, PassPlan &pl) {
   // Wide shapes (the full pass's beta gradient does not fit its register
   // tiles): the X-block utilities from the separate GEMM, in both passes.
   const bool ux = plan_pass_beta_ext(s);
-  for (int rpw : {2}) {
+  // the log-likelihood-only pass of a wide shape: 8-row tiles, whose ring fits two CTAs per SM
+  const int rpw_first = ux && !full ? 1 : 2;
+  for (int rpw = rpw_first; rpw <= 2; ++rpw) {
     if (!make_tile_dims(s, full, rpw, D, smem, ux)) continue;
     pl.tiled = true;
     pl.ux = ux;
@@ -852,12 +854,12 @@ cudaError_t launch_pass_tiled(const Shape &s, const PassPlan &pl, bool full, con
                          (s.d ? reinterpret_cast<uintptr_t>(io.Y) : 0) | (s.f ? reinterpret_cast<uintptr_t>(io.Z) : 0)) &
                         15) == 0;
   if (!aligned) return cudaErrorInvalidValue;
-  if (pl.rows != 16) return cudaErrorInvalidValue;
+  if (pl.rows != 16 && !(pl.rows == 8 && pl.ux && !full)) return cudaErrorInvalidValue;
   if (pl.ux) {
     cudaError_t e = launch_ux(s, io, st);
     if (e != cudaSuccess) return e;
   }
-  if (!full) return launch_cs<2, false>(D, pl.grid, smem, io, st);
+  if (!full) return pl.rows == 8 ? launch_cs<1, false>(D, pl.grid, smem, io, st) : launch_cs<2, false>(D, pl.grid, smem, io, st);
   if (io.Pin && D.beta_ext && !io.Wout) return cudaErrorInvalidValue;
   cudaError_t e = launch_cs<2, true>(D, pl.grid, smem, io, st);
   if (e == cudaSuccess && D.beta_ext) e = launch_grad_beta(s, pl.grid, io, st);
